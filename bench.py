@@ -1,0 +1,324 @@
+#!/usr/bin/env python3
+"""Benchmark: time to an FP64-verified relative residual of 1e-10 on the
+128^3 high-contrast 7-point diffusion system (2,097,152 unknowns), AMP-PCG vs
+FP64 PCG on the same kernels, one B300; HBM GB/s of the kernels.
+
+One step = one complete solve (every row of the hot path: initial residual,
+selector, scale+precondition, search direction, SpMV, updates, stopping test,
+FP64 verification), inputs resident in HBM.  L2 is flushed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (bounded sample, scaled to the same metric).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 rel. residual, AMP-PCG vs FP64 PCG on 1 B300; HBM GB/s"
+TOL = 1e-10
+MAXIT = 20000
+GRID = 128
+SIGMA = 2.0
+
+
+def workload():
+    import workloads as W
+    a = W.diffusion3d(GRID, SIGMA, seed=0)
+    b = W.rhs_uniform(a.n, seed=1)
+    return a, b
+
+
+def config_dict(a, extra=None):
+    d = {"workload": f"{GRID}^3 7-point variable-coefficient diffusion (Dirichlet), face coeff "
+                     f"exp((g_i+g_j)/2), g = 3x box-filtered N(0,1) field scaled to sigma={SIGMA}; "
+                     "Jacobi; b~U[-1,1] seed 1; x0=0; tol 1e-10 FP64-verified",
+         "n": int(a.n), "nnz": int(a.nnz), "coef_contrast": float(a.info["contrast"]),
+         "solver": "AMP-PCG(FP16) linear criterion (ell=5, C=1), LINF_POW2 scaling, FP64 verify+replace",
+         "baseline_solver": "PCG(FP64), Alg. 1, same kernels", "l2_flush": True}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            with open(self.f.name) as g:
+                for line in g:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def alg_bytes(kernel: str, phase: str, n: int, nnz: int, nslices: int, idx_bytes: int) -> float:
+    """Algorithmic bytes of one launch (each array the step must read or write,
+    once, in the storage precision the iteration uses)."""
+    sz = {"64": 8, "32": 4, "16": 2}
+    zb, rb = sz[phase[2:4]], sz[phase[7:9]]
+    if kernel == "precond_rho":
+        return n * (rb + 2 * zb)
+    if kernel == "search_dir":
+        return n * 3 * zb
+    if kernel == "spmv_gamma":
+        return nnz * (rb + idx_bytes) + n * (zb + rb) + nslices * 12
+    if kernel == "update_norm":
+        return n * (16 + zb + 3 * rb)
+    raise KeyError(kernel)
+
+
+def cpu_oracle_sample(a, b, gpu_iters: int, budget_iters: int = 12):
+    """Times the oracle's AMP-PCG (software-rounded) on the host for a bounded
+    number of iterations and scales to the GPU's iteration count."""
+    import oracle
+    pol = oracle.Policy(u0=oracle.FP16, criterion=oracle.LINEAR, verify_refresh=3)
+    t0 = time.perf_counter()
+    oracle.ampcg(a.rowptr, a.col, a.val, b, tol=TOL, maxit=2, policy=pol)
+    t1 = time.perf_counter()
+    oracle.ampcg(a.rowptr, a.col, a.val, b, tol=TOL, maxit=2 + budget_iters, policy=pol)
+    t2 = time.perf_counter()
+    per_iter = ((t2 - t1) - (t1 - t0)) / budget_iters
+    setup = (t1 - t0)
+    est_ms = (setup + per_iter * gpu_iters) * 1e3
+    return est_ms, {"kind": "oracle", "cores": 1, "value": est_ms, "unit": "ms",
+                    "sample": f"{budget_iters} iterations of the oracle's AMP-PCG(FP16) (software-rounded, "
+                              f"single thread) on the full system; per-iteration time x {gpu_iters} "
+                              f"iterations (the GPU's count) + setup",
+                    "per_iter_ms": per_iter * 1e3}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    a, b = workload()
+    # iteration count of the method on this workload, from the oracle itself would take
+    # minutes; the sample is scaled to the FP64-PCG-equivalent count measured by the
+    # oracle's plain PCG over a bounded run is not possible either, so use a fixed
+    # estimate recorded in the design doc when no GPU count is at hand.
+    iters = int(os.environ.get("AMPCG_REF_ITERS", "2000"))
+    steps = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        est_ms, cb = cpu_oracle_sample(a, b, iters, budget_iters=4)
+        if i >= args.warmup:
+            steps.append(est_ms)
+    v = statistics.mean(steps)
+    cb["value"] = v
+    out = {"metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f16+f32+f64 (software-rounded)", "data": "synthetic",
+           "impl": "reference", "config": config_dict(a, {"iters_assumed": iters}),
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2505_04155_b300 as P
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    a, b = workload()
+    bd = torch.as_tensor(b, device="cuda")
+    s = P.Solver(a.rowptr, a.col, a.val)
+    amp = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3)
+    f64 = P.Policy.pcg64(verify_refresh=3)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(policy, k):
+        xs, infos, ms = [], [], []
+        for _ in range(k):
+            flush.fill_(1.0)                      # evict L2 between steps
+            x = torch.zeros_like(bd)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            x, info = s.solve(bd, x, tol=TOL, maxit=MAXIT, policy=policy, history=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return ms, infos, x
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up (also builds the device-side loop graph)
+    timed(amp, args.warmup)
+    timed(f64, args.warmup)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        amp_ms, amp_info, x_amp = timed(amp, args.steps)
+        f64_ms, f64_info, x_64 = timed(f64, args.steps)
+    barrier()
+    clocks = clk.summary()
+    t_amp = statistics.mean(amp_ms)
+    t_64 = statistics.mean(f64_ms)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_amp, t_64], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_amp, t_64 = tt.tolist()
+    ia, i64 = amp_info[-1], f64_info[-1]
+
+    # per-kernel device times (same kernels, launched one by one with events)
+    _, tinfo = s.solve(bd, torch.zeros_like(bd), tol=TOL, maxit=MAXIT, policy=amp, history=False, timed=True)
+    _, tinfo64 = s.solve(bd, torch.zeros_like(bd), tol=TOL, maxit=MAXIT, policy=f64, history=False, timed=True)
+    peak, peak_kind = peaks()
+    nslices = (a.n + 31) // 32
+    idx_bytes = 2  # int16 column offsets (7-point offsets fit)
+    kernels = {}
+    for tag, ti in (("amp", tinfo), ("fp64", tinfo64)):
+        for (kn, ph), ms in ti.kernel_ms.items():
+            L = ti.kernel_launches[(kn, ph)]
+            us = ms / L * 1e3
+            by = alg_bytes(kn, ph, a.n, a.nnz, nslices, idx_bytes)
+            kernels[f"{tag}:{kn}:{ph}"] = {"launches": L, "avg_us": round(us, 2), "alg_bytes": int(by),
+                                           "gbs": round(by / (us * 1e-6) / 1e9, 1),
+                                           "frac": round(by / (us * 1e-6) / 1e9 / peak, 3),
+                                           "share": round(ms / ti.kernel_total_ms, 3)}
+    # dominant kernel of the AMP solve
+    dom = max(((k, v) for k, v in kernels.items() if k.startswith("amp:")),
+              key=lambda kv: kv[1]["avg_us"] * kv[1]["launches"])
+    dk, dv = dom
+    achieved = dv["gbs"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 3), "traffic": None, "kernel": dk,
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+
+    # end to end through the C ABI with pinned host buffers
+    bh = torch.as_tensor(b).pin_memory()
+    xh = torch.zeros(a.n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        xh.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, einfo = s.solve(bh, xh, tol=TOL, maxit=MAXIT, policy=amp, history=False)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e = {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": int(16 * a.n),
+           "d2h_bytes_per_step": int(8 * a.n), "note": "wall clock around ampcg_solve with pinned host b, x"}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            _, cpu = cpu_oracle_sample(a, b, ia.iters)
+        launches = int(sum(i.kernel_launches for i in amp_info + f64_info))
+        out = {"metric": METRIC, "value": round(t_amp, 3), "unit": "ms", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_amp, 3),
+               "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f16+f32+f64", "data": "synthetic",
+               "config": config_dict(a, {"parallelism": "replicas" if world > 1 else "single"}),
+               "fp64_pcg_ms": round(t_64, 3), "speedup_vs_fp64_pcg": round(t_64 / t_amp, 3),
+               "iters_amp": ia.iters, "iters_fp64": i64.iters, "refreshes_amp": ia.refreshes,
+               "true_relres_amp": ia.true_relres, "true_relres_fp64": i64.true_relres,
+               "switch_iter_amp": list(ia.switch_iter),
+               "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+               "clocks": clocks, "gpu_launches": launches,
+               "gpu_launches_note": "library kernels in the timed region (AMP and FP64 solves), counted by the library"}
+        print(json.dumps(out), flush=True)
+    s.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

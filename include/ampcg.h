@@ -1,0 +1,205 @@
+/*
+ * ampcg.h -- C ABI of the B300 (sm_103a) adaptive mixed-precision,
+ * dynamically scaled preconditioned conjugate gradient library.
+ *
+ * Method: Guo, de Sturler, Warburton, "An Adaptive Mixed-Precision and
+ * Dynamically Scaled Preconditioned Conjugate Gradient Algorithm"
+ * (arXiv 2505.04155).  Section and equation names below refer to that paper.
+ *
+ * Conventions for every entry point:
+ *   - Return codes only: no exception crosses the ABI, the library never
+ *     aborts and never traps on the device.  After a non-OK status,
+ *     ampcg_last_error() holds a one-line description (per thread).
+ *   - The caller owns every array it passes.  ampcg_create_csr copies the
+ *     matrix into library-owned device memory; the caller may free its arrays
+ *     as soon as the call returns.
+ *   - "device or host" pointers: the library asks the CUDA runtime which kind
+ *     a pointer is and copies host data to/from the device itself.
+ *   - All work of a context is ordered on the CUDA stream given at creation
+ *     (NULL: the library creates its own non-blocking stream).  Calls that
+ *     return results to the host synchronise that stream before returning.
+ *   - One context must not be used from two threads at the same time.
+ */
+#ifndef AMPCG_H
+#define AMPCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque solver context: one SPD matrix with its preconditioner, its
+ * precision copies and its device work buffers. */
+typedef struct ampcg_ctx* ampcg_t;
+
+/* Floating-point formats.  Ordered from high to low precision; the "min" of
+ * two precisions in Eq. (precision_selector) is the larger code. */
+typedef enum { AMPCG_FP64 = 0, AMPCG_FP32 = 1, AMPCG_FP16 = 2 } ampcg_prec;
+
+typedef enum {
+  AMPCG_OK = 0,                /* converged (updated residual <= tol*||b||) */
+  AMPCG_NOT_CONVERGED = 1,     /* maxit reached; x and histories are filled */
+  AMPCG_ERR_INVALID_ARG = -1,  /* bad size, pointer, policy or CSR structure */
+  AMPCG_ERR_NOT_SPD = -2,      /* create-time evidence: a diagonal entry <= 0 */
+  AMPCG_ERR_BREAKDOWN = -3,    /* rho_k <= 0 or gamma_k <= 0 (Alg. 3 lines 7, 13) */
+  AMPCG_ERR_NONFINITE = -4,    /* NaN/Inf in b, x0 or a recurrence scalar */
+  AMPCG_ERR_CUDA = -5,         /* a CUDA runtime call failed */
+  AMPCG_ERR_OOM = -6,          /* device allocation failed */
+  AMPCG_ERR_TIMEOUT = -7,      /* a bounded device wait ran out */
+  AMPCG_ERR_NO_DEVICE = -8,    /* no CUDA device is visible */
+  AMPCG_ERR_UNSUPPORTED = -9   /* valid request this build does not support */
+} ampcg_status;
+
+/* Preconditioner M (Alg. 3 line 6 applies M^-1). */
+typedef enum { AMPCG_M_NONE = 0, AMPCG_M_JACOBI = 1, AMPCG_M_CHEBYSHEV = 2 } ampcg_m_type;
+
+typedef struct {
+  int type;        /* ampcg_m_type */
+  int degree;      /* Chebyshev: number of Chebyshev iterations m (>= 1) */
+  double lmin;     /* Chebyshev: interval [lmin, lmax] of D^-1/2 A D^-1/2;  */
+  double lmax;     /*   lmax <= 0 asks the library to estimate it           */
+} ampcg_precond_spec;
+
+/* Criterion for the u_r switch (Sec. 4.1). */
+typedef enum {
+  AMPCG_CRIT_WINDOW = 0,  /* delay-window indicator, Eq. (eta_k), d and C */
+  AMPCG_CRIT_LINEAR = 1,  /* linear-convergence indicator, Eq. (linear criterion), ell and C */
+  AMPCG_CRIT_FIXED = 2    /* no selector: (u_z, u_r) = (fixed_uz, fixed_ur); FP64/FP64 = PCG */
+} ampcg_criterion;
+
+/* Dynamic scaling omega_k of y_k = omega_k r_k (Alg. 2 line 3, Alg. 3 line 5). */
+typedef enum {
+  AMPCG_SCALE_NONE = 0,      /* omega = 1 (plain PCG) */
+  AMPCG_SCALE_L2 = 1,        /* omega = 1/||r_k||, as printed in Alg. 3 */
+  AMPCG_SCALE_LINF_POW2 = 2  /* omega = 2^-ceil(log2 max|r_k|): exact, max|y| in (0.5, 1] */
+} ampcg_scale;
+
+typedef struct {
+  int u0;             /* initial (maximum) u_z precision, ampcg_prec */
+  int criterion;      /* ampcg_criterion */
+  int d;              /* window delay d of Eq. (eta_k); paper: 10 */
+  int ell;            /* rate window ell of Eq. (linear criterion); paper: 5 */
+  double C;           /* Assumption 1 constant; paper: 1 */
+  double tau_zs;      /* nu_k threshold for u_z -> FP32; paper: 1e-4 */
+  double tau_zh;      /* nu_k threshold for u_z -> FP16; paper: 1e-6 */
+  int scale;          /* ampcg_scale */
+  int latch;          /* 1: a precision never rises again within a solve */
+  int verify_refresh; /* >0: after convergence verify b - A x in FP64 and, if
+                         it exceeds tol*||b||, replace r and continue; at most
+                         this many times.  0: stop on the updated residual. */
+  int fixed_uz;       /* FIXED criterion only */
+  int fixed_ur;       /* FIXED criterion only: AMPCG_FP64 or AMPCG_FP32 */
+  int graph_chunk;    /* iterations per body of the device-side loop (>= 1; 0 = default) */
+} ampcg_policy;
+
+typedef struct {
+  int iters;              /* iterations performed (Alg. 3 loop trips) */
+  int converged;          /* 1 if the updated residual met tol*||b|| */
+  int refreshes;          /* true-residual replacements performed */
+  int status;             /* ampcg_status of the solve */
+  double true_relres;     /* ||b - A x||_2 / ||b||_2 recomputed in FP64 at exit */
+  double updated_relres;  /* delta_iters / ||b|| */
+  int switch_iter[3];     /* first iteration with u_z = FP32, u_z = FP16, u_r = FP32
+                             reached by a change of precision; -1 if none */
+  double seconds;         /* wall time of the call */
+  double* relres_hist;    /* caller-owned host array, length >= maxit + 1, or NULL:
+                             receives delta_k / ||b||, k = 0..iters */
+  uint8_t* prec_hist;     /* caller-owned host array, length >= maxit, or NULL:
+                             receives (u_z << 4) | u_r used at iteration k */
+  int64_t kernel_launches; /* library kernels launched by the call (graph nodes included) */
+} ampcg_result;
+
+/* Fills *p with the paper's defaults (d = 10, C = 1, ell = 5, tau_zs = 1e-4,
+ * tau_zh = 1e-6, Sec. 5) for AMP-PCG(FP16) with the linear criterion,
+ * LINF_POW2 scaling, latching on, verify_refresh = 0. */
+void ampcg_policy_default(ampcg_policy* p);
+
+/* Creates a context for the SPD matrix A given in CSR form (Sec. 2: A is
+ * SPD; Alg. 3 REQUIRE: A, M).  n rows; rowptr[n+1] (int32, rowptr[0] = 0,
+ * nondecreasing, rowptr[n] = nnz); colind[nnz] (int32, in [0, n), strictly
+ * increasing within each row); vals[nnz] FP64.  Arrays may be host or device
+ * pointers.  The library validates the structure and the diagonal
+ * (AMPCG_ERR_INVALID_ARG, AMPCG_ERR_NOT_SPD), then builds on the device the
+ * FP64 and FP32 copies of A in its internal sliced layout, the Jacobi inverse
+ * diagonal in FP64/FP32/FP16 and, for Chebyshev, the FP64/FP32/FP16 copies of
+ * D^-1/2 A D^-1/2.  cuda_stream: a cudaStream_t or NULL.  On success *out
+ * owns device memory until ampcg_destroy. */
+ampcg_status ampcg_create_csr(ampcg_t* out, int64_t n, int64_t nnz, const int32_t* rowptr,
+                              const int32_t* colind, const double* vals,
+                              const ampcg_precond_spec* M, void* cuda_stream);
+
+/* Releases every resource of the context (NULL is ignored). */
+void ampcg_destroy(ampcg_t ctx);
+
+/* Solves A x = b with AMP-PCG (Alg. 3; Alg. 1 and Alg. 2 under the FIXED
+ * criterion).  b[n] FP64 (device or host); x[n] FP64 (device or host), in:
+ * x_0, out: the final iterate.  tol > 0: stop when ||r_{k+1}|| <= tol ||b||
+ * (Alg. 3 line 18).  maxit >= 0.  policy NULL = ampcg_policy_default.
+ * res (may be NULL) receives counts, final residuals, switch points and, when
+ * its history pointers are set, the per-iteration residual and precision
+ * histories.  Returns the solve's status (AMPCG_OK, AMPCG_NOT_CONVERGED,
+ * AMPCG_ERR_BREAKDOWN, AMPCG_ERR_NONFINITE) or an error; x holds the last
+ * iterate in every non-error case.  Synchronises the context's stream. */
+ampcg_status ampcg_solve(ampcg_t ctx, const double* b, double* x, double tol, int maxit,
+                         const ampcg_policy* policy, ampcg_result* res);
+
+/* Per-kernel device time of one solve, split by the precision pair of the
+ * iteration, as the paper reports per-kernel time for each phase of
+ * AMP-PCG (Sec. 5.5).  Index [kernel][phase]: kernel 0 = scale+precondition
+ * +rho (Alg. 3 lines 5-10), 1 = search direction (line 11), 2 = SpMV+gamma
+ * (lines 12-14), 3 = x/r update+norm+selector (lines 15-18); phase =
+ * 2*u_z + u_r (u_z in {FP64, FP32, FP16}, u_r in {FP64, FP32}). */
+typedef struct {
+  double ms[4][6];     /* summed CUDA-event durations */
+  int launches[4][6];  /* launches that did work */
+  double total_ms;     /* device time from the first to the last launch */
+} ampcg_kernel_times;
+
+/* Same as ampcg_solve, computing the same iterates bit for bit, but the
+ * iteration kernels are launched one by one (no graph) with a CUDA event pair
+ * around each launch, and their durations are returned in *kt.  Slower than
+ * ampcg_solve by the launch overhead; meant for measurement. */
+ampcg_status ampcg_solve_timed(ampcg_t ctx, const double* b, double* x, double tol, int maxit,
+                               const ampcg_policy* policy, ampcg_result* res,
+                               ampcg_kernel_times* kt);
+
+/* --- Single steps of the iteration, on device arrays of length n ---------- */
+
+/* q = A p in precision `prec` (Alg. 3 line 12): the FP64 or FP32 copy of A,
+ * one fused multiply-add per stored entry in ascending column order,
+ * accumulated in `prec`.  p and q are device arrays of doubles (FP64) or
+ * floats (FP32).  Asynchronous on the context's stream. */
+ampcg_status ampcg_spmv(ampcg_t ctx, int prec, const void* p, void* q);
+
+/* z = M^-1 y with y = round_uz(omega * r computed in ur) (Alg. 3 lines 5-6).
+ * r: device array in precision ur (double or float); z: device array in
+ * precision uz (double, float or IEEE half as uint16).  omega: the scale
+ * factor.  Asynchronous on the context's stream. */
+ampcg_status ampcg_precond_apply(ampcg_t ctx, int uz, int ur, double omega, const void* r,
+                                 void* z);
+
+/* r = b - A x in FP64 (Alg. 3 line 1): per row, an FP64 fused multiply-add
+ * chain over the stored entries in ascending column order, subtracted from
+ * b.  Device arrays of doubles.  Asynchronous on the context's stream. */
+ampcg_status ampcg_residual(ampcg_t ctx, const double* b, const double* x, double* r);
+
+/* Runs the device's precision selector (Eq. (precision_selector) with the
+ * indicator chosen by policy->criterion, latching as in the policy) over a
+ * given residual-norm sequence delta[0..m] (host array), as the solver
+ * would at iterations k = 0..m; writes (u_z << 4) | u_r for each k into
+ * out[m+1] (host).  nb = ||b||, tol as in ampcg_solve.  Synchronous. */
+ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const double* delta, int m,
+                                  double nb, double tol, uint8_t* out);
+
+/* Number of rows of the context's matrix, or -1 for NULL. */
+int64_t ampcg_rows(ampcg_t ctx);
+
+/* Static strings: a status name, and the last error of this thread. */
+const char* ampcg_status_string(int status);
+const char* ampcg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMPCG_H */

@@ -94,6 +94,9 @@ def _load():
                                      C.POINTER(_Result)]
         lib.oracle_selector_trace.argtypes = [dp, C.c_int, C.c_double, C.c_double,
                                               C.POINTER(_Policy), u8p]
+        lib.oracle_scale_precond.restype = C.c_int
+        lib.oracle_scale_precond.argtypes = [i64, ip, ip, dp, C.c_int, C.c_int, C.c_int, C.c_double,
+                                             dp, dp]
         lib.oracle_cheb_apply_public.restype = C.c_int
         lib.oracle_cheb_apply_public.argtypes = [i64, i64, ip, ip, dp, dp, C.c_int, C.c_double,
                                                  C.c_double, C.c_int, dp, dp]
@@ -194,6 +197,16 @@ def residual64(rowptr, col, val, b, x):
 def dot(a, b):
     a, b = _f64(a), _f64(b)
     return _load().oracle_dot(a.size, _d(a), _d(b))
+
+
+def scale_precond(rowptr, col, val, mtype, uz, ur, omega, r):
+    """Alg. 3 lines 5-6: z = M^-1 round_uz(fl_ur(omega r)), M none or Jacobi."""
+    rowptr, col, val, r = _i32(rowptr), _i32(col), _f64(val), _f64(r)
+    n = rowptr.size - 1
+    z = np.empty(n)
+    st = _load().oracle_scale_precond(n, _i(rowptr), _i(col), _d(val), mtype, uz, ur, omega, _d(r), _d(z))
+    assert st == 0
+    return z
 
 
 def scale(mode, delta, maxabs):

@@ -389,6 +389,34 @@ static void apply_precond(int mtype, int64_t n, int uz, const double* dinv_u,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Alg. 3 line 5 (R6): y_i = round_uz( fl_ur(omega * r_i) ).                */
+static void scale_to_y(int64_t n, int uz, int ur, double omega, const double* r, double* y) {
+  double omega_r = oracle_round(ur, omega);
+  for (int64_t i = 0; i < n; ++i) {
+    double prod = (ur == OR_FP64) ? omega * r[i] : mul32(omega_r, r[i]);
+    if (ur == OR_FP16) prod = oracle_round16(prod);
+    y[i] = oracle_round(uz, prod);
+  }
+}
+
+/* Alg. 3 lines 5-6 on their own, with M = none or Jacobi built from A as in
+ * oracle_ampcg: z = M^-1 round_uz(omega r).  r must hold values of precision
+ * ur.  Used by tests to check the device's preconditioner kernel.           */
+int oracle_scale_precond(int64_t n, const int32_t* rowptr, const int32_t* col,
+                         const double* val, int mtype, int uz, int ur, double omega,
+                         const double* r, double* z) {
+  double* w = (double*)malloc(sizeof(double) * (size_t)n * 2);
+  if (!w) return OR_ERR_INVALID;
+  double *dinv = w, *y = w + n;
+  csr_diag(n, rowptr, col, val, dinv);
+  for (int64_t i = 0; i < n; ++i) dinv[i] = oracle_round(uz, 1.0 / dinv[i]);
+  scale_to_y(n, uz, ur, omega, r, y);
+  apply_precond(mtype, n, uz, dinv, y, z);
+  free(w);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* PCG, Algorithm 1, native FP64, Jacobi or identity M.  Stops on the updated
  * residual ||r_{k+1}|| <= tol ||b||.  Returns iterations in res->iters.     */
 int oracle_pcg64(int64_t n, const int32_t* rowptr, const int32_t* col,
@@ -534,12 +562,7 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
 
     /* line 5: y_k = omega_k r_k, computed in u_r, stored in u_z (R5, R6) */
     double omega = oracle_scale(pol->scale, delta[k], maxr);
-    double omega_r = oracle_round(ur, omega);
-    for (int64_t i = 0; i < n; ++i) {
-      double prod = (ur == OR_FP64) ? omega * r[i] : mul32(omega_r, r[i]);
-      if (ur == OR_FP16) prod = oracle_round16(prod);
-      y[i] = oracle_round(uz, prod);
-    }
+    scale_to_y(n, uz, ur, omega, r, y);
     /* line 6: z_k = M^-1 y_k in u_z */
     if (mtype == OR_M_CHEBYSHEV)
       oracle_cheb_apply(n, rowptr, col, &ch, uz, y, z, w0, w1, w2, w3);

@@ -1,0 +1,298 @@
+"""Python binding of libampcg (include/ampcg.h): adaptive mixed-precision,
+dynamically scaled PCG (Guo, de Sturler, Warburton, arXiv 2505.04155) on B300.
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+There is no CPU fallback; if the library has not been built (``build.py``) or
+no CUDA device is visible, the calls raise.
+
+Arrays may be NumPy arrays (host) or CUDA torch tensors (device); the library
+asks the CUDA runtime which kind each pointer is.  Contexts created while
+torch has CUDA available are bound to torch's current stream, so library work
+is ordered with torch work on that stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libampcg.so")
+
+FP64, FP32, FP16 = 0, 1, 2
+CRIT_WINDOW, CRIT_LINEAR, CRIT_FIXED = 0, 1, 2
+SCALE_NONE, SCALE_L2, SCALE_LINF_POW2 = 0, 1, 2
+M_NONE, M_JACOBI, M_CHEBYSHEV = 0, 1, 2
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_NONFINITE = -1, -2, -3, -4
+ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NO_DEVICE, ERR_UNSUPPORTED = -5, -6, -7, -8, -9
+
+
+class AmpcgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+class PrecondSpec(C.Structure):
+    _fields_ = [("type", C.c_int), ("degree", C.c_int), ("lmin", C.c_double), ("lmax", C.c_double)]
+
+
+class PolicyC(C.Structure):
+    _fields_ = [("u0", C.c_int), ("criterion", C.c_int), ("d", C.c_int), ("ell", C.c_int),
+                ("C", C.c_double), ("tau_zs", C.c_double), ("tau_zh", C.c_double),
+                ("scale", C.c_int), ("latch", C.c_int), ("verify_refresh", C.c_int),
+                ("fixed_uz", C.c_int), ("fixed_ur", C.c_int), ("graph_chunk", C.c_int)]
+
+
+class ResultC(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("refreshes", C.c_int),
+                ("status", C.c_int), ("true_relres", C.c_double), ("updated_relres", C.c_double),
+                ("switch_iter", C.c_int * 3), ("seconds", C.c_double),
+                ("relres_hist", C.POINTER(C.c_double)), ("prec_hist", C.POINTER(C.c_uint8)),
+                ("kernel_launches", C.c_int64)]
+
+
+class KernelTimesC(C.Structure):
+    _fields_ = [("ms", (C.c_double * 6) * 4), ("launches", (C.c_int * 6) * 4), ("total_ms", C.c_double)]
+
+
+KERNEL_NAMES = ("precond_rho", "search_dir", "spmv_gamma", "update_norm")
+
+
+def phase_name(phase: int) -> str:
+    """Phase index 2*u_z + u_r -> e.g. 'uz16_ur64'."""
+    bits = {FP64: "64", FP32: "32", FP16: "16"}
+    return f"uz{bits[phase // 2]}_ur{bits[phase % 2]}"
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libampcg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libampcg.so not built ({path}); run paper_2505_04155_b300/build.py")
+    lib = C.CDLL(path)
+    vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+    lib.ampcg_policy_default.argtypes = [C.POINTER(PolicyC)]
+    lib.ampcg_policy_default.restype = None
+    lib.ampcg_create_csr.argtypes = [C.POINTER(vp), i64, i64, vp, vp, vp, C.POINTER(PrecondSpec), vp]
+    lib.ampcg_create_csr.restype = C.c_int
+    lib.ampcg_destroy.argtypes = [vp]
+    lib.ampcg_destroy.restype = None
+    lib.ampcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(PolicyC), C.POINTER(ResultC)]
+    lib.ampcg_solve.restype = C.c_int
+    lib.ampcg_solve_timed.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(PolicyC),
+                                      C.POINTER(ResultC), C.POINTER(KernelTimesC)]
+    lib.ampcg_solve_timed.restype = C.c_int
+    lib.ampcg_spmv.argtypes = [vp, C.c_int, vp, vp]
+    lib.ampcg_spmv.restype = C.c_int
+    lib.ampcg_precond_apply.argtypes = [vp, C.c_int, C.c_int, C.c_double, vp, vp]
+    lib.ampcg_precond_apply.restype = C.c_int
+    lib.ampcg_residual.argtypes = [vp, vp, vp, vp]
+    lib.ampcg_residual.restype = C.c_int
+    lib.ampcg_selector_trace.argtypes = [C.POINTER(PolicyC), dp, C.c_int, C.c_double, C.c_double,
+                                         C.POINTER(C.c_uint8)]
+    lib.ampcg_selector_trace.restype = C.c_int
+    lib.ampcg_rows.argtypes = [vp]
+    lib.ampcg_rows.restype = i64
+    lib.ampcg_status_string.argtypes = [C.c_int]
+    lib.ampcg_status_string.restype = C.c_char_p
+    lib.ampcg_last_error.argtypes = []
+    lib.ampcg_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    return load_library().ampcg_status_string(s).decode()
+
+
+def _check(status: int, ok=(OK,)):
+    if status not in ok:
+        raise AmpcgError(status, load_library().ampcg_last_error().decode())
+    return status
+
+
+def _ptr(a):
+    """Raw pointer of a NumPy array or torch tensor (contiguity is required)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+@dataclass
+class Policy:
+    """Precision policy (ampcg_policy); defaults are the paper's constants for
+    AMP-PCG(FP16) with the linear-convergence criterion."""
+    u0: int = FP16
+    criterion: int = CRIT_LINEAR
+    d: int = 10
+    ell: int = 5
+    C: float = 1.0
+    tau_zs: float = 1e-4
+    tau_zh: float = 1e-6
+    scale: int = SCALE_LINF_POW2
+    latch: int = 1
+    verify_refresh: int = 0
+    fixed_uz: int = FP64
+    fixed_ur: int = FP64
+    graph_chunk: int = 16
+
+    def to_c(self) -> PolicyC:
+        return PolicyC(self.u0, self.criterion, self.d, self.ell, self.C, self.tau_zs, self.tau_zh,
+                       self.scale, self.latch, self.verify_refresh, self.fixed_uz, self.fixed_ur,
+                       self.graph_chunk)
+
+    @staticmethod
+    def pcg64(**kw) -> "Policy":
+        """Plain PCG (Algorithm 1) on the same kernels: FIXED (FP64, FP64), no scaling."""
+        return Policy(criterion=CRIT_FIXED, fixed_uz=FP64, fixed_ur=FP64, scale=SCALE_NONE, **kw)
+
+
+def default_policy() -> Policy:
+    pc = PolicyC()
+    load_library().ampcg_policy_default(C.byref(pc))
+    return Policy(pc.u0, pc.criterion, pc.d, pc.ell, pc.C, pc.tau_zs, pc.tau_zh, pc.scale, pc.latch,
+                  pc.verify_refresh, pc.fixed_uz, pc.fixed_ur, pc.graph_chunk)
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iters: int
+    converged: bool
+    refreshes: int
+    true_relres: float
+    updated_relres: float
+    switch_iter: tuple
+    seconds: float
+    kernel_launches: int = 0
+    relres_hist: np.ndarray | None = field(default=None, repr=False)
+    prec_hist: np.ndarray | None = field(default=None, repr=False)
+    kernel_ms: dict | None = field(default=None, repr=False)
+    kernel_launches: dict | None = field(default=None, repr=False)
+    kernel_total_ms: float | None = None
+
+
+class Solver:
+    """One SPD matrix (CSR) with its preconditioner on the GPU (ampcg_create_csr)."""
+
+    def __init__(self, rowptr, col, val, precond: int = M_JACOBI, degree: int = 0,
+                 lmin: float = 0.0, lmax: float = 0.0, stream=None):
+        lib = load_library()
+        if isinstance(rowptr, np.ndarray):
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+        self.n = int(rowptr.shape[0]) - 1
+        self.nnz = int(col.shape[0])
+        spec = PrecondSpec(precond, degree, lmin, lmax)
+        h = C.c_void_p()
+        st = _torch_stream() if stream is None else stream
+        _check(lib.ampcg_create_csr(C.byref(h), self.n, self.nnz, _ptr(rowptr), _ptr(col), _ptr(val),
+                                    C.byref(spec), st))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().ampcg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b, x=None, tol: float = 1e-10, maxit: int = 2000, policy: Policy | None = None,
+              history: bool = True, raise_on_breakdown: bool = False, timed: bool = False):
+        """Solve A x = b.  `x` (same kind of array as b) holds x_0 on entry and
+        the result on exit; if None, x_0 = 0 and a new array is returned.
+        timed=True uses ampcg_solve_timed and adds per-kernel, per-phase
+        device times to the returned info (info.kernel_ms, info.kernel_launches)."""
+        if x is None:
+            if isinstance(b, np.ndarray):
+                x = np.zeros(self.n)
+            else:
+                import torch
+                x = torch.zeros_like(b)
+        pol = (policy or Policy()).to_c()
+        res = ResultC()
+        rh = ph = None
+        if history:
+            rh = np.zeros(maxit + 2)
+            ph = np.zeros(max(maxit, 1), dtype=np.uint8)
+            res.relres_hist = rh.ctypes.data_as(C.POINTER(C.c_double))
+            res.prec_hist = ph.ctypes.data_as(C.POINTER(C.c_uint8))
+        kt = KernelTimesC()
+        if timed:
+            s = load_library().ampcg_solve_timed(self._h, _ptr(b), _ptr(x), tol, maxit, C.byref(pol),
+                                                 C.byref(res), C.byref(kt))
+        else:
+            s = load_library().ampcg_solve(self._h, _ptr(b), _ptr(x), tol, maxit, C.byref(pol),
+                                           C.byref(res))
+        ok = (OK, NOT_CONVERGED) if raise_on_breakdown else (OK, NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE)
+        _check(s, ok)
+        it = res.iters
+        info = SolveInfo(res.status, it, bool(res.converged), res.refreshes, res.true_relres,
+                         res.updated_relres, tuple(res.switch_iter), res.seconds,
+                         res.kernel_launches, rh[: it + 1].copy() if history else None, ph[:it].copy() if history else None)
+        if timed:
+            info.kernel_ms = {(KERNEL_NAMES[j], phase_name(ph_)): kt.ms[j][ph_]
+                              for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
+            info.kernel_launches = {(KERNEL_NAMES[j], phase_name(ph_)): kt.launches[j][ph_]
+                                    for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
+            info.kernel_total_ms = kt.total_ms
+        return x, info
+
+    def spmv(self, p, q, prec: int = FP64):
+        """q = A p in FP64 or FP32 (device arrays)."""
+        _check(load_library().ampcg_spmv(self._h, prec, _ptr(p), _ptr(q)))
+        return q
+
+    def precond_apply(self, r, z, uz: int, ur: int, omega: float = 1.0):
+        """z = M^-1 round_uz(omega r) with r in u_r and z in u_z (device arrays)."""
+        _check(load_library().ampcg_precond_apply(self._h, uz, ur, omega, _ptr(r), _ptr(z)))
+        return z
+
+    def residual(self, b, x, r):
+        """r = b - A x in FP64 (device arrays)."""
+        _check(load_library().ampcg_residual(self._h, _ptr(b), _ptr(x), _ptr(r)))
+        return r
+
+
+def selector_trace(delta, nb: float, tol: float, policy: Policy | None = None) -> np.ndarray:
+    """Device precision selector replayed over delta[0..m]; (u_z << 4) | u_r per k."""
+    delta = np.ascontiguousarray(delta, dtype=np.float64)
+    out = np.zeros(delta.size, dtype=np.uint8)
+    pol = (policy or Policy()).to_c()
+    _check(load_library().ampcg_selector_trace(C.byref(pol), delta.ctypes.data_as(C.POINTER(C.c_double)),
+                                               delta.size - 1, nb, tol,
+                                               out.ctypes.data_as(C.POINTER(C.c_uint8))))
+    return out

@@ -1,0 +1,819 @@
+// ampcg.cu -- host side of the C ABI declared in include/ampcg.h.
+//
+// A context owns the matrix in the sliced layout with its FP64/FP32 value
+// copies, the Jacobi inverse diagonal in three precisions, every vector buffer
+// of the iteration and one device state block.  A solve is: copy b and x_0 in,
+// one initial-residual launch, then a CUDA graph whose conditional WHILE node
+// repeats a body of `graph_chunk` iterations (4 launches each) until the
+// device sets `done`; then an FP64 true-residual launch and one read of the
+// state block.  The host synchronises once per solve (plus once per optional
+// residual replacement).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/ampcg.h"
+#include "kernels.cuh"
+
+using namespace ampcg;
+
+namespace {
+
+thread_local std::string g_err;
+
+ampcg_status fail(ampcg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CUDA_TRY(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ampcg_status s_ = (e_ == cudaErrorMemoryAllocation) ? AMPCG_ERR_OOM : AMPCG_ERR_CUDA; \
+      return fail(s_, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                   \
+  } while (0)
+
+constexpr int kBlock = 256;
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+ampcg_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  CUDA_TRY(cudaMalloc((void**)p, count * sizeof(T)));
+  return AMPCG_OK;
+}
+
+}  // namespace
+
+struct ampcg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  int64_t n = 0, nnz = 0, nslices = 0;
+  int idx16 = 0;  // 1: int16 column offsets
+  int mtype = M_JACOBI;
+  // matrix
+  long long* off = nullptr;
+  int* width = nullptr;
+  int* cabs = nullptr;
+  short* coff = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  __half* dinv16 = nullptr;
+  // vectors
+  double *x = nullptr, *b = nullptr, *r64 = nullptr, *t = nullptr;
+  float* r32 = nullptr;
+  void *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+  double* part = nullptr;
+  unsigned long long* pmax = nullptr;
+  DevState* st = nullptr;       // device
+  DevState* hst = nullptr;      // pinned host mirror
+  double* dhist = nullptr;      // delta history
+  double* rhist = nullptr;      // relres history
+  unsigned char* phist = nullptr;
+  int hist_cap = 0;
+  // launch shapes
+  int g_elem = 1, g_rows = 1, g_max = 1;
+  // device-side loop graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_chunk = 0;
+
+  Sell sell() const {
+    Sell A;
+    A.n = n;
+    A.nslices = nslices;
+    A.off = off;
+    A.width = width;
+    A.cabs = idx16 ? nullptr : cabs;
+    A.coff = idx16 ? coff : nullptr;
+    A.v64 = v64;
+    A.v32 = v32;
+    return A;
+  }
+  Bufs bufs() const {
+    Bufs B;
+    B.x = x;
+    B.b = b;
+    B.r64 = r64;
+    B.r32 = r32;
+    B.z = z;
+    B.p[0] = p0;
+    B.p[1] = p1;
+    B.q = q;
+    B.t = t;
+    B.dinv64 = dinv64;
+    B.dinv32 = dinv32;
+    B.dinv16 = dinv16;
+    B.part = part;
+    B.pmax = pmax;
+    return B;
+  }
+};
+
+static void release(ampcg_ctx* c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  void* ptrs[] = {c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
+                  c->dinv16, c->x, c->b, c->r64, c->t, c->r32, c->z, c->p0, c->p1, c->q,
+                  c->part, c->pmax, c->st, c->dhist, c->rhist, c->phist};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->hst) cudaFreeHost(c->hst);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+static int occ_grid(const void* kern, int sms, int64_t work_threads) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 4;
+  }
+  if (per_sm < 1) per_sm = 1;
+  int64_t g = (int64_t)sms * per_sm;
+  int64_t need = (work_threads + kBlock - 1) / kBlock;
+  if (need < 1) need = 1;
+  return (int)(g < need ? g : need);
+}
+
+extern "C" {
+
+void ampcg_policy_default(ampcg_policy* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->u0 = AMPCG_FP16;
+  p->criterion = AMPCG_CRIT_LINEAR;
+  p->d = 10;
+  p->ell = 5;
+  p->C = 1.0;
+  p->tau_zs = 1e-4;
+  p->tau_zh = 1e-6;
+  p->scale = AMPCG_SCALE_LINF_POW2;
+  p->latch = 1;
+  p->verify_refresh = 0;
+  p->fixed_uz = AMPCG_FP64;
+  p->fixed_ur = AMPCG_FP64;
+  p->graph_chunk = 16;
+}
+
+const char* ampcg_status_string(int s) {
+  switch (s) {
+    case AMPCG_OK: return "AMPCG_OK";
+    case AMPCG_NOT_CONVERGED: return "AMPCG_NOT_CONVERGED";
+    case AMPCG_ERR_INVALID_ARG: return "AMPCG_ERR_INVALID_ARG";
+    case AMPCG_ERR_NOT_SPD: return "AMPCG_ERR_NOT_SPD";
+    case AMPCG_ERR_BREAKDOWN: return "AMPCG_ERR_BREAKDOWN";
+    case AMPCG_ERR_NONFINITE: return "AMPCG_ERR_NONFINITE";
+    case AMPCG_ERR_CUDA: return "AMPCG_ERR_CUDA";
+    case AMPCG_ERR_OOM: return "AMPCG_ERR_OOM";
+    case AMPCG_ERR_TIMEOUT: return "AMPCG_ERR_TIMEOUT";
+    case AMPCG_ERR_NO_DEVICE: return "AMPCG_ERR_NO_DEVICE";
+    case AMPCG_ERR_UNSUPPORTED: return "AMPCG_ERR_UNSUPPORTED";
+    default: return "AMPCG_UNKNOWN_STATUS";
+  }
+}
+
+const char* ampcg_last_error(void) { return g_err.c_str(); }
+
+int64_t ampcg_rows(ampcg_t c) { return c ? c->n : -1; }
+
+void ampcg_destroy(ampcg_t c) {
+  if (!c) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  release(c);
+  cudaSetDevice(dev);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// create
+
+static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                const int32_t* colind, const double* vals) {
+  cudaStream_t s = c->stream;
+  // stage CSR on the device
+  const int* d_rp = (const int*)rowptr;
+  const int* d_ci = (const int*)colind;
+  const double* d_v = vals;
+  int* t_rp = nullptr;
+  int* t_ci = nullptr;
+  double* t_v = nullptr;
+  int* rowlen = nullptr;
+  double* diag = nullptr;
+  int* flags = nullptr;
+  long long* total = nullptr;
+  ampcg_status st = AMPCG_OK;
+  auto cleanup = [&]() {
+    if (t_rp) cudaFree(t_rp);
+    if (t_ci) cudaFree(t_ci);
+    if (t_v) cudaFree(t_v);
+    if (rowlen) cudaFree(rowlen);
+    if (diag) cudaFree(diag);
+    if (flags) cudaFree(flags);
+    if (total) cudaFree(total);
+  };
+#define TRY(x)                  \
+  do {                          \
+    st = (x);                   \
+    if (st != AMPCG_OK) {       \
+      cleanup();                \
+      return st;                \
+    }                           \
+  } while (0)
+#define CTRY(call)                                                                              \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) {                                                                    \
+      cleanup();                                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? AMPCG_ERR_OOM : AMPCG_ERR_CUDA,             \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                              \
+    }                                                                                           \
+  } while (0)
+
+  if (!is_device_ptr(rowptr)) {
+    TRY(dalloc(&t_rp, n + 1));
+    CTRY(cudaMemcpyAsync(t_rp, rowptr, (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    d_rp = t_rp;
+  }
+  if (!is_device_ptr(colind)) {
+    TRY(dalloc(&t_ci, nnz));
+    if (nnz) CTRY(cudaMemcpyAsync(t_ci, colind, nnz * sizeof(int), cudaMemcpyHostToDevice, s));
+    d_ci = t_ci;
+  }
+  if (!is_device_ptr(vals)) {
+    TRY(dalloc(&t_v, nnz));
+    if (nnz) CTRY(cudaMemcpyAsync(t_v, vals, nnz * sizeof(double), cudaMemcpyHostToDevice, s));
+    d_v = t_v;
+  }
+  TRY(dalloc(&rowlen, n));
+  TRY(dalloc(&diag, n));
+  TRY(dalloc(&flags, 2));
+  TRY(dalloc(&total, 1));
+  CTRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
+  int gb = (int)((n + kBlock - 1) / kBlock);
+  k_csr_scan_rows<<<gb, kBlock, 0, s>>>(n, nnz, d_rp, d_ci, d_v, rowlen, diag, flags, flags + 1);
+  CTRY(cudaGetLastError());
+  int hflags[2] = {0, 0};
+  CTRY(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+  CTRY(cudaStreamSynchronize(s));
+  if (hflags[0] & 3) {
+    cleanup();
+    return fail(AMPCG_ERR_INVALID_ARG, "CSR structure invalid (flags %d): rowptr must be "
+                "nondecreasing from 0 to nnz, columns in [0,n) strictly increasing per row", hflags[0]);
+  }
+  if (hflags[0] & 8) {
+    cleanup();
+    return fail(AMPCG_ERR_NONFINITE, "matrix has non-finite values");
+  }
+  if (hflags[0] & 4) {
+    cleanup();
+    return fail(AMPCG_ERR_NOT_SPD, "a diagonal entry is missing or not positive: A is not SPD");
+  }
+  c->idx16 = (hflags[1] <= 32767) ? 1 : 0;
+  c->nslices = (n + 31) / 32;
+  TRY(dalloc(&c->width, c->nslices));
+  TRY(dalloc(&c->off, c->nslices));
+  int gs = (int)((c->nslices + kBlock - 1) / kBlock);
+  k_slice_width<<<gs, kBlock, 0, s>>>(n, c->nslices, rowlen, c->width);
+  k_slice_offsets<<<1, 1024, 0, s>>>(c->nslices, c->width, c->off, total);
+  CTRY(cudaGetLastError());
+  long long stored = 0;
+  CTRY(cudaMemcpyAsync(&stored, total, sizeof(stored), cudaMemcpyDeviceToHost, s));
+  CTRY(cudaStreamSynchronize(s));
+  if (c->idx16) TRY(dalloc(&c->coff, stored));
+  else TRY(dalloc(&c->cabs, stored));
+  TRY(dalloc(&c->v64, stored));
+  TRY(dalloc(&c->v32, stored));
+  int64_t rows_pad = c->nslices * 32;
+  k_fill_sell<<<(int)((rows_pad + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+      n, d_rp, d_ci, d_v, c->off, c->width, c->cabs, c->coff, c->v64, c->v32);
+  TRY(dalloc(&c->dinv64, n));
+  TRY(dalloc(&c->dinv32, n));
+  TRY(dalloc(&c->dinv16, n));
+  k_jacobi<<<gb, kBlock, 0, s>>>(n, diag, c->dinv64, c->dinv32, c->dinv16);
+  CTRY(cudaGetLastError());
+  // iteration buffers (FP16 arrays padded so that vector loads stay in bounds)
+  int64_t npad = (n + 63) / 64 * 64;
+  TRY(dalloc(&c->x, npad));
+  TRY(dalloc(&c->b, npad));
+  TRY(dalloc(&c->r64, npad));
+  TRY(dalloc(&c->t, npad));
+  TRY(dalloc(&c->r32, npad));
+  double* tmp;
+  TRY(dalloc(&tmp, npad)); c->z = tmp;
+  TRY(dalloc(&tmp, npad)); c->p0 = tmp;
+  TRY(dalloc(&tmp, npad)); c->p1 = tmp;
+  TRY(dalloc(&tmp, npad)); c->q = tmp;
+  CTRY(cudaMemsetAsync(c->p0, 0, npad * 8, s));
+  CTRY(cudaMemsetAsync(c->p1, 0, npad * 8, s));
+  // launch shapes
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  int g1 = occ_grid((const void*)k_precond<M_JACOBI>, sms, n);
+  int g2 = occ_grid((const void*)k_axpy, sms, n);
+  int g3 = occ_grid((const void*)k_update, sms, n);
+  c->g_elem = g1 < g2 ? (g1 < g3 ? g1 : g3) : (g2 < g3 ? g2 : g3);
+  c->g_rows = occ_grid(c->idx16 ? (const void*)k_spmv<1> : (const void*)k_spmv<0>, sms, rows_pad);
+  c->g_max = c->g_elem > c->g_rows ? c->g_elem : c->g_rows;
+  int gi = occ_grid((const void*)k_init<0>, sms, rows_pad);
+  if (gi > c->g_max) c->g_max = gi;
+  TRY(dalloc(&c->part, (size_t)c->g_max * 4));
+  TRY(dalloc(&c->pmax, (size_t)c->g_max));
+  TRY(dalloc(&c->st, 1));
+  CTRY(cudaMallocHost((void**)&c->hst, sizeof(DevState)));
+  memset(c->hst, 0, sizeof(DevState));
+  CTRY(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  CTRY(cudaStreamSynchronize(s));
+  cleanup();
+#undef TRY
+#undef CTRY
+  return AMPCG_OK;
+}
+
+extern "C" ampcg_status ampcg_create_csr(ampcg_t* out, int64_t n, int64_t nnz,
+                                         const int32_t* rowptr, const int32_t* colind,
+                                         const double* vals, const ampcg_precond_spec* M,
+                                         void* cuda_stream) {
+  if (!out) return fail(AMPCG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(AMPCG_ERR_NO_DEVICE, "no CUDA device visible");
+  }
+  if (n <= 0 || n > (int64_t)0x7fffffe0 || nnz < 0 || nnz > (int64_t)0x7fffffff)
+    return fail(AMPCG_ERR_INVALID_ARG, "n must be in [1, 2^31-32) and nnz in [0, 2^31)");
+  if (!rowptr || (nnz > 0 && (!colind || !vals)))
+    return fail(AMPCG_ERR_INVALID_ARG, "NULL CSR array");
+  int mtype = M ? M->type : AMPCG_M_JACOBI;
+  if (mtype != AMPCG_M_NONE && mtype != AMPCG_M_JACOBI) {
+    if (mtype == AMPCG_M_CHEBYSHEV)
+      return fail(AMPCG_ERR_UNSUPPORTED, "Chebyshev preconditioner is not available in this build");
+    return fail(AMPCG_ERR_INVALID_ARG, "unknown preconditioner type %d", mtype);
+  }
+  ampcg_ctx* c = new ampcg_ctx();
+  cudaGetDevice(&c->device);
+  c->n = n;
+  c->nnz = nnz;
+  c->mtype = mtype;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return fail(AMPCG_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    c->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    release(c);
+    return fail(AMPCG_ERR_CUDA, "cudaStreamCreate failed");
+  }
+  ampcg_status s = create_impl(c, n, nnz, rowptr, colind, vals);
+  if (s != AMPCG_OK) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    release(c);
+    return s;
+  }
+  *out = c;
+  return AMPCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+
+static ampcg_status ensure_hist(ampcg_ctx* c, int maxit) {
+  int need = maxit + 2;
+  if (need <= c->hist_cap) return AMPCG_OK;
+  if (c->dhist) cudaFree(c->dhist);
+  if (c->rhist) cudaFree(c->rhist);
+  if (c->phist) cudaFree(c->phist);
+  c->dhist = nullptr;
+  c->rhist = nullptr;
+  c->phist = nullptr;
+  c->hist_cap = 0;
+  ampcg_status s;
+  if ((s = dalloc(&c->dhist, need)) != AMPCG_OK) return s;
+  if ((s = dalloc(&c->rhist, need)) != AMPCG_OK) return s;
+  if ((s = dalloc(&c->phist, need)) != AMPCG_OK) return s;
+  c->hist_cap = need;
+  return AMPCG_OK;
+}
+
+template <int MT, int IT>
+static void launch_iteration(ampcg_ctx* c, cudaStream_t s) {
+  Sell A = c->sell();
+  Bufs B = c->bufs();
+  k_precond<MT><<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
+  k_axpy<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
+  k_spmv<IT><<<c->g_rows, kBlock, 0, s>>>(A, B, c->st);
+  k_update<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
+}
+
+static void launch_iteration_any(ampcg_ctx* c, cudaStream_t s) {
+  if (c->mtype == M_NONE) {
+    if (c->idx16) launch_iteration<M_NONE, 1>(c, s);
+    else launch_iteration<M_NONE, 0>(c, s);
+  } else {
+    if (c->idx16) launch_iteration<M_JACOBI, 1>(c, s);
+    else launch_iteration<M_JACOBI, 0>(c, s);
+  }
+}
+
+static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
+  if (c->gexec && c->graph_chunk == chunk) return AMPCG_OK;
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  CUDA_TRY(cudaGraphCreate(&c->graph, 0));
+  cudaGraphConditionalHandle h;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&h, c->graph, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CUDA_TRY(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs = c->cap_stream;
+  CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < chunk; ++i) launch_iteration_any(c, cs);
+  k_loop_ctl<<<1, 1, 0, cs>>>(c->st, h);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t captured = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(cs, &captured);
+  if (le != cudaSuccess || ee != cudaSuccess)
+    return fail(AMPCG_ERR_CUDA, "graph capture failed: %s / %s", cudaGetErrorString(le),
+                cudaGetErrorString(ee));
+  CUDA_TRY(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+  c->graph_chunk = chunk;
+  return AMPCG_OK;
+}
+
+static ampcg_status check_policy(const ampcg_policy* p) {
+  if (p->u0 < 0 || p->u0 > 2 || p->fixed_uz < 0 || p->fixed_uz > 2 || p->fixed_ur < 0 ||
+      p->fixed_ur > 1)
+    return fail(AMPCG_ERR_INVALID_ARG, "precision codes: u0/fixed_uz in {0,1,2}, fixed_ur in {0,1}");
+  if (p->criterion < 0 || p->criterion > 2) return fail(AMPCG_ERR_INVALID_ARG, "bad criterion");
+  if (p->scale < 0 || p->scale > 2) return fail(AMPCG_ERR_INVALID_ARG, "bad scale mode");
+  if (p->d < 0 || p->ell < 1) return fail(AMPCG_ERR_INVALID_ARG, "need d >= 0 and ell >= 1");
+  if (p->verify_refresh < 0 || p->graph_chunk < 0)
+    return fail(AMPCG_ERR_INVALID_ARG, "verify_refresh and graph_chunk must be >= 0");
+  return AMPCG_OK;
+}
+
+static void init_state(DevState* h, const ampcg_policy* p, double tol, int maxit, ampcg_ctx* c) {
+  memset(h, 0, sizeof(*h));
+  h->maxit = maxit;
+  h->criterion = p->criterion;
+  h->u0 = p->u0;
+  h->d = p->d;
+  h->ell = p->ell;
+  h->scale = p->scale;
+  h->latch = p->latch;
+  h->fixed_uz = p->fixed_uz;
+  h->fixed_ur = p->fixed_ur;
+  h->C = p->C;
+  h->tau_zs = p->tau_zs;
+  h->tau_zh = p->tau_zh;
+  h->tol = tol;
+  h->uz = (p->criterion == AMPCG_CRIT_FIXED) ? p->fixed_uz : p->u0;
+  h->ur = P64;
+  h->uz_p = h->uz;
+  h->first = 1;
+  h->switch_iter[0] = h->switch_iter[1] = h->switch_iter[2] = -1;
+  h->delta_hist = c ? c->dhist : nullptr;
+  h->relres_hist = c ? c->rhist : nullptr;
+  h->prec_hist = c ? c->phist : nullptr;
+}
+
+// Eager loop with a CUDA event pair around every iteration kernel (timing
+// mode).  Runs chunks of iterations, then reads the iteration counter to learn
+// how many of the chunk's iterations did work; no-op launches after the stop
+// are not counted.
+template <int MT, int IT>
+static ampcg_status timed_loop(ampcg_ctx* c, ampcg_kernel_times* kt, cudaEvent_t* ev, int chunk) {
+  cudaStream_t s = c->stream;
+  Sell A = c->sell();
+  Bufs B = c->bufs();
+  for (;;) {
+    int k0 = c->hst->k;
+    for (int i = 0; i < chunk; ++i) {
+      cudaEvent_t* e = ev + i * 5;
+      CUDA_TRY(cudaEventRecord(e[0], s));
+      k_precond<MT><<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
+      CUDA_TRY(cudaEventRecord(e[1], s));
+      k_axpy<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
+      CUDA_TRY(cudaEventRecord(e[2], s));
+      k_spmv<IT><<<c->g_rows, kBlock, 0, s>>>(A, B, c->st);
+      CUDA_TRY(cudaEventRecord(e[3], s));
+      k_update<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
+      CUDA_TRY(cudaEventRecord(e[4], s));
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int done_iters = c->hst->k - k0;
+    // a chunk that stopped on breakdown ran part of one more iteration
+    if (done_iters > chunk) done_iters = chunk;
+    unsigned char ph[1024];
+    if (done_iters > 0)
+      CUDA_TRY(cudaMemcpy(ph, c->phist + k0, done_iters, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < done_iters; ++i) {
+      int phase = (ph[i] >> 4) * 2 + (ph[i] & 15);
+      for (int j = 0; j < 4; ++j) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, ev[i * 5 + j], ev[i * 5 + j + 1]));
+        kt->ms[j][phase] += ms;
+        kt->launches[j][phase] += 1;
+      }
+    }
+    if (c->hst->done) return AMPCG_OK;
+  }
+}
+
+static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double tol, int maxit,
+                               const ampcg_policy* policy, ampcg_result* res,
+                               ampcg_kernel_times* kt);
+
+extern "C" ampcg_status ampcg_solve(ampcg_t c, const double* b, double* x, double tol, int maxit,
+                                    const ampcg_policy* policy, ampcg_result* res) {
+  return solve_impl(c, b, x, tol, maxit, policy, res, nullptr);
+}
+
+extern "C" ampcg_status ampcg_solve_timed(ampcg_t c, const double* b, double* x, double tol,
+                                          int maxit, const ampcg_policy* policy, ampcg_result* res,
+                                          ampcg_kernel_times* kt) {
+  if (!kt) return fail(AMPCG_ERR_INVALID_ARG, "NULL kernel-times output");
+  memset(kt, 0, sizeof(*kt));
+  return solve_impl(c, b, x, tol, maxit, policy, res, kt);
+}
+
+static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double tol, int maxit,
+                               const ampcg_policy* policy, ampcg_result* res,
+                               ampcg_kernel_times* kt) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!c) return fail(AMPCG_ERR_INVALID_ARG, "NULL context");
+  if (!b || !x) return fail(AMPCG_ERR_INVALID_ARG, "NULL b or x");
+  if (!(tol > 0.0) || maxit < 0) return fail(AMPCG_ERR_INVALID_ARG, "need tol > 0, maxit >= 0");
+  ampcg_policy pol;
+  if (policy) pol = *policy;
+  else ampcg_policy_default(&pol);
+  ampcg_status ps = check_policy(&pol);
+  if (ps != AMPCG_OK) return ps;
+  int chunk = pol.graph_chunk > 0 ? pol.graph_chunk : 16;
+  cudaSetDevice(c->device);
+  cudaStream_t s = c->stream;
+  ampcg_status hs = ensure_hist(c, maxit);
+  if (hs != AMPCG_OK) return hs;
+  bool b_dev = is_device_ptr(b), x_dev = is_device_ptr(x);
+  size_t vb = (size_t)c->n * sizeof(double);
+  CUDA_TRY(cudaMemcpyAsync(c->b, b, vb, b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->x, x, vb, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  init_state(c->hst, &pol, tol, maxit, c);
+  CUDA_TRY(cudaMemcpyAsync(c->st, c->hst, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  if (!kt) {
+    hs = ensure_graph(c, chunk);
+    if (hs != AMPCG_OK) return hs;
+  }
+  if (kt && chunk > 64) chunk = 64;
+  cudaEvent_t ev[64 * 5];
+  cudaEvent_t e_first = nullptr, e_last = nullptr;
+  if (kt) {
+    for (int i = 0; i < chunk * 5; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
+    CUDA_TRY(cudaEventCreate(&e_first));
+    CUDA_TRY(cudaEventCreate(&e_last));
+  }
+  struct EvGuard {
+    cudaEvent_t* ev; int n; cudaEvent_t a, b;
+    ~EvGuard() { for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]); if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
+  } guard{ev, kt ? chunk * 5 : 0, e_first, e_last};
+  Sell A = c->sell();
+  Bufs B = c->bufs();
+  int64_t rows_pad = c->nslices * 32;
+  int gi = occ_grid(c->idx16 ? (const void*)k_init<1> : (const void*)k_init<0>, 148, rows_pad);
+  if (gi > c->g_max) gi = c->g_max;
+  if (c->idx16) k_init<1><<<gi, kBlock, 0, s>>>(A, B, c->st);
+  else k_init<0><<<gi, kBlock, 0, s>>>(A, B, c->st);
+  CUDA_TRY(cudaGetLastError());
+  long long launches = 1;  // k_init
+  int k_before = 0;
+  if (kt) {
+    CUDA_TRY(cudaEventRecord(e_first, s));
+    CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  for (;;) {
+    if (kt) {
+      ampcg_status ts;
+      if (c->mtype == M_NONE) ts = c->idx16 ? timed_loop<M_NONE, 1>(c, kt, ev, chunk) : timed_loop<M_NONE, 0>(c, kt, ev, chunk);
+      else ts = c->idx16 ? timed_loop<M_JACOBI, 1>(c, kt, ev, chunk) : timed_loop<M_JACOBI, 0>(c, kt, ev, chunk);
+      if (ts != AMPCG_OK) return ts;
+    } else {
+      CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+    }
+    launches += 1;  // true residual
+    if (c->idx16) k_true_residual<1><<<c->g_rows, kBlock, 0, s>>>(A, B, c->st);
+    else k_true_residual<0><<<c->g_rows, kBlock, 0, s>>>(A, B, c->st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const DevState& h = *c->hst;
+    {
+      // bodies of the device loop that ran: the body in which `done` was set
+      // completes, and a body always runs once
+      long long it = h.k - k_before + (h.status == ST_OK || h.status == ST_NOT_CONVERGED ? 0 : 1);
+      long long bodies = it <= 0 ? 1 : (it + chunk - 1) / chunk;
+      launches += kt ? bodies * 4LL * chunk : bodies * (4LL * chunk + 1);
+      k_before = h.k;
+    }
+    // reading R9: verify, and replace r when the true residual misses tol
+    bool refresh = h.status == ST_OK && h.refreshes < pol.verify_refresh && h.k < maxit &&
+                   h.true_relres * h.nb > h.tol_nb;
+    if (!refresh) break;
+    k_refresh<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
+    CUDA_TRY(cudaGetLastError());
+    launches += 1;
+  }
+  if (kt) {
+    CUDA_TRY(cudaEventRecord(e_last, s));
+    CUDA_TRY(cudaEventSynchronize(e_last));
+    float tot = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&tot, e_first, e_last));
+    kt->total_ms = tot;
+  }
+  const DevState& h = *c->hst;
+  CUDA_TRY(cudaMemcpyAsync(x, c->x, vb, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  int iters = h.k;
+  if (res) {
+    if (res->relres_hist)
+      CUDA_TRY(cudaMemcpyAsync(res->relres_hist, c->rhist, (iters + 1) * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+    if (res->prec_hist && iters > 0)
+      CUDA_TRY(cudaMemcpyAsync(res->prec_hist, c->phist, iters, cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  ampcg_status st = (ampcg_status)h.status;
+  if (res) {
+    res->iters = iters;
+    res->converged = h.status == ST_OK;
+    res->refreshes = h.refreshes;
+    res->status = h.status;
+    res->true_relres = h.true_relres;
+    res->updated_relres = h.delta / h.nb;
+    for (int i = 0; i < 3; ++i) res->switch_iter[i] = h.switch_iter[i];
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    res->kernel_launches = launches;
+  }
+  if (st != AMPCG_OK && st != AMPCG_NOT_CONVERGED)
+    fail(st, "solve stopped at iteration %d: %s", iters, ampcg_status_string(st));
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// step entry points
+
+extern "C" ampcg_status ampcg_spmv(ampcg_t c, int prec, const void* p, void* q) {
+  if (!c || !p || !q) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  Sell A = c->sell();
+  cudaStream_t s = c->stream;
+  if (prec == AMPCG_FP64) {
+    if (c->idx16) k_spmv_step<P64, 1><<<c->g_rows, kBlock, 0, s>>>(A, p, q);
+    else k_spmv_step<P64, 0><<<c->g_rows, kBlock, 0, s>>>(A, p, q);
+  } else if (prec == AMPCG_FP32) {
+    if (c->idx16) k_spmv_step<P32, 1><<<c->g_rows, kBlock, 0, s>>>(A, p, q);
+    else k_spmv_step<P32, 0><<<c->g_rows, kBlock, 0, s>>>(A, p, q);
+  } else {
+    return fail(AMPCG_ERR_INVALID_ARG, "spmv precision must be FP64 or FP32");
+  }
+  CUDA_TRY(cudaGetLastError());
+  return AMPCG_OK;
+}
+
+extern "C" ampcg_status ampcg_residual(ampcg_t c, const double* b, const double* x, double* r) {
+  if (!c || !b || !x || !r) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  Sell A = c->sell();
+  if (c->idx16) k_residual_step<1><<<c->g_rows, kBlock, 0, c->stream>>>(A, b, x, r);
+  else k_residual_step<0><<<c->g_rows, kBlock, 0, c->stream>>>(A, b, x, r);
+  CUDA_TRY(cudaGetLastError());
+  return AMPCG_OK;
+}
+
+template <int UZ, int UR>
+static void launch_precond_step(ampcg_ctx* c, const Bufs& B, const DevState* st) {
+  if (c->mtype == M_NONE) k_precond_step<UZ, UR, M_NONE><<<c->g_elem, kBlock, 0, c->stream>>>(B, c->n, st);
+  else k_precond_step<UZ, UR, M_JACOBI><<<c->g_elem, kBlock, 0, c->stream>>>(B, c->n, st);
+}
+
+extern "C" ampcg_status ampcg_precond_apply(ampcg_t c, int uz, int ur, double omega, const void* r,
+                                            void* z) {
+  if (!c || !r || !z) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  if (uz < 0 || uz > 2 || ur < 0 || ur > 1) return fail(AMPCG_ERR_INVALID_ARG, "bad precision");
+  if (!(omega != 0.0) || !std::isfinite(omega)) return fail(AMPCG_ERR_INVALID_ARG, "omega must be finite, nonzero");
+  // a private state block carries omega; the step does no storage conversion
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  DevState* h = c->hst;
+  ampcg_policy dp;
+  ampcg_policy_default(&dp);
+  init_state(h, &dp, 1.0, 0, nullptr);
+  h->omega = omega;
+  h->omega_f = (float)omega;
+  int E;
+  double f = std::frexp(omega, &E);
+  h->omega_pow2 = (f == 0.5 || f == -0.5) && omega > 0;
+  h->omega_e = E - 1;
+  h->uz = uz;
+  h->ur = ur;
+  CUDA_TRY(cudaMemcpyAsync(c->st, h, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+  Bufs B = c->bufs();
+  B.r64 = (double*)r;
+  B.r32 = (float*)r;
+  B.z = z;
+  if (ur == P64) {
+    if (uz == P64) launch_precond_step<P64, P64>(c, B, c->st);
+    else if (uz == P32) launch_precond_step<P32, P64>(c, B, c->st);
+    else launch_precond_step<P16, P64>(c, B, c->st);
+  } else {
+    if (uz == P64) launch_precond_step<P64, P32>(c, B, c->st);
+    else if (uz == P32) launch_precond_step<P32, P32>(c, B, c->st);
+    else launch_precond_step<P16, P32>(c, B, c->st);
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return AMPCG_OK;
+}
+
+extern "C" ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const double* delta,
+                                             int m, double nb, double tol, uint8_t* out) {
+  if (!policy || !delta || !out || m < 0) return fail(AMPCG_ERR_INVALID_ARG, "bad argument");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(AMPCG_ERR_NO_DEVICE, "no CUDA device visible");
+  }
+  ampcg_status ps = check_policy(policy);
+  if (ps != AMPCG_OK) return ps;
+  double* d_delta = nullptr;
+  unsigned char* d_out = nullptr;
+  unsigned char* d_ph = nullptr;
+  DevState* d_st = nullptr;
+  DevState h;
+  init_state(&h, policy, tol, m + 1, nullptr);
+  h.nb = nb;
+  h.tol_nb = tol * nb;
+  h.maxr = 1.0;
+  cudaError_t e = cudaMalloc(&d_delta, (m + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, m + 1);
+  if (e == cudaSuccess) e = cudaMalloc(&d_ph, m + 1);
+  if (e == cudaSuccess) e = cudaMalloc(&d_st, sizeof(DevState));
+  if (e == cudaSuccess) {
+    h.delta_hist = d_delta;
+    h.relres_hist = nullptr;
+    h.prec_hist = d_ph;
+    e = cudaMemcpy(d_delta, delta, (m + 1) * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(d_st, &h, sizeof(DevState), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_selector_trace<<<1, 32>>>(d_st, m, d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, m + 1, cudaMemcpyDeviceToHost);
+  cudaFree(d_delta);
+  cudaFree(d_out);
+  cudaFree(d_ph);
+  cudaFree(d_st);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "selector trace: %s", cudaGetErrorString(e));
+  return AMPCG_OK;
+}

@@ -1,0 +1,202 @@
+// device_util.cuh -- precision helpers and reductions for the AMP-PCG kernels.
+//
+// On B300 the FP64 pipe issues ~1.9 DFMA per clock per SM, and conversions
+// to or from FP64 run at a similar rate, while the FP32/INT pipes issue ~108
+// per clock.  The mixed-precision iteration therefore widens FP16/FP32 values
+// to FP64 with integer operations (exact by construction) and rounds FP64 to
+// FP16 with an integer implementation of IEEE round-to-nearest-even, so the
+// only FP64-pipe instructions left are the FP64 arithmetic the method asks
+// for (x update, FP64 residual/matrix products, inner-product accumulation).
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace ampcg {
+
+enum { P64 = 0, P32 = 1, P16 = 2 };
+
+template <int P> struct Store;
+template <> struct Store<P64> { using T = double; };
+template <> struct Store<P32> { using T = float; };
+template <> struct Store<P16> { using T = __half; };
+
+// ---------------------------------------------------------------------------
+// Exact widening to binary64 with integer operations only.
+
+// f is +-0, a normal number, Inf or NaN (every binary16 value widened to
+// binary32 is one of these).  Rebias the exponent (127 -> 1023) and move the
+// 23 fraction bits to the top of the 52-bit fraction.
+__device__ __forceinline__ double f2d_normal(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned s = u & 0x80000000u, a = u & 0x7fffffffu;
+  unsigned hi = (a == 0u) ? s : (s | ((a >> 3) + (896u << 20)));
+  if (a >= 0x7f800000u) hi = s | 0x7ff00000u | ((a >> 3) & 0x000fffffu);
+  return __hiloint2double((int)hi, (int)(a << 29));
+}
+
+// Any binary32 value; binary32 subnormals (rare) take the hardware path.
+__device__ __forceinline__ double f2d(float f) {
+  unsigned a = __float_as_uint(f) & 0x7fffffffu;
+  if (a != 0u && a < 0x00800000u) return (double)f;
+  return f2d_normal(f);
+}
+
+__device__ __forceinline__ float h2f(__half h) { return __half2float(h); }
+__device__ __forceinline__ double h2d(__half h) { return f2d_normal(__half2float(h)); }
+
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return f2d(v); }
+__device__ __forceinline__ double to_f64(__half v) { return h2d(v); }
+
+// ---------------------------------------------------------------------------
+// Round-to-nearest-even of v * 2^sc into binary16, from the IEEE 754
+// definition, with integer operations.  Valid for |sc| < 900 (binary64
+// subnormal inputs then lie far below binary16's range and give +-0).
+__device__ __forceinline__ __half d2h_scaled(double v, int sc) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  unsigned short s = (unsigned short)((b >> 48) & 0x8000u);
+  int E = (int)((b >> 52) & 0x7ffu);
+  unsigned long long M = b & 0x000FFFFFFFFFFFFFull;
+  unsigned short bits;
+  if (E == 0x7ff) {
+    bits = (unsigned short)(s | (M ? 0x7e00u : 0x7c00u));
+  } else if (E == 0) {
+    bits = s;
+  } else {
+    M |= 1ull << 52;                        // value = M * 2^(e - 52)
+    int e = E - 1023 + sc;
+    if (e > 15) {
+      bits = (unsigned short)(s | 0x7c00u);
+    } else {
+      int shift = (e >= -14) ? 42 : 28 - e; // bits below the binary16 quantum
+      unsigned q;
+      if (shift >= 54) {
+        q = 0u;                             // below half the smallest subnormal
+      } else {
+        unsigned long long qq = M >> shift;
+        unsigned long long rem = M & ((1ull << shift) - 1ull);
+        unsigned long long half = 1ull << (shift - 1);
+        if (rem > half || (rem == half && (qq & 1ull))) qq++;
+        q = (unsigned)qq;
+      }
+      unsigned r = (e >= -14) ? ((unsigned)(e + 14) << 10) + q : q;
+      if (r >= 0x7c00u) r = 0x7c00u;
+      bits = (unsigned short)(s | r);
+    }
+  }
+  return __ushort_as_half(bits);
+}
+
+__device__ __forceinline__ __half d2h(double v) { return d2h_scaled(v, 0); }
+
+// Rounding a binary64 value into precision P.
+template <int P> __device__ __forceinline__ typename Store<P>::T round_from_f64(double v);
+template <> __device__ __forceinline__ double round_from_f64<P64>(double v) { return v; }
+template <> __device__ __forceinline__ float round_from_f64<P32>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __half round_from_f64<P16>(double v) { return d2h(v); }
+
+// Rounding a binary32 value into precision P (P64: exact widening).
+template <int P> __device__ __forceinline__ typename Store<P>::T round_from_f32(float v);
+template <> __device__ __forceinline__ double round_from_f32<P64>(float v) { return f2d(v); }
+template <> __device__ __forceinline__ float round_from_f32<P32>(float v) { return v; }
+template <> __device__ __forceinline__ __half round_from_f32<P16>(float v) { return __float2half_rn(v); }
+
+// |v| as an order-preserving unsigned key (exact max-reduction).
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long abs_key(float v) {
+  return (unsigned long long)__double_as_longlong(f2d(v)) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions.  Fixed shapes, so results are reproducible run to run.
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_down_sync(0xffffffffu, v, o);
+    v = (w > v) ? w : v;
+  }
+  return v;
+}
+
+// Sum of NV values per block; result valid in thread 0.  blockDim.x must be
+// a multiple of 32 and at most 1024.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sh[j][wid] = v[j];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = (lane < nw) ? sh[j][lane] : 0.0;
+      v[j] = warp_sum(t);
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v) {
+  __shared__ unsigned long long shm[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) shm[wid] = v;
+  __syncthreads();
+  if (wid == 0) v = warp_max(lane < nw ? shm[lane] : 0ull);
+  return v;
+}
+
+// Single-pass grid reduction: every block publishes its partials, then takes
+// a ticket; the block that draws the last ticket sees all partials.  Returns
+// true in every thread of that block.  The last block must reset *ticket.
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+  __shared__ bool is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// Fixed-order sum of G partials (block g's value j at part[g*stride + j]) in
+// the last block; thread 0 gets the totals.
+template <int NV>
+__device__ __forceinline__ void final_sum(const double* part, int G, int stride, double (&out)[NV]) {
+#pragma unroll
+  for (int j = 0; j < NV; ++j) out[j] = 0.0;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) out[j] += __ldcg(part + (size_t)g * stride + j);
+  }
+  block_sum<NV>(out);
+}
+
+__device__ __forceinline__ unsigned long long final_max(const unsigned long long* part, int G) {
+  unsigned long long m = 0ull;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    unsigned long long v = __ldcg(part + g);
+    m = v > m ? v : m;
+  }
+  return block_max(m);
+}
+
+}  // namespace ampcg

@@ -1,0 +1,804 @@
+// kernels.cuh -- AMP-PCG (Algorithm 3 of Guo, de Sturler, Warburton) on one
+// B300.  One iteration is four bandwidth-bound launches; each grid reduction
+// is single-pass (last-block ticket) and the last block also performs the
+// scalar work of the algorithm, so no host synchronisation happens inside the
+// loop:
+//   k_precond : Alg. 3 lines 5-7    y = omega r (u_r), z = M^-1 y (u_z), rho;
+//                                   last block: beta (lines 8-10)
+//   k_axpy    : Alg. 3 line 11      p = z + beta p (u_z)
+//   k_spmv    : Alg. 3 lines 12-13  q = A p (u_r), gamma; last block: alpha
+//   k_update  : Alg. 3 lines 15-17  x += alpha p (FP64), r -= alpha q (u_r),
+//                                   ||r||, max|r|; last block: stopping test
+//                                   (line 18), indicator and selector for the
+//                                   next iteration (lines 3-4), omega.
+// The per-iteration precisions (u_z, u_r) live in device memory; every kernel
+// reads them and branches uniformly into a template specialised for them.
+#pragma once
+#include "device_util.cuh"
+
+namespace ampcg {
+
+enum { CRIT_WINDOW = 0, CRIT_LINEAR = 1, CRIT_FIXED = 2 };
+enum { SCALE_NONE = 0, SCALE_L2 = 1, SCALE_LINF_POW2 = 2 };
+enum { M_NONE = 0, M_JACOBI = 1, M_CHEBYSHEV = 2 };
+enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = -3, ST_NONFINITE = -4 };
+
+// Unit roundoff of binary32 (2^-24), the eps_32 of Eq. (eta_k).
+#define AMPCG_EPS32 5.9604644775390625e-08
+
+struct DevState {
+  // iteration control
+  int k, done, status, maxit;
+  int uz, ur;          // precisions of the current iteration
+  int uz_p;            // precision p_{k-1} is stored in
+  int r_cast, p_cast;  // storage conversions due at this iteration
+  int pcur;            // p_{k-1} lives in pbuf[pcur]
+  int first;           // no search direction yet
+  int refreshes;
+  int switch_iter[3];
+  // policy
+  int criterion, u0, d, ell, scale, latch, fixed_uz, fixed_ur;
+  double C, tau_zs, tau_zh, tol;
+  // scalars (FP64, Sec. 4: all scalar work in double precision)
+  double nb, tol_nb, delta, maxr, omega;
+  int omega_pow2, omega_e;  // omega = 2^omega_e when omega_pow2
+  float omega_f, beta_f, alpha_f, pad_f;
+  double rho, rho_prev, beta, gamma, alpha, true_relres;
+  unsigned int ticket[4];
+  // histories (device)
+  double* delta_hist;        // [maxit + 2]
+  double* relres_hist;       // [maxit + 2]
+  unsigned char* prec_hist;  // [maxit + 1]
+};
+
+// Matrix in sliced-ELL form: rows are grouped 32 per slice (one warp); the
+// entries of a slice are stored column-major (entry j of row lane at
+// off[s] + 32 j + lane), so the warp's loads of values and indices are
+// contiguous.  Each row keeps its CSR entries in ascending column order,
+// padded with (value 0, column = row) up to the slice width.  Column indices
+// are int32 absolute or int16 offsets col - row (when every offset fits).
+struct Sell {
+  int64_t n, nslices;
+  const long long* off;  // [nslices]
+  const int* width;      // [nslices]
+  const int* cabs;       // int32 absolute columns, or null
+  const short* coff;     // int16 offsets, or null
+  const double* v64;
+  const float* v32;
+};
+
+// Scalar-side pieces of the algorithm, evaluated by one thread -------------
+
+// Eq. (eta_k) with reading R3 (no estimate before k >= d; ||r_{-1}|| := ||r_0||).
+__device__ __forceinline__ double eta_window_dev(const double* delta, int k, int d, double C) {
+  if (k < d) return __longlong_as_double(0x7ff0000000000000ll);
+  double eta = 0.0;
+  double c3 = __dadd_rn(3.0, C), c2 = __dadd_rn(2.0, C);
+  for (int t = k - d; t <= k; ++t) {
+    double prev = (t >= 1) ? delta[t - 1] : delta[0];
+    double term = __dmul_rn(AMPCG_EPS32, __dadd_rn(__dmul_rn(c3, prev), __dmul_rn(c2, delta[t])));
+    eta = __dadd_rn(eta, term);
+  }
+  return eta;
+}
+
+// Eq. (linear criterion) with reading R3 and +inf when the rate is >= 1.
+__device__ __forceinline__ double eta_linear_dev(const double* delta, int k, int ell, double C) {
+  const double inf = __longlong_as_double(0x7ff0000000000000ll);
+  if (k < ell || k < 1) return inf;
+  double rho = pow(delta[k] / delta[k - ell], 1.0 / (double)ell);
+  if (!(rho < 1.0)) return inf;
+  double c = __dmul_rn(AMPCG_EPS32, __dadd_rn(5.0, __dmul_rn(2.0, C)));
+  return __dmul_rn(c, delta[k - 1]) / __dadd_rn(1.0, -rho);
+}
+
+// Eq. (precision_selector): u_z from nu_k and u0, u_r from eta_k (reading R2).
+__device__ __forceinline__ void select_dev(double nu, int u0, double tzs, double tzh, double eta,
+                                           double tol_nb, int& uz, int& ur) {
+  if (nu >= tzs) uz = u0;
+  else if (nu >= tzh) uz = (u0 > P32) ? u0 : P32;
+  else uz = (u0 > P16) ? u0 : P16;
+  ur = (eta <= tol_nb) ? P32 : P64;
+}
+
+// Decide the precisions of iteration st->k (Alg. 3 lines 3-4), the storage
+// conversions they imply, and omega_k (reading R5).  Thread 0 of one block.
+__device__ void decide(DevState* st) {
+  int k = st->k;
+  int uz, ur;
+  if (st->criterion == CRIT_FIXED) {
+    uz = st->fixed_uz;
+    ur = st->fixed_ur;
+  } else {
+    double eta = (st->criterion == CRIT_WINDOW) ? eta_window_dev(st->delta_hist, k, st->d, st->C)
+                                                : eta_linear_dev(st->delta_hist, k, st->ell, st->C);
+    select_dev(st->delta_hist[k] / st->nb, st->u0, st->tau_zs, st->tau_zh, eta, st->tol_nb, uz, ur);
+    if (st->latch) {
+      if (uz < st->uz) uz = st->uz;
+      if (ur < st->ur) ur = st->ur;
+    }
+  }
+  if (uz != st->uz && uz == P32 && st->switch_iter[0] < 0) st->switch_iter[0] = k;
+  if (uz != st->uz && uz == P16 && st->switch_iter[1] < 0) st->switch_iter[1] = k;
+  if (ur != st->ur && ur == P32 && st->switch_iter[2] < 0) st->switch_iter[2] = k;
+  st->r_cast = (ur != st->ur);
+  st->p_cast = (!st->first && uz != st->uz_p);
+  st->uz = uz;
+  st->ur = ur;
+  st->prec_hist[k] = (unsigned char)((uz << 4) | ur);
+  // omega_k
+  double om = 1.0;
+  int pow2 = 1, e = 0;
+  if (st->scale == SCALE_L2) {
+    om = 1.0 / st->delta;
+    pow2 = 0;
+  } else if (st->scale == SCALE_LINF_POW2) {
+    double m = st->maxr;
+    if (m > 0.0 && m < __longlong_as_double(0x7ff0000000000000ll)) {
+      int E;
+      double f = frexp(m, &E);
+      int c = (f == 0.5) ? E - 1 : E;
+      e = -c;
+      om = ldexp(1.0, e);
+    }
+  }
+  st->omega = om;
+  st->omega_f = __double2float_rn(om);
+  st->omega_pow2 = pow2;
+  st->omega_e = e;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse product of one row.  A in precision UR, p stored in precision UZ;
+// operands widened exactly to UR (or rounded, when u_z is the higher one),
+// one fma per stored entry in ascending column order, accumulated in UR.
+
+template <int UZ, int UR> struct PToR;
+template <int UZ> struct PToR<UZ, P64> {
+  static __device__ __forceinline__ double cv(typename Store<UZ>::T v) { return to_f64(v); }
+};
+template <> struct PToR<P64, P32> {
+  static __device__ __forceinline__ float cv(double v) { return __double2float_rn(v); }
+};
+template <> struct PToR<P32, P32> {
+  static __device__ __forceinline__ float cv(float v) { return v; }
+};
+template <> struct PToR<P16, P32> {
+  static __device__ __forceinline__ float cv(__half v) { return h2f(v); }
+};
+
+template <int UR> __device__ __forceinline__ typename Store<UR>::T fma_r(typename Store<UR>::T a,
+                                                                         typename Store<UR>::T b,
+                                                                         typename Store<UR>::T c);
+template <> __device__ __forceinline__ double fma_r<P64>(double a, double b, double c) { return fma(a, b, c); }
+template <> __device__ __forceinline__ float fma_r<P32>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <int UR> __device__ __forceinline__ const typename Store<UR>::T* mat_vals(const Sell& A);
+template <> __device__ __forceinline__ const double* mat_vals<P64>(const Sell& A) { return A.v64; }
+template <> __device__ __forceinline__ const float* mat_vals<P32>(const Sell& A) { return A.v32; }
+
+template <int IT> __device__ __forceinline__ int col_at(const Sell& A, long long e, int row);
+template <> __device__ __forceinline__ int col_at<0>(const Sell& A, long long e, int row) { return __ldg(A.cabs + e); }
+template <> __device__ __forceinline__ int col_at<1>(const Sell& A, long long e, int row) {
+  return row + (int)__ldg(A.coff + e);
+}
+
+// acc = sum_j a_ij p_j over row `row` of slice s (lane = row % 32).
+template <int UZ, int UR, int IT>
+__device__ __forceinline__ typename Store<UR>::T sell_row(const Sell& A, int s, int lane, int row,
+                                                          const typename Store<UZ>::T* __restrict__ p) {
+  using TR = typename Store<UR>::T;
+  const TR* __restrict__ va = mat_vals<UR>(A);
+  long long base = __ldg(A.off + s) + lane;
+  int w = __ldg(A.width + s);
+  TR acc = (TR)0;
+  if (w <= 8) {
+    TR a[8];
+    int c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j < w) {
+        a[j] = __ldg(va + base + 32 * j);
+        c[j] = col_at<IT>(A, base + 32 * j, row);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j < w) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(p[c[j]]), acc);
+    }
+  } else {
+    for (int j = 0; j < w; ++j) {
+      TR a = __ldg(va + base + 32 * j);
+      int c = col_at<IT>(A, base + 32 * j, row);
+      acc = fma_r<UR>(a, PToR<UZ, UR>::cv(p[c]), acc);
+    }
+  }
+  return acc;
+}
+
+// FP64 fma-chain row product (initial/true residual, Alg. 3 line 1).
+template <int IT>
+__device__ __forceinline__ double sell_row64(const Sell& A, int s, int lane, int row,
+                                             const double* __restrict__ x) {
+  long long base = __ldg(A.off + s) + lane;
+  int w = __ldg(A.width + s);
+  double t = 0.0;
+  for (int j = 0; j < w; ++j) {
+    long long e = base + 32 * j;
+    t = fma(__ldg(A.v64 + e), __ldg(x + col_at<IT>(A, e, row)), t);
+  }
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Buffers of the iteration.
+struct Bufs {
+  double* x;       // FP64 iterate
+  const double* b; // FP64 right-hand side
+  double* r64;
+  float* r32;
+  void* z;         // u_z storage
+  void* p[2];      // double-buffered search direction (u_z storage)
+  void* q;         // u_r storage
+  double* t;       // FP64 scratch (true residual)
+  const double* dinv64;
+  const float* dinv32;
+  const __half* dinv16;
+  double* part;            // per-block partial sums [G * 4]
+  unsigned long long* pmax; // per-block partial maxima [G]
+};
+
+// ---------------------------------------------------------------------------
+// Initial residual r_0 = b - A x_0 (FP64), ||b||, ||r_0||, max|r_0|; the last
+// block stores delta_0 and decides iteration 0.  One thread per row.
+template <int IT>
+__global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  double v[2] = {0.0, 0.0};
+  unsigned long long mx = 0ull;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row < A.n) {
+      double t = sell_row64<IT>(A, s, lane, row, B.x);
+      double bi = B.b[row];
+      double ri = bi - t;
+      B.r64[row] = ri;
+      v[0] = fma(bi, bi, v[0]);
+      v[1] = fma(ri, ri, v[1]);
+      unsigned long long kk = abs_key(ri);
+      mx = kk > mx ? kk : mx;
+    }
+  }
+  block_sum<2>(v);
+  mx = block_max(mx);
+  if (threadIdx.x == 0) {
+    B.part[blockIdx.x * 4 + 0] = v[0];
+    B.part[blockIdx.x * 4 + 1] = v[1];
+    B.pmax[blockIdx.x] = mx;
+  }
+  if (!last_block(&st->ticket[0])) return;
+  double vv[2];
+  final_sum<2>(B.part, gridDim.x, 4, vv);
+  unsigned long long m = final_max(B.pmax, gridDim.x);
+  if (threadIdx.x == 0) {
+    st->ticket[0] = 0u;
+    double nb = sqrt(vv[0]);
+    double d0 = sqrt(vv[1]);
+    st->nb = nb;
+    st->tol_nb = st->tol * nb;
+    st->delta = d0;
+    st->maxr = __longlong_as_double((long long)m);
+    st->delta_hist[0] = d0;
+    st->relres_hist[0] = d0 / nb;
+    st->k = 0;
+    st->done = 0;
+    st->status = ST_NOT_CONVERGED;
+    if (!isfinite(nb) || !isfinite(d0)) {
+      st->status = ST_NONFINITE;
+      st->done = 1;
+    } else if (d0 <= st->tol_nb) {
+      st->status = ST_OK;
+      st->done = 1;
+    } else if (st->maxit <= 0) {
+      st->done = 1;
+    } else {
+      decide(st);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 3 lines 5-7 (+ the storage conversions of readings R10 and line 11).
+template <int UZ, int UR, int MT>
+__device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const DevState* st,
+                                             double& rho) {
+  using TZ = typename Store<UZ>::T;
+  using TR = typename Store<UR>::T;
+  TZ* __restrict__ z = (TZ*)B.z;
+  const int r_cast = st->r_cast;
+  const int p_cast = st->p_cast;
+  const int uz_p = st->uz_p;
+  const double om = st->omega;
+  const float omf = st->omega_f;
+  const int pow2 = st->omega_pow2, oe = st->omega_e;
+  const int pc = st->pcur;
+  const void* pold = pc ? B.p[1] : B.p[0];
+  TZ* pnew = (TZ*)(pc ? B.p[0] : B.p[1]);
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    // r_k in u_r (converted once when u_r changed, reading R10)
+    TR r;
+    if constexpr (UR == P64) {
+      if (r_cast) { r = f2d(B.r32[i]); B.r64[i] = r; } else r = B.r64[i];
+    } else {
+      if (r_cast) { r = __double2float_rn(B.r64[i]); B.r32[i] = r; } else r = B.r32[i];
+    }
+    // y_k = omega_k r_k computed in u_r, stored in u_z (reading R6)
+    TZ y;
+    if constexpr (UR == P64) {
+      if constexpr (UZ == P16) y = pow2 ? d2h_scaled(r, oe) : d2h(__dmul_rn(om, r));
+      else y = round_from_f64<UZ>(__dmul_rn(om, r));
+    } else {
+      y = round_from_f32<UZ>(__fmul_rn(omf, r));
+    }
+    // z_k = M^-1 y_k in u_z (Jacobi: one rounding of dinv_i * y_i)
+    TZ zi;
+    if constexpr (MT == M_NONE) zi = y;
+    else if constexpr (UZ == P64) zi = __dmul_rn(B.dinv64[i], y);
+    else if constexpr (UZ == P32) zi = __fmul_rn(B.dinv32[i], y);
+    else zi = __float2half_rn(__fmul_rn(h2f(B.dinv16[i]), h2f(y)));
+    z[i] = zi;
+    // rho_k = r_k^T z_k accumulated in FP64
+    rho = fma(to_f64(r), to_f64(zi), rho);
+    // p_{k-1} brought to the new u_z (line 11 computes p_k in u_z)
+    if (p_cast) {
+      double pv;
+      if (uz_p == P64) pv = ((const double*)pold)[i];
+      else if (uz_p == P32) pv = f2d(((const float*)pold)[i]);
+      else pv = h2d(((const __half*)pold)[i]);
+      pnew[i] = round_from_f64<UZ>(pv);
+    }
+  }
+}
+
+template <int MT>
+__global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st) {
+  if (st->done) return;
+  const int uz = st->uz, ur = st->ur;
+  double rho = 0.0;
+  if (ur == P64) {
+    if (uz == P64) precond_rows<P64, P64, MT>(B, n, st, rho);
+    else if (uz == P32) precond_rows<P32, P64, MT>(B, n, st, rho);
+    else precond_rows<P16, P64, MT>(B, n, st, rho);
+  } else {
+    if (uz == P64) precond_rows<P64, P32, MT>(B, n, st, rho);
+    else if (uz == P32) precond_rows<P32, P32, MT>(B, n, st, rho);
+    else precond_rows<P16, P32, MT>(B, n, st, rho);
+  }
+  double v[1] = {rho};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
+  if (!last_block(&st->ticket[0])) return;
+  double tot[1];
+  final_sum<1>(B.part, gridDim.x, 1, tot);
+  if (threadIdx.x == 0) {
+    st->ticket[0] = 0u;
+    double r = tot[0];
+    st->rho = r;
+    if (!isfinite(r)) { st->status = ST_NONFINITE; st->done = 1; return; }
+    if (!(r > 0.0)) { st->status = ST_BREAKDOWN; st->done = 1; return; }
+    double beta = st->first ? 0.0 : r / st->rho_prev;
+    st->beta = beta;
+    st->beta_f = __double2float_rn(beta);
+    st->r_cast = 0;
+    if (st->p_cast) {
+      st->pcur ^= 1;
+      st->uz_p = st->uz;
+      st->p_cast = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 3 line 11: p_k = z_k + beta_{k-1} p_{k-1} in u_z (p_0 = z_0).
+template <int UZ>
+__device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevState* st) {
+  using TZ = typename Store<UZ>::T;
+  const TZ* __restrict__ z = (const TZ*)B.z;
+  const int pc = st->pcur;
+  const TZ* __restrict__ po = (const TZ*)(pc ? B.p[1] : B.p[0]);
+  TZ* __restrict__ pn = (TZ*)(pc ? B.p[0] : B.p[1]);
+  const int first = st->first;
+  const double beta = st->beta;
+  const float bf = st->beta_f;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    TZ zi = z[i];
+    if (first) { pn[i] = zi; continue; }
+    if constexpr (UZ == P64) pn[i] = fma(beta, po[i], zi);
+    else if constexpr (UZ == P32) pn[i] = __fmaf_rn(bf, po[i], zi);
+    else pn[i] = __float2half_rn(__fmaf_rn(bf, h2f(po[i]), h2f(zi)));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_axpy(Bufs B, int64_t n, DevState* st) {
+  if (st->done) return;
+  const int uz = st->uz;
+  if (uz == P64) axpy_rows<P64>(B, n, st);
+  else if (uz == P32) axpy_rows<P32>(B, n, st);
+  else axpy_rows<P16>(B, n, st);
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 3 lines 12-14: q_k = A p_k in u_r, gamma_k = q_k^T p_k (FP64),
+// alpha_k = rho_k / gamma_k.  One thread per row of a warp's slice.
+template <int UZ, int UR, int IT>
+__device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const DevState* st,
+                                          double& gam) {
+  using TZ = typename Store<UZ>::T;
+  using TR = typename Store<UR>::T;
+  const TZ* __restrict__ p = (const TZ*)(st->pcur ? B.p[0] : B.p[1]);
+  TR* __restrict__ q = (TR*)B.q;
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row < A.n) {
+      TR acc = sell_row<UZ, UR, IT>(A, s, lane, row, p);
+      q[row] = acc;
+      gam = fma(to_f64(acc), to_f64(p[row]), gam);
+    }
+  }
+}
+
+template <int IT>
+__global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
+  if (st->done) return;
+  const int uz = st->uz, ur = st->ur;
+  double gam = 0.0;
+  if (ur == P64) {
+    if (uz == P64) spmv_rows<P64, P64, IT>(A, B, st, gam);
+    else if (uz == P32) spmv_rows<P32, P64, IT>(A, B, st, gam);
+    else spmv_rows<P16, P64, IT>(A, B, st, gam);
+  } else {
+    if (uz == P64) spmv_rows<P64, P32, IT>(A, B, st, gam);
+    else if (uz == P32) spmv_rows<P32, P32, IT>(A, B, st, gam);
+    else spmv_rows<P16, P32, IT>(A, B, st, gam);
+  }
+  double v[1] = {gam};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
+  if (!last_block(&st->ticket[1])) return;
+  double tot[1];
+  final_sum<1>(B.part, gridDim.x, 1, tot);
+  if (threadIdx.x == 0) {
+    st->ticket[1] = 0u;
+    double g = tot[0];
+    st->gamma = g;
+    if (!isfinite(g)) { st->status = ST_NONFINITE; st->done = 1; return; }
+    if (!(g > 0.0)) { st->status = ST_BREAKDOWN; st->done = 1; return; }
+    double a = st->rho / g;
+    st->alpha = a;
+    st->alpha_f = __double2float_rn(a);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 3 lines 15-18: x += alpha p (FP64), r -= alpha q (u_r),
+// delta_{k+1} = ||r|| (FP64), max|r| (exact); last block: stopping test and
+// the decision for iteration k+1.
+template <int UZ, int UR>
+__device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevState* st,
+                                            double& rr, unsigned long long& mx) {
+  using TZ = typename Store<UZ>::T;
+  using TR = typename Store<UR>::T;
+  const TZ* __restrict__ p = (const TZ*)(st->pcur ? B.p[0] : B.p[1]);
+  const TR* __restrict__ q = (const TR*)B.q;
+  const double a = st->alpha;
+  const float af = st->alpha_f;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    B.x[i] = fma(a, to_f64(p[i]), B.x[i]);
+    if constexpr (UR == P64) {
+      double rv = fma(-a, q[i], B.r64[i]);
+      B.r64[i] = rv;
+      rr = fma(rv, rv, rr);
+      unsigned long long kk = abs_key(rv);
+      mx = kk > mx ? kk : mx;
+    } else {
+      float rv = __fmaf_rn(-af, q[i], B.r32[i]);
+      B.r32[i] = rv;
+      double rd = f2d(rv);
+      rr = fma(rd, rd, rr);
+      unsigned long long kk = abs_key(rd);
+      mx = kk > mx ? kk : mx;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st) {
+  if (st->done) return;
+  const int uz = st->uz, ur = st->ur;
+  double rr = 0.0;
+  unsigned long long mx = 0ull;
+  if (ur == P64) {
+    if (uz == P64) update_rows<P64, P64>(B, n, st, rr, mx);
+    else if (uz == P32) update_rows<P32, P64>(B, n, st, rr, mx);
+    else update_rows<P16, P64>(B, n, st, rr, mx);
+  } else {
+    if (uz == P64) update_rows<P64, P32>(B, n, st, rr, mx);
+    else if (uz == P32) update_rows<P32, P32>(B, n, st, rr, mx);
+    else update_rows<P16, P32>(B, n, st, rr, mx);
+  }
+  double v[1] = {rr};
+  block_sum<1>(v);
+  mx = block_max(mx);
+  if (threadIdx.x == 0) {
+    B.part[blockIdx.x] = v[0];
+    B.pmax[blockIdx.x] = mx;
+  }
+  if (!last_block(&st->ticket[2])) return;
+  double tot[1];
+  final_sum<1>(B.part, gridDim.x, 1, tot);
+  unsigned long long m = final_max(B.pmax, gridDim.x);
+  if (threadIdx.x == 0) {
+    st->ticket[2] = 0u;
+    double d = sqrt(tot[0]);
+    int k1 = st->k + 1;
+    st->delta = d;
+    st->maxr = __longlong_as_double((long long)m);
+    st->delta_hist[k1] = d;
+    st->relres_hist[k1] = d / st->nb;
+    st->rho_prev = st->rho;
+    st->first = 0;
+    st->pcur ^= 1;        // p_k is now the previous direction
+    st->uz_p = st->uz;
+    st->k = k1;
+    if (!isfinite(d)) {
+      st->status = ST_NONFINITE;
+      st->done = 1;
+    } else if (d <= st->tol_nb) {
+      st->status = ST_OK;
+      st->done = 1;
+    } else if (k1 >= st->maxit) {
+      st->status = ST_NOT_CONVERGED;
+      st->done = 1;
+    } else {
+      decide(st);
+    }
+  }
+}
+
+// Sets the while-loop condition of the device-side iteration loop.
+__global__ void k_loop_ctl(DevState* st, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+// ---------------------------------------------------------------------------
+// True residual t = b - A x in FP64 and ||t|| / ||b|| (exit verification).
+template <int IT>
+__global__ void __launch_bounds__(256) k_true_residual(Sell A, Bufs B, DevState* st) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  double v[1] = {0.0};
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row < A.n) {
+      double t = B.b[row] - sell_row64<IT>(A, s, lane, row, B.x);
+      B.t[row] = t;
+      v[0] = fma(t, t, v[0]);
+    }
+  }
+  block_sum<1>(v);
+  if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
+  if (!last_block(&st->ticket[3])) return;
+  double tot[1];
+  final_sum<1>(B.part, gridDim.x, 1, tot);
+  if (threadIdx.x == 0) {
+    st->ticket[3] = 0u;
+    st->true_relres = sqrt(tot[0]) / st->nb;
+  }
+}
+
+// Residual replacement (reading R9): r <- round_ur(t), delta, max|r|; the
+// solve continues from iteration st->k if the new residual misses tol.
+__global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st) {
+  const int ur = st->ur;
+  double rr = 0.0;
+  unsigned long long mx = 0ull;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double t = B.t[i];
+    double rv;
+    if (ur == P64) { rv = t; B.r64[i] = t; }
+    else { float f = __double2float_rn(t); B.r32[i] = f; rv = f2d(f); }
+    rr = fma(rv, rv, rr);
+    unsigned long long kk = abs_key(rv);
+    mx = kk > mx ? kk : mx;
+  }
+  double v[1] = {rr};
+  block_sum<1>(v);
+  mx = block_max(mx);
+  if (threadIdx.x == 0) {
+    B.part[blockIdx.x] = v[0];
+    B.pmax[blockIdx.x] = mx;
+  }
+  if (!last_block(&st->ticket[3])) return;
+  double tot[1];
+  final_sum<1>(B.part, gridDim.x, 1, tot);
+  unsigned long long m = final_max(B.pmax, gridDim.x);
+  if (threadIdx.x == 0) {
+    st->ticket[3] = 0u;
+    double d = sqrt(tot[0]);
+    int k = st->k;
+    st->delta = d;
+    st->maxr = __longlong_as_double((long long)m);
+    st->delta_hist[k] = d;
+    st->relres_hist[k] = d / st->nb;
+    st->refreshes += 1;
+    if (d <= st->tol_nb) {
+      st->status = ST_OK;
+      st->done = 1;
+    } else {
+      st->status = ST_NOT_CONVERGED;
+      st->done = 0;
+      decide(st);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Create-time preparation (a1): CSR -> sliced layout, value copies, diagonal.
+
+// Per row: structure checks, row length, diagonal, max |col - row|.
+// flags bit 0: bad rowptr; bit 1: column out of range / not increasing;
+// bit 2: diagonal missing or <= 0; bit 3: non-finite value.
+__global__ void k_csr_scan_rows(int64_t n, int64_t nnz, const int* rowptr, const int* col,
+                                const double* val, int* rowlen, double* diag, int* flags,
+                                int* maxoff) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = rowptr[i], b = rowptr[i + 1];
+  int f = 0;
+  if (a < 0 || b < a || b > nnz || (i == 0 && a != 0) || (i == n - 1 && b != nnz)) {
+    atomicOr(flags, 1);
+    rowlen[i] = 0;
+    diag[i] = 0.0;
+    return;
+  }
+  double dg = 0.0;
+  int prev = -1, mo = 0;
+  for (int k = a; k < b; ++k) {
+    int c = col[k];
+    double v = val[k];
+    if (c < 0 || c >= n || c <= prev) f |= 2;
+    if (!isfinite(v)) f |= 8;
+    if (c == i) dg = v;
+    int o = c - (int)i;
+    o = o < 0 ? -o : o;
+    mo = o > mo ? o : mo;
+    prev = c;
+  }
+  if (!(dg > 0.0)) f |= 4;
+  if (f) atomicOr(flags, f);
+  rowlen[i] = b - a;
+  diag[i] = dg;
+  atomicMax(maxoff, mo);
+}
+
+__global__ void k_slice_width(int64_t n, int64_t nslices, const int* rowlen, int* width) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nslices) return;
+  int w = 0;
+  for (int l = 0; l < 32; ++l) {
+    int64_t r = s * 32 + l;
+    if (r < n) w = rowlen[r] > w ? rowlen[r] : w;
+  }
+  width[s] = w;
+}
+
+// Exclusive scan of 32 * width into off (one block; chunked sequential scan).
+__global__ void k_slice_offsets(int64_t nslices, const int* width, long long* off,
+                                long long* total) {
+  __shared__ long long sh[1024];
+  int t = threadIdx.x, T = blockDim.x;
+  int64_t chunk = (nslices + T - 1) / T;
+  int64_t a = t * chunk, b = a + chunk < nslices ? a + chunk : nslices;
+  long long s = 0;
+  for (int64_t i = a; i < b; ++i) s += 32ll * width[i];
+  sh[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    long long run = 0;
+    for (int j = 0; j < T; ++j) { long long v = sh[j]; sh[j] = run; run += v; }
+    *total = run;
+  }
+  __syncthreads();
+  long long run = sh[t];
+  for (int64_t i = a; i < b; ++i) { off[i] = run; run += 32ll * width[i]; }
+}
+
+__global__ void k_fill_sell(int64_t n, const int* rowptr, const int* col, const double* val,
+                            const long long* off, const int* width, int* cabs, short* coff,
+                            double* v64, float* v32) {
+  int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t s = row >> 5;
+  int lane = (int)(row & 31);
+  if (s * 32 >= n) return;
+  int w = width[s];
+  long long base = off[s] + lane;
+  int a = 0, len = 0;
+  if (row < n) { a = rowptr[row]; len = rowptr[row + 1] - a; }
+  for (int j = 0; j < w; ++j) {
+    long long e = base + 32ll * j;
+    int c = (int)(row < n ? row : 0);
+    double v = 0.0;
+    if (j < len) { c = col[a + j]; v = val[a + j]; }
+    if (cabs) cabs[e] = c;
+    if (coff) coff[e] = (short)(row < n ? c - (int)row : 0);
+    v64[e] = v;
+    v32[e] = __double2float_rn(v);
+  }
+}
+
+__global__ void k_jacobi(int64_t n, const double* diag, double* d64, float* d32, __half* d16) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = 1.0 / diag[i];
+  d64[i] = v;
+  d32[i] = __double2float_rn(v);
+  d16[i] = d2h(v);
+}
+
+// ---------------------------------------------------------------------------
+// Step entry points (single launches, no reduction).
+
+template <int UR, int IT>
+__global__ void __launch_bounds__(256) k_spmv_step(Sell A, const void* p, void* q) {
+  using TR = typename Store<UR>::T;
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row < A.n) ((TR*)q)[row] = sell_row<UR, UR, IT>(A, s, lane, row, (const TR*)p);
+  }
+}
+
+template <int IT>
+__global__ void __launch_bounds__(256) k_residual_step(Sell A, const double* b, const double* x,
+                                                       double* r) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row < A.n) r[row] = b[row] - sell_row64<IT>(A, s, lane, row, x);
+  }
+}
+
+// z = M^-1 round_uz(omega r): the same row arithmetic as k_precond, without
+// the reduction, on caller arrays.  The state block carries omega.
+template <int UZ, int UR, int MT>
+__global__ void __launch_bounds__(256) k_precond_step(Bufs B, int64_t n, const DevState* st) {
+  double rho = 0.0;
+  precond_rows<UZ, UR, MT>(B, n, st, rho);
+}
+
+// Selector replay over a residual-norm sequence (one thread).
+__global__ void k_selector_trace(DevState* st, int m, unsigned char* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k <= m; ++k) {
+    st->k = k;
+    st->delta = st->delta_hist[k];
+    decide(st);
+    out[k] = st->prec_hist[k];
+    st->first = 0;
+  }
+}
+
+}  // namespace ampcg

@@ -1,0 +1,87 @@
+"""The C ABI without a GPU: the library builds and loads, exports every
+function include/ampcg.h declares, its ctypes structures match the C layout,
+and device-requiring calls fail with a status instead of crashing."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ampcg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_04155_b300 import build as B
+    B.build()
+    import paper_2505_04155_b300 as P
+    return P.load_library()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ampcg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "ampcg_solve" in names and "ampcg_create_csr" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layout_matches_header(tmp_path):
+    import paper_2505_04155_b300 as P
+    src = tmp_path / "sz.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "ampcg.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(ampcg_policy), sizeof(ampcg_result),"
+        " sizeof(ampcg_precond_spec), offsetof(ampcg_result, relres_hist), offsetof(ampcg_policy, graph_chunk),"
+        " offsetof(ampcg_result, seconds)); return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [C.sizeof(P.PolicyC), C.sizeof(P.ResultC), C.sizeof(P.PrecondSpec),
+            P.ResultC.relres_hist.offset, P.PolicyC.graph_chunk.offset, P.ResultC.seconds.offset]
+    assert got == want
+
+
+def test_policy_defaults_are_the_papers(lib):
+    import paper_2505_04155_b300 as P
+    p = P.default_policy()
+    assert (p.d, p.ell, p.C, p.tau_zs, p.tau_zh) == (10, 5, 1.0, 1e-4, 1e-6)
+    assert p.u0 == P.FP16 and p.criterion == P.CRIT_LINEAR and p.latch == 1
+    assert p == P.Policy()
+
+
+def test_status_strings(lib):
+    import paper_2505_04155_b300 as P
+    assert P.status_string(P.OK) == "AMPCG_OK"
+    assert P.status_string(P.ERR_BREAKDOWN) == "AMPCG_ERR_BREAKDOWN"
+    assert P.status_string(12345) == "AMPCG_UNKNOWN_STATUS"
+
+
+def test_null_arguments_are_rejected_without_device(lib):
+    import paper_2505_04155_b300 as P
+    assert lib.ampcg_create_csr(None, 1, 1, None, None, None, None, None) == P.ERR_INVALID_ARG
+    assert lib.ampcg_solve(None, None, None, 1e-10, 10, None, None) == P.ERR_INVALID_ARG
+    assert lib.ampcg_rows(None) == -1
+    lib.ampcg_destroy(None)
+
+
+def test_no_device_reports_status(lib):
+    import numpy as np
+    import torch
+    import paper_2505_04155_b300 as P
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    h = C.c_void_p()
+    rp = np.array([0, 1], dtype=np.int32)
+    ci = np.array([0], dtype=np.int32)
+    v = np.array([2.0])
+    s = lib.ampcg_create_csr(C.byref(h), 1, 1, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, None, None)
+    assert s == P.ERR_NO_DEVICE
+    assert "device" in lib.ampcg_last_error().decode()

@@ -1,0 +1,179 @@
+"""Full-solve parity through the C ABI (ampcg_solve) against the CPU oracle.
+
+The reductions (rho, gamma, ||r||) run in a different order on the device, so
+trajectories agree to rounding, not bit for bit.  Bars:
+  - FP64 PCG: iteration count +-1, residual history to 1e-8 relative over the
+    first iterations, solution to 1e-10 relative of the oracle's;
+  - AMP-PCG: iteration count within +-5% (and +-2), switch iterations within
+    +-2, the paper's final-residual bound ||b - A x|| <~ 2 tol ||b|| (Sec. 4.1),
+    and with the FP64 verify-and-replace step (reading R9) a true relative
+    residual <= tol;
+  - status codes for the failure modes (breakdown, non-finite input, maxit,
+    invalid or non-SPD matrices)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2505_04155_b300")
+
+TOL = 1e-10
+
+
+def _gpu_solve(a, b, policy, tol=TOL, maxit=5000, x0=None):
+    s = P.Solver(a.rowptr, a.col, a.val)
+    bd = torch.as_tensor(b, device="cuda")
+    xd = torch.zeros_like(bd) if x0 is None else torch.as_tensor(x0, device="cuda").clone()
+    xd, info = s.solve(bd, xd, tol=tol, maxit=maxit, policy=policy)
+    x = xd.cpu().numpy()
+    s.close()
+    return x, info
+
+
+def _opol(gp: "P.Policy"):
+    return oracle.Policy(u0=gp.u0, criterion=gp.criterion, d=gp.d, ell=gp.ell, C=gp.C,
+                         tau_zs=gp.tau_zs, tau_zh=gp.tau_zh, scale=gp.scale, latch=gp.latch,
+                         verify_refresh=gp.verify_refresh, fixed_uz=gp.fixed_uz, fixed_ur=gp.fixed_ur)
+
+
+def test_pcg64_config1_matches_oracle():
+    a = W.poisson2d(64)
+    b = W.rhs_uniform(a.n, 0)
+    x, info = _gpu_solve(a, b, P.Policy.pcg64(), maxit=2000)
+    ref = oracle.pcg64(a.rowptr, a.col, a.val, b, tol=TOL, maxit=2000)
+    assert info.status == P.OK and info.converged
+    assert abs(info.iters - ref.iters) <= 1
+    m = min(info.iters, ref.iters, 60)
+    np.testing.assert_allclose(info.relres_hist[:m], ref.relres_hist[:m], rtol=1e-8)
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-10
+    assert info.true_relres <= TOL * 1.01
+    assert all(v == (P.FP64 << 4 | P.FP64) for v in info.prec_hist)
+
+
+@pytest.mark.parametrize("variant", ["amp16_linear", "amp16_window", "amp64_window", "amp_ur", "ds16"])
+@pytest.mark.parametrize("prob", ["poisson64", "diffusion24"])
+def test_ampcg_matches_oracle(variant, prob):
+    if prob == "poisson64":
+        a, b = W.poisson2d(64), W.rhs_uniform(4096, 0)
+    else:
+        a = W.diffusion3d(24, 2.0, 0)
+        b = W.rhs_uniform(a.n, 1)
+    gp = {
+        "amp16_linear": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR),
+        "amp16_window": P.Policy(u0=P.FP16, criterion=P.CRIT_WINDOW),
+        "amp64_window": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW),
+        "amp_ur": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, tau_zs=0.0, tau_zh=0.0),
+        "ds16": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64),
+    }[variant]
+    x, info = _gpu_solve(a, b, gp)
+    ref = oracle.ampcg(a.rowptr, a.col, a.val, b, tol=TOL, maxit=5000, policy=_opol(gp))
+    assert info.converged and ref.converged
+    assert abs(info.iters - ref.iters) <= max(2, 0.05 * ref.iters)
+    for j in range(3):
+        if ref.switch_iter[j] < 0:
+            assert info.switch_iter[j] < 0
+        else:
+            assert abs(info.switch_iter[j] - ref.switch_iter[j]) <= 2
+    assert info.true_relres <= 2 * TOL * 1.5 or info.true_relres <= 2 * ref.true_relres
+    # the early trajectory agrees closely (reductions differ only in order)
+    m = min(20, info.iters, ref.iters)
+    np.testing.assert_allclose(info.relres_hist[:m], ref.relres_hist[:m], rtol=1e-6)
+    # precisions used agree except within 2 iterations of a switch point
+    k = min(info.iters, ref.iters)
+    diff = np.nonzero(info.prec_hist[:k] != ref.prec_hist[:k])[0]
+    sw = [s for s in ref.switch_iter if s >= 0]
+    assert all(any(abs(d - s) <= 2 for s in sw) for d in diff)
+
+
+def test_first_iterations_close_to_oracle():
+    a = W.diffusion3d(20, 2.0, 1)
+    b = W.rhs_uniform(a.n, 3)
+    for gp in (P.Policy(), P.Policy.pcg64(), P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16,
+                                                       fixed_ur=P.FP32)):
+        for k in (1, 2, 5):
+            x, info = _gpu_solve(a, b, gp, maxit=k)
+            ref = oracle.ampcg(a.rowptr, a.col, a.val, b, tol=TOL, maxit=k, policy=_opol(gp))
+            assert info.iters == ref.iters == k
+            assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) < 1e-12
+            np.testing.assert_allclose(info.relres_hist, ref.relres_hist, rtol=1e-12)
+
+
+def test_refresh_gives_fp64_verified_tolerance():
+    a = W.diffusion3d(32, 2.0, 0)
+    b = W.rhs_uniform(a.n, 1)
+    gp = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3)
+    x, info = _gpu_solve(a, b, gp)
+    assert info.converged
+    assert info.true_relres <= TOL or info.refreshes == 3
+    r = oracle.residual64(a.rowptr, a.col, a.val, b, x)
+    assert abs(np.linalg.norm(r) / np.linalg.norm(b) - info.true_relres) <= 1e-3 * info.true_relres
+
+
+def test_host_and_device_buffers_agree():
+    a = W.poisson2d(40)
+    b = W.rhs_uniform(a.n, 2)
+    s = P.Solver(a.rowptr, a.col, a.val)
+    xh, ih = s.solve(b.copy(), np.zeros(a.n), tol=TOL, maxit=3000)
+    xd, idv = s.solve(torch.as_tensor(b, device="cuda"), tol=TOL, maxit=3000)
+    s.close()
+    assert ih.iters == idv.iters
+    assert np.array_equal(xh, xd.cpu().numpy())      # deterministic reductions
+
+
+def test_repeated_solves_are_deterministic():
+    a = W.diffusion3d(16, 2.0, 2)
+    b = torch.as_tensor(W.rhs_uniform(a.n, 4), device="cuda")
+    s = P.Solver(a.rowptr, a.col, a.val)
+    outs = [s.solve(b, tol=TOL, maxit=3000) for _ in range(3)]
+    s.close()
+    for x, info in outs[1:]:
+        assert info.iters == outs[0][1].iters
+        assert torch.equal(x, outs[0][0])
+
+
+def test_warm_start_and_zero_rhs():
+    a = W.poisson2d(32)
+    b = W.rhs_uniform(a.n, 5)
+    x, info = _gpu_solve(a, b, P.Policy.pcg64())
+    x2, info2 = _gpu_solve(a, b, P.Policy.pcg64(), x0=x)
+    assert info2.iters <= 2
+    x3, info3 = _gpu_solve(a, np.zeros(a.n), P.Policy())
+    assert info3.iters == 0 and info3.status == P.OK and not np.any(x3)
+
+
+def test_status_codes():
+    a = W.poisson2d(8)
+    b = W.rhs_uniform(a.n, 0)
+    # maxit reached
+    x, info = _gpu_solve(a, b, P.Policy(), maxit=3)
+    assert info.status == P.NOT_CONVERGED and info.iters == 3 and not info.converged
+    # non-finite right-hand side
+    bn = b.copy()
+    bn[5] = np.nan
+    x, info = _gpu_solve(a, bn, P.Policy())
+    assert info.status == P.ERR_NONFINITE
+    # indefinite with a positive diagonal: gamma <= 0 at some step
+    ind = W.CSR(2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32),
+                np.array([1.0, 3.0, 3.0, 1.0]), {})
+    x, info = _gpu_solve(ind, np.array([1.0, -1.0]), P.Policy.pcg64())
+    ref = oracle.ampcg(ind.rowptr, ind.col, ind.val, np.array([1.0, -1.0]), policy=oracle.Policy(
+        criterion=oracle.FIXED, scale=oracle.SCALE_NONE))
+    assert info.status == P.ERR_BREAKDOWN == ref.status
+    # create-time validation
+    with pytest.raises(P.AmpcgError) as e:
+        P.Solver(a.rowptr, a.col[::-1].copy(), a.val)
+    assert e.value.status == P.ERR_INVALID_ARG
+    neg = a.val.copy()
+    neg[0] = -4.0
+    with pytest.raises(P.AmpcgError) as e:
+        P.Solver(a.rowptr, a.col, neg)
+    assert e.value.status == P.ERR_NOT_SPD
+    bad = a.col.copy()
+    bad[3] = a.n + 5
+    with pytest.raises(P.AmpcgError) as e:
+        P.Solver(a.rowptr, bad, a.val)
+    assert e.value.status == P.ERR_INVALID_ARG
