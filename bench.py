@@ -241,7 +241,7 @@ def run_ours(args, rank, world):
     kernels = {}
     for tag, ti in (("amp", tinfo), ("fp64", tinfo64)):
         for (kn, ph), ms in ti.kernel_ms.items():
-            L = ti.kernel_launches[(kn, ph)]
+            L = ti.kernel_launches_by[(kn, ph)]
             us = ms / L * 1e3
             by = alg_bytes(kn, ph, a.n, a.nnz, nslices, idx_bytes)
             kernels[f"{tag}:{kn}:{ph}"] = {"launches": L, "avg_us": round(us, 2), "alg_bytes": int(by),
@@ -296,6 +296,33 @@ def run_ours(args, rank, world):
     return out
 
 
+def run_profile(args):
+    """One solve of the benchmark system for a profiler, with the iteration
+    kernels launched one by one (ampcg_solve_timed: the same kernels and
+    iterates as the graph path; profilers cannot see kernel nodes of graphs
+    with conditional nodes).  `amp` is the benchmarked AMP-PCG policy;
+    `p1`/`p2`/`fp64` pin the precision pair of Phase 1 (u_z=FP16, u_r=FP64),
+    Phase 2 (FP16, FP32) or PCG(FP64)."""
+    import torch
+    import paper_2505_04155_b300 as P
+    torch.cuda.set_device(0)
+    a, b = workload()
+    s = P.Solver(a.rowptr, a.col, a.val)
+    pol = {"amp": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3),
+           "p1": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64),
+           "p2": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32),
+           "fp64": P.Policy.pcg64()}[args.profile]
+    maxit = args.profile_iters if args.profile_iters > 0 else MAXIT
+    bd = torch.as_tensor(b, device="cuda")
+    _, info = s.solve(bd, tol=TOL, maxit=maxit, policy=pol, history=False, timed=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "iters": info.iters, "status": info.status,
+                      "true_relres": info.true_relres, "launches": info.kernel_launches,
+                      "kernel_us": {f"{k[0]}:{k[1]}": round(v / info.kernel_launches_by[k] * 1e3, 2)
+                                    for k, v in info.kernel_ms.items()}}), flush=True)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,7 +330,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--profile", choices=["amp", "p1", "p2", "fp64"], default=None,
+                    help="run one solve for a profiler and exit")
+    ap.add_argument("--profile-iters", type=int, default=0, help="maxit of the profiled solve (0: converge)")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":

@@ -196,7 +196,7 @@ class SolveInfo:
     relres_hist: np.ndarray | None = field(default=None, repr=False)
     prec_hist: np.ndarray | None = field(default=None, repr=False)
     kernel_ms: dict | None = field(default=None, repr=False)
-    kernel_launches: dict | None = field(default=None, repr=False)
+    kernel_launches_by: dict | None = field(default=None, repr=False)
     kernel_total_ms: float | None = None
 
 
@@ -235,7 +235,7 @@ class Solver:
         """Solve A x = b.  `x` (same kind of array as b) holds x_0 on entry and
         the result on exit; if None, x_0 = 0 and a new array is returned.
         timed=True uses ampcg_solve_timed and adds per-kernel, per-phase
-        device times to the returned info (info.kernel_ms, info.kernel_launches)."""
+        device times to the returned info (info.kernel_ms, info.kernel_launches_by)."""
         if x is None:
             if isinstance(b, np.ndarray):
                 x = np.zeros(self.n)
@@ -266,7 +266,7 @@ class Solver:
         if timed:
             info.kernel_ms = {(KERNEL_NAMES[j], phase_name(ph_)): kt.ms[j][ph_]
                               for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
-            info.kernel_launches = {(KERNEL_NAMES[j], phase_name(ph_)): kt.launches[j][ph_]
+            info.kernel_launches_by = {(KERNEL_NAMES[j], phase_name(ph_)): kt.launches[j][ph_]
                                     for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
             info.kernel_total_ms = kt.total_ms
         return x, info

@@ -318,13 +318,13 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   int64_t rows_pad = c->nslices * 32;
   k_fill_sell<<<(int)((rows_pad + kBlock - 1) / kBlock), kBlock, 0, s>>>(
       n, d_rp, d_ci, d_v, c->off, c->width, c->cabs, c->coff, c->v64, c->v32);
-  TRY(dalloc(&c->dinv64, n));
-  TRY(dalloc(&c->dinv32, n));
-  TRY(dalloc(&c->dinv16, n));
+  int64_t npad = (n + 63) / 64 * 64;  // per-row arrays: whole 8-element vectors in bounds
+  TRY(dalloc(&c->dinv64, npad));
+  TRY(dalloc(&c->dinv32, npad));
+  TRY(dalloc(&c->dinv16, npad));
   k_jacobi<<<gb, kBlock, 0, s>>>(n, diag, c->dinv64, c->dinv32, c->dinv16);
   CTRY(cudaGetLastError());
-  // iteration buffers (FP16 arrays padded so that vector loads stay in bounds)
-  int64_t npad = (n + 63) / 64 * 64;
+  // iteration buffers (padded like dinv)
   TRY(dalloc(&c->x, npad));
   TRY(dalloc(&c->b, npad));
   TRY(dalloc(&c->r64, npad));

@@ -101,6 +101,51 @@ template <> __device__ __forceinline__ double round_from_f32<P64>(float v) { ret
 template <> __device__ __forceinline__ float round_from_f32<P32>(float v) { return v; }
 template <> __device__ __forceinline__ __half round_from_f32<P16>(float v) { return __float2half_rn(v); }
 
+// ---------------------------------------------------------------------------
+// Vector access to V consecutive elements starting at an index that is a
+// multiple of V (16-byte transactions when V elements fill whole 16-byte
+// chunks).  Callers guarantee the V elements lie inside the allocation.
+template <int V, class T>
+__device__ __forceinline__ void vld(const T* __restrict__ p, T (&o)[V]) {
+  if constexpr (V > 1 && (V * sizeof(T)) % 16 == 0) {
+    constexpr int NQ = (int)(V * sizeof(T) / 16);
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) reinterpret_cast<uint4*>(o)[j] = reinterpret_cast<const uint4*>(p)[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) o[j] = p[j];
+  }
+}
+
+// Read-only (non-coherent path) variant for arrays the kernel does not write.
+template <int V, class T>
+__device__ __forceinline__ void vldg(const T* __restrict__ p, T (&o)[V]) {
+  if constexpr (V > 1 && (V * sizeof(T)) % 16 == 0) {
+    constexpr int NQ = (int)(V * sizeof(T) / 16);
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) reinterpret_cast<uint4*>(o)[j] = __ldg(reinterpret_cast<const uint4*>(p) + j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) o[j] = p[j];
+  }
+}
+
+// Stores the first m of V elements (all V with one vector store when m == V).
+template <int V, class T>
+__device__ __forceinline__ void vst(T* __restrict__ p, const T (&o)[V], int m) {
+  if constexpr (V > 1 && (V * sizeof(T)) % 16 == 0) {
+    if (m == V) {
+      constexpr int NQ = (int)(V * sizeof(T) / 16);
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) reinterpret_cast<uint4*>(p)[j] = reinterpret_cast<const uint4*>(o)[j];
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < V; ++j)
+    if (j < m) p[j] = o[j];
+}
+
 // |v| as an order-preserving unsigned key (exact max-reduction).
 __device__ __forceinline__ unsigned long long abs_key(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;

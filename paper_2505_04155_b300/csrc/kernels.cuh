@@ -310,57 +310,103 @@ __global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
 }
 
 // ---------------------------------------------------------------------------
+// Elementwise kernels process V consecutive elements per thread and loop trip
+// (V = 8 on the solver's buffers, which are padded to a multiple of 64
+// elements so whole vectors stay in bounds; V = 1 on caller arrays).  Only the
+// first m = min(V, n - i0) elements of a vector are used and stored.
+
 // Alg. 3 lines 5-7 (+ the storage conversions of readings R10 and line 11).
-template <int UZ, int UR, int MT>
+template <int UZ, int UR, int MT, int V>
 __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const DevState* st,
                                              double& rho) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
   TZ* __restrict__ z = (TZ*)B.z;
   const int r_cast = st->r_cast;
-  const int p_cast = st->p_cast;
-  const int uz_p = st->uz_p;
   const double om = st->omega;
   const float omf = st->omega_f;
   const int pow2 = st->omega_pow2, oe = st->omega_e;
+  const int64_t nv = (n + V - 1) / V;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+    const int64_t i0 = v * V;
+    const int m = (n - i0 < V) ? (int)(n - i0) : V;
+    // r_k in u_r (converted once when u_r changed, reading R10)
+    alignas(16) TR r[V];
+    if constexpr (UR == P64) {
+      if (r_cast) {
+        alignas(16) float t[V];
+        vld<V>(B.r32 + i0, t);
+#pragma unroll
+        for (int j = 0; j < V; ++j) r[j] = f2d(t[j]);
+        vst<V>(B.r64 + i0, r, m);
+      } else {
+        vld<V>(B.r64 + i0, r);
+      }
+    } else {
+      if (r_cast) {
+        alignas(16) double t[V];
+        vld<V>(B.r64 + i0, t);
+#pragma unroll
+        for (int j = 0; j < V; ++j) r[j] = __double2float_rn(t[j]);
+        vst<V>(B.r32 + i0, r, m);
+      } else {
+        vld<V>(B.r32 + i0, r);
+      }
+    }
+    // y_k = omega_k r_k computed in u_r, stored in u_z (reading R6), then
+    // z_k = M^-1 y_k in u_z (Jacobi: one rounding of dinv_i * y_i)
+    alignas(16) TZ zz[V];
+    alignas(16) TZ dv[V];
+    if constexpr (MT != M_NONE) {
+      if constexpr (UZ == P64) vldg<V>(B.dinv64 + i0, dv);
+      else if constexpr (UZ == P32) vldg<V>(B.dinv32 + i0, dv);
+      else vldg<V>(B.dinv16 + i0, dv);
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      TZ y;
+      if constexpr (UR == P64) {
+        if constexpr (UZ == P16) y = pow2 ? d2h_scaled(r[j], oe) : d2h(__dmul_rn(om, r[j]));
+        else y = round_from_f64<UZ>(__dmul_rn(om, r[j]));
+      } else {
+        y = round_from_f32<UZ>(__fmul_rn(omf, r[j]));
+      }
+      if constexpr (MT == M_NONE) zz[j] = y;
+      else if constexpr (UZ == P64) zz[j] = __dmul_rn(dv[j], y);
+      else if constexpr (UZ == P32) zz[j] = __fmul_rn(dv[j], y);
+      else zz[j] = __float2half_rn(__fmul_rn(h2f(dv[j]), h2f(y)));
+      // rho_k = r_k^T z_k accumulated in FP64
+      if (j < m) rho = fma(to_f64(r[j]), to_f64(zz[j]), rho);
+    }
+    vst<V>(z + i0, zz, m);
+  }
+}
+
+// p_{k-1} brought to the new u_z once, when u_z changed (line 11 computes p_k
+// in u_z); the converted copy goes to the other search-direction buffer.
+template <int UZ>
+__device__ __forceinline__ void cast_p(const Bufs& B, int64_t n, const DevState* st) {
+  using TZ = typename Store<UZ>::T;
+  const int uz_p = st->uz_p;
   const int pc = st->pcur;
   const void* pold = pc ? B.p[1] : B.p[0];
   TZ* pnew = (TZ*)(pc ? B.p[0] : B.p[1]);
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    // r_k in u_r (converted once when u_r changed, reading R10)
-    TR r;
-    if constexpr (UR == P64) {
-      if (r_cast) { r = f2d(B.r32[i]); B.r64[i] = r; } else r = B.r64[i];
-    } else {
-      if (r_cast) { r = __double2float_rn(B.r64[i]); B.r32[i] = r; } else r = B.r32[i];
-    }
-    // y_k = omega_k r_k computed in u_r, stored in u_z (reading R6)
-    TZ y;
-    if constexpr (UR == P64) {
-      if constexpr (UZ == P16) y = pow2 ? d2h_scaled(r, oe) : d2h(__dmul_rn(om, r));
-      else y = round_from_f64<UZ>(__dmul_rn(om, r));
-    } else {
-      y = round_from_f32<UZ>(__fmul_rn(omf, r));
-    }
-    // z_k = M^-1 y_k in u_z (Jacobi: one rounding of dinv_i * y_i)
-    TZ zi;
-    if constexpr (MT == M_NONE) zi = y;
-    else if constexpr (UZ == P64) zi = __dmul_rn(B.dinv64[i], y);
-    else if constexpr (UZ == P32) zi = __fmul_rn(B.dinv32[i], y);
-    else zi = __float2half_rn(__fmul_rn(h2f(B.dinv16[i]), h2f(y)));
-    z[i] = zi;
-    // rho_k = r_k^T z_k accumulated in FP64
-    rho = fma(to_f64(r), to_f64(zi), rho);
-    // p_{k-1} brought to the new u_z (line 11 computes p_k in u_z)
-    if (p_cast) {
-      double pv;
-      if (uz_p == P64) pv = ((const double*)pold)[i];
-      else if (uz_p == P32) pv = f2d(((const float*)pold)[i]);
-      else pv = h2d(((const __half*)pold)[i]);
-      pnew[i] = round_from_f64<UZ>(pv);
-    }
+    double pv;
+    if (uz_p == P64) pv = ((const double*)pold)[i];
+    else if (uz_p == P32) pv = f2d(((const float*)pold)[i]);
+    else pv = h2d(((const __half*)pold)[i]);
+    pnew[i] = round_from_f64<UZ>(pv);
   }
+}
+
+template <int UZ, int UR, int MT, int V>
+__device__ __forceinline__ void precond_and_cast(const Bufs& B, int64_t n, const DevState* st,
+                                                 double& rho) {
+  precond_rows<UZ, UR, MT, V>(B, n, st, rho);
+  if (st->p_cast) cast_p<UZ>(B, n, st);
 }
 
 template <int MT>
@@ -369,13 +415,13 @@ __global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st
   const int uz = st->uz, ur = st->ur;
   double rho = 0.0;
   if (ur == P64) {
-    if (uz == P64) precond_rows<P64, P64, MT>(B, n, st, rho);
-    else if (uz == P32) precond_rows<P32, P64, MT>(B, n, st, rho);
-    else precond_rows<P16, P64, MT>(B, n, st, rho);
+    if (uz == P64) precond_and_cast<P64, P64, MT, 8>(B, n, st, rho);
+    else if (uz == P32) precond_and_cast<P32, P64, MT, 8>(B, n, st, rho);
+    else precond_and_cast<P16, P64, MT, 8>(B, n, st, rho);
   } else {
-    if (uz == P64) precond_rows<P64, P32, MT>(B, n, st, rho);
-    else if (uz == P32) precond_rows<P32, P32, MT>(B, n, st, rho);
-    else precond_rows<P16, P32, MT>(B, n, st, rho);
+    if (uz == P64) precond_and_cast<P64, P32, MT, 8>(B, n, st, rho);
+    else if (uz == P32) precond_and_cast<P32, P32, MT, 8>(B, n, st, rho);
+    else precond_and_cast<P16, P32, MT, 8>(B, n, st, rho);
   }
   double v[1] = {rho};
   block_sum<1>(v);
@@ -403,7 +449,7 @@ __global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st
 
 // ---------------------------------------------------------------------------
 // Alg. 3 line 11: p_k = z_k + beta_{k-1} p_{k-1} in u_z (p_0 = z_0).
-template <int UZ>
+template <int UZ, int V>
 __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevState* st) {
   using TZ = typename Store<UZ>::T;
   const TZ* __restrict__ z = (const TZ*)B.z;
@@ -413,22 +459,35 @@ __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevSta
   const int first = st->first;
   const double beta = st->beta;
   const float bf = st->beta_f;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    TZ zi = z[i];
-    if (first) { pn[i] = zi; continue; }
-    if constexpr (UZ == P64) pn[i] = fma(beta, po[i], zi);
-    else if constexpr (UZ == P32) pn[i] = __fmaf_rn(bf, po[i], zi);
-    else pn[i] = __float2half_rn(__fmaf_rn(bf, h2f(po[i]), h2f(zi)));
+  const int64_t nv = (n + V - 1) / V;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+    const int64_t i0 = v * V;
+    const int m = (n - i0 < V) ? (int)(n - i0) : V;
+    alignas(16) TZ zz[V];
+    alignas(16) TZ pp[V];
+    vldg<V>(z + i0, zz);
+    if (first) {
+      vst<V>(pn + i0, zz, m);
+      continue;
+    }
+    vldg<V>(po + i0, pp);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      if constexpr (UZ == P64) pp[j] = fma(beta, pp[j], zz[j]);
+      else if constexpr (UZ == P32) pp[j] = __fmaf_rn(bf, pp[j], zz[j]);
+      else pp[j] = __float2half_rn(__fmaf_rn(bf, h2f(pp[j]), h2f(zz[j])));
+    }
+    vst<V>(pn + i0, pp, m);
   }
 }
 
 __global__ void __launch_bounds__(256) k_axpy(Bufs B, int64_t n, DevState* st) {
   if (st->done) return;
   const int uz = st->uz;
-  if (uz == P64) axpy_rows<P64>(B, n, st);
-  else if (uz == P32) axpy_rows<P32>(B, n, st);
-  else axpy_rows<P16>(B, n, st);
+  if (uz == P64) axpy_rows<P64, 8>(B, n, st);
+  else if (uz == P32) axpy_rows<P32, 8>(B, n, st);
+  else axpy_rows<P16, 8>(B, n, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -490,32 +549,48 @@ __global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
 // Alg. 3 lines 15-18: x += alpha p (FP64), r -= alpha q (u_r),
 // delta_{k+1} = ||r|| (FP64), max|r| (exact); last block: stopping test and
 // the decision for iteration k+1.
-template <int UZ, int UR>
+template <int UZ, int UR, int V>
 __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevState* st,
                                             double& rr, unsigned long long& mx) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
   const TZ* __restrict__ p = (const TZ*)(st->pcur ? B.p[0] : B.p[1]);
   const TR* __restrict__ q = (const TR*)B.q;
+  TR* __restrict__ rv = UR == P64 ? (TR*)B.r64 : (TR*)B.r32;
   const double a = st->alpha;
   const float af = st->alpha_f;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    B.x[i] = fma(a, to_f64(p[i]), B.x[i]);
-    if constexpr (UR == P64) {
-      double rv = fma(-a, q[i], B.r64[i]);
-      B.r64[i] = rv;
-      rr = fma(rv, rv, rr);
-      unsigned long long kk = abs_key(rv);
-      mx = kk > mx ? kk : mx;
-    } else {
-      float rv = __fmaf_rn(-af, q[i], B.r32[i]);
-      B.r32[i] = rv;
-      double rd = f2d(rv);
-      rr = fma(rd, rd, rr);
-      unsigned long long kk = abs_key(rd);
-      mx = kk > mx ? kk : mx;
+  const int64_t nv = (n + V - 1) / V;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+    const int64_t i0 = v * V;
+    const int m = (n - i0 < V) ? (int)(n - i0) : V;
+    alignas(16) TZ pp[V];
+    alignas(16) TR qq[V];
+    alignas(16) TR rr_[V];
+    alignas(16) double xx[V];
+    vldg<V>(p + i0, pp);
+    vldg<V>(q + i0, qq);
+    vld<V>(rv + i0, rr_);
+    vld<V>(B.x + i0, xx);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      xx[j] = fma(a, to_f64(pp[j]), xx[j]);
+      double rd;
+      if constexpr (UR == P64) {
+        rr_[j] = fma(-a, qq[j], rr_[j]);
+        rd = rr_[j];
+      } else {
+        rr_[j] = __fmaf_rn(-af, qq[j], rr_[j]);
+        rd = f2d(rr_[j]);
+      }
+      if (j < m) {
+        rr = fma(rd, rd, rr);
+        unsigned long long kk = abs_key(rd);
+        mx = kk > mx ? kk : mx;
+      }
     }
+    vst<V>(B.x + i0, xx, m);
+    vst<V>(rv + i0, rr_, m);
   }
 }
 
@@ -525,13 +600,13 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st)
   double rr = 0.0;
   unsigned long long mx = 0ull;
   if (ur == P64) {
-    if (uz == P64) update_rows<P64, P64>(B, n, st, rr, mx);
-    else if (uz == P32) update_rows<P32, P64>(B, n, st, rr, mx);
-    else update_rows<P16, P64>(B, n, st, rr, mx);
+    if (uz == P64) update_rows<P64, P64, 8>(B, n, st, rr, mx);
+    else if (uz == P32) update_rows<P32, P64, 8>(B, n, st, rr, mx);
+    else update_rows<P16, P64, 8>(B, n, st, rr, mx);
   } else {
-    if (uz == P64) update_rows<P64, P32>(B, n, st, rr, mx);
-    else if (uz == P32) update_rows<P32, P32>(B, n, st, rr, mx);
-    else update_rows<P16, P32>(B, n, st, rr, mx);
+    if (uz == P64) update_rows<P64, P32, 8>(B, n, st, rr, mx);
+    else if (uz == P32) update_rows<P32, P32, 8>(B, n, st, rr, mx);
+    else update_rows<P16, P32, 8>(B, n, st, rr, mx);
   }
   double v[1] = {rr};
   block_sum<1>(v);
@@ -786,7 +861,7 @@ __global__ void __launch_bounds__(256) k_residual_step(Sell A, const double* b, 
 template <int UZ, int UR, int MT>
 __global__ void __launch_bounds__(256) k_precond_step(Bufs B, int64_t n, const DevState* st) {
   double rho = 0.0;
-  precond_rows<UZ, UR, MT>(B, n, st, rho);
+  precond_rows<UZ, UR, MT, 1>(B, n, st, rho);
 }
 
 // Selector replay over a residual-norm sequence (one thread).
