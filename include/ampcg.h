@@ -192,6 +192,27 @@ ampcg_status ampcg_residual(ampcg_t ctx, const double* b, const double* x, doubl
 ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const double* delta, int m,
                                   double nb, double tol, uint8_t* out);
 
+/* The same selector replay as ampcg_selector_trace, with the same arguments
+ * and results, but it allocates no device memory: its device scratch (a state
+ * block and three arrays of m+1 entries) lives in one static array compiled
+ * into the library, about 650 KB, which every GPU that loads the library
+ * holds until the process exits.  It is for callers that must not call
+ * cudaMalloc, for example code that runs while a caching allocator has
+ * reserved the device's free memory for itself, or latency-critical loops
+ * where cudaMalloc's implicit device synchronisation is not acceptable.
+ *   - m + 1 must be at most 65536; larger m is rejected with
+ *     AMPCG_ERR_INVALID_ARG and nothing is run.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address once; make that first call before any stream
+ *     capture.
+ *   - All calls share the one array: calls that overlap on the GPU (for
+ *     example from two host threads) race and must be serialised by the
+ *     caller.  Each call writes everything it reads before reading it.
+ *   - Synchronous; uses the legacy default stream, like ampcg_selector_trace.
+ * The paper has no counterpart to this entry point. */
+ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy, const double* delta, int m,
+                                          double nb, double tol, uint8_t* out);
+
 /* Number of rows of the context's matrix, or -1 for NULL. */
 int64_t ampcg_rows(ampcg_t ctx);
 

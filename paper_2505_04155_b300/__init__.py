@@ -101,6 +101,9 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_selector_trace.argtypes = [C.POINTER(PolicyC), dp, C.c_int, C.c_double, C.c_double,
                                          C.POINTER(C.c_uint8)]
     lib.ampcg_selector_trace.restype = C.c_int
+    lib.ampcg_selector_trace_noalloc.argtypes = [C.POINTER(PolicyC), dp, C.c_int, C.c_double,
+                                                 C.c_double, C.POINTER(C.c_uint8)]
+    lib.ampcg_selector_trace_noalloc.restype = C.c_int
     lib.ampcg_rows.argtypes = [vp]
     lib.ampcg_rows.restype = i64
     lib.ampcg_status_string.argtypes = [C.c_int]
@@ -295,4 +298,17 @@ def selector_trace(delta, nb: float, tol: float, policy: Policy | None = None) -
     _check(load_library().ampcg_selector_trace(C.byref(pol), delta.ctypes.data_as(C.POINTER(C.c_double)),
                                                delta.size - 1, nb, tol,
                                                out.ctypes.data_as(C.POINTER(C.c_uint8))))
+    return out
+
+
+def selector_trace_noalloc(delta, nb: float, tol: float, policy: Policy | None = None) -> np.ndarray:
+    """selector_trace without any device allocation (ampcg_selector_trace_noalloc):
+    for callers that must not call cudaMalloc.  At most 65536 residual norms;
+    concurrent calls share one static device array and must be serialised."""
+    delta = np.ascontiguousarray(delta, dtype=np.float64)
+    out = np.zeros(delta.size, dtype=np.uint8)
+    pol = (policy or Policy()).to_c()
+    _check(load_library().ampcg_selector_trace_noalloc(
+        C.byref(pol), delta.ctypes.data_as(C.POINTER(C.c_double)), delta.size - 1, nb, tol,
+        out.ctypes.data_as(C.POINTER(C.c_uint8))))
     return out

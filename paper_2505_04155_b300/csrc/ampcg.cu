@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "../../include/ampcg.h"
@@ -815,5 +816,98 @@ extern "C" ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const d
   cudaFree(d_ph);
   cudaFree(d_st);
   if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "selector trace: %s", cudaGetErrorString(e));
+  return AMPCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Selector replay without any device allocation.
+//
+// ampcg_selector_trace above allocates its device scratch (the state block,
+// the residual history and two byte arrays) with cudaMalloc on every call.
+// This variant keeps that scratch in one file-scope device array instead, so
+// callers that must not allocate device memory can use it.  Every GPU that
+// loads the library holds the array (kNoAllocTraceBytes) until process exit.
+// Host code cannot use the array's name as a device address: the address is
+// looked up per device with cudaGetSymbolAddress, on the first call made with
+// that device current, and cached.
+
+namespace {
+
+constexpr int kNoAllocTraceMax = 65536;  // entries delta[0..m], i.e. m + 1 <= this
+
+struct NoAllocTraceScratch {
+  DevState st;
+  double delta[kNoAllocTraceMax];
+  unsigned char prec[kNoAllocTraceMax];
+  unsigned char out[kNoAllocTraceMax];
+};
+
+constexpr size_t kNoAllocTraceBytes = sizeof(NoAllocTraceScratch);
+
+static __device__ __align__(256) unsigned char g_noalloc_trace_scratch[kNoAllocTraceBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (set-up once per
+// device, with that device current).
+ampcg_status noalloc_scratch(NoAllocTraceScratch** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(AMPCG_ERR_UNSUPPORTED, "device index %d too large", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_trace_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(AMPCG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (NoAllocTraceScratch*)g_noalloc_addr[dev];
+  return AMPCG_OK;
+}
+
+}  // namespace
+
+extern "C" ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy,
+                                                     const double* delta, int m, double nb,
+                                                     double tol, uint8_t* out) {
+  if (!policy || !delta || !out || m < 0) return fail(AMPCG_ERR_INVALID_ARG, "bad argument");
+  if (m + 1 > kNoAllocTraceMax)
+    return fail(AMPCG_ERR_INVALID_ARG,
+                "selector replay without allocation takes at most %d residual norms (m <= %d); got m = %d",
+                kNoAllocTraceMax, kNoAllocTraceMax - 1, m);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(AMPCG_ERR_NO_DEVICE, "no CUDA device visible");
+  }
+  ampcg_status ps = check_policy(policy);
+  if (ps != AMPCG_OK) return ps;
+  NoAllocTraceScratch* sc = nullptr;
+  ps = noalloc_scratch(&sc);
+  if (ps != AMPCG_OK) return ps;
+  // Everything the kernel reads is written here first: the whole state block
+  // (zeroed fields included) and delta[0..m]; prec[k] and out[k] are written
+  // by the kernel before they are read.  Entries past m keep the previous
+  // call's contents and are never read.
+  DevState h;
+  init_state(&h, policy, tol, m + 1, nullptr);
+  h.nb = nb;
+  h.tol_nb = tol * nb;
+  h.maxr = 1.0;
+  h.delta_hist = sc->delta;
+  h.relres_hist = nullptr;
+  h.prec_hist = sc->prec;
+  cudaError_t e = cudaMemcpy(sc->delta, delta, (size_t)(m + 1) * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(&sc->st, &h, sizeof(DevState), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_selector_trace<<<1, 32>>>(&sc->st, m, sc->out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, sc->out, (size_t)(m + 1), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "selector trace (no allocation): %s", cudaGetErrorString(e));
   return AMPCG_OK;
 }
