@@ -17,6 +17,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/ampcg.h"
 #include "kernels.cuh"
@@ -74,6 +75,7 @@ struct ampcg_ctx {
   cudaStream_t cap_stream = nullptr;
   int64_t n = 0, nnz = 0, nslices = 0;
   int idx16 = 0;  // 1: int16 column offsets
+  int maxw = 0;   // largest slice width
   int mtype = M_JACOBI;
   // matrix
   long long* off = nullptr;
@@ -99,6 +101,8 @@ struct ampcg_ctx {
   int hist_cap = 0;
   // launch shapes
   int g_elem = 1, g_rows = 1, g_max = 1;
+  const void* fn[6][4] = {};  // iteration kernels per phase (2 u_z + u_r)
+  int grid[6][4] = {};        // their grids (occupancy-limited, 8 elements per thread)
   // device-side loop graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -108,6 +112,7 @@ struct ampcg_ctx {
     Sell A;
     A.n = n;
     A.nslices = nslices;
+    A.maxw = maxw;
     A.off = off;
     A.width = width;
     A.cabs = idx16 ? nullptr : cabs;
@@ -220,6 +225,9 @@ void ampcg_destroy(ampcg_t c) {
 // ---------------------------------------------------------------------------
 // create
 
+template <int MT, int IT>
+static void fill_phase_table(ampcg_ctx* c);
+
 static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int32_t* rowptr,
                                 const int32_t* colind, const double* vals) {
   cudaStream_t s = c->stream;
@@ -280,7 +288,7 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   TRY(dalloc(&rowlen, n));
   TRY(dalloc(&diag, n));
   TRY(dalloc(&flags, 2));
-  TRY(dalloc(&total, 1));
+  TRY(dalloc(&total, 2));
   CTRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
   int gb = (int)((n + kBlock - 1) / kBlock);
   k_csr_scan_rows<<<gb, kBlock, 0, s>>>(n, nnz, d_rp, d_ci, d_v, rowlen, diag, flags, flags + 1);
@@ -309,9 +317,11 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   k_slice_width<<<gs, kBlock, 0, s>>>(n, c->nslices, rowlen, c->width);
   k_slice_offsets<<<1, 1024, 0, s>>>(c->nslices, c->width, c->off, total);
   CTRY(cudaGetLastError());
-  long long stored = 0;
-  CTRY(cudaMemcpyAsync(&stored, total, sizeof(stored), cudaMemcpyDeviceToHost, s));
+  long long tot2[2] = {0, 0};
+  CTRY(cudaMemcpyAsync(tot2, total, sizeof(tot2), cudaMemcpyDeviceToHost, s));
   CTRY(cudaStreamSynchronize(s));
+  long long stored = tot2[0];
+  c->maxw = (int)tot2[1];
   if (c->idx16) TRY(dalloc(&c->coff, stored));
   else TRY(dalloc(&c->cabs, stored));
   TRY(dalloc(&c->v64, stored));
@@ -341,12 +351,19 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   // launch shapes
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  int g1 = occ_grid((const void*)k_precond<M_JACOBI>, sms, n);
-  int g2 = occ_grid((const void*)k_axpy, sms, n);
-  int g3 = occ_grid((const void*)k_update, sms, n);
-  c->g_elem = g1 < g2 ? (g1 < g3 ? g1 : g3) : (g2 < g3 ? g2 : g3);
-  c->g_rows = occ_grid(c->idx16 ? (const void*)k_spmv<1> : (const void*)k_spmv<0>, sms, rows_pad);
+  int64_t nvec = (n + 7) / 8;
+  if (c->mtype == M_NONE) { if (c->idx16) fill_phase_table<M_NONE, 1>(c); else fill_phase_table<M_NONE, 0>(c); }
+  else { if (c->idx16) fill_phase_table<M_JACOBI, 1>(c); else fill_phase_table<M_JACOBI, 0>(c); }
+  for (int ph = 0; ph < 6; ++ph)
+    for (int j = 0; j < 4; ++j)
+      c->grid[ph][j] = occ_grid(c->fn[ph][j], sms, j == 2 ? (c->nslices * 32 + 1) / 2 : nvec);
+  c->g_elem = occ_grid((const void*)k_refresh, sms, n);
+  c->g_rows = occ_grid(c->idx16 ? (const void*)k_true_residual<1> : (const void*)k_true_residual<0>, sms,
+                       rows_pad);
   c->g_max = c->g_elem > c->g_rows ? c->g_elem : c->g_rows;
+  for (int ph = 0; ph < 6; ++ph)
+    for (int j = 0; j < 4; ++j)
+      if (c->grid[ph][j] > c->g_max) c->g_max = c->grid[ph][j];
   int gi = occ_grid((const void*)k_init<0>, sms, rows_pad);
   if (gi > c->g_max) c->g_max = gi;
   TRY(dalloc(&c->part, (size_t)c->g_max * 4));
@@ -432,52 +449,121 @@ static ampcg_status ensure_hist(ampcg_ctx* c, int maxit) {
   return AMPCG_OK;
 }
 
+// The four iteration kernels of a phase (2 u_z + u_r): precond, axpy, spmv,
+// update.  Argument lists: (Bufs, n, state) for precond/axpy, (Sell, Bufs,
+// state) for spmv, (Bufs, n, state, next switch handle, has_next) for update.
 template <int MT, int IT>
-static void launch_iteration(ampcg_ctx* c, cudaStream_t s) {
-  Sell A = c->sell();
-  Bufs B = c->bufs();
-  k_precond<MT><<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
-  k_axpy<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
-  k_spmv<IT><<<c->g_rows, kBlock, 0, s>>>(A, B, c->st);
-  k_update<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
+static void fill_phase_table(ampcg_ctx* c) {
+#define AMPCG_PHASE_FNS(UZ, UR)                                                             \
+  {(const void*)k_precond<UZ, UR, MT>, (const void*)k_axpy<UZ>, (const void*)k_spmv<UZ, UR, IT>, \
+   (const void*)k_update<UZ, UR>}
+  const void* t[6][4] = {AMPCG_PHASE_FNS(P64, P64), AMPCG_PHASE_FNS(P64, P32),
+                         AMPCG_PHASE_FNS(P32, P64), AMPCG_PHASE_FNS(P32, P32),
+                         AMPCG_PHASE_FNS(P16, P64), AMPCG_PHASE_FNS(P16, P32)};
+#undef AMPCG_PHASE_FNS
+  memcpy(c->fn, t, sizeof(t));
 }
 
-static void launch_iteration_any(ampcg_ctx* c, cudaStream_t s) {
-  if (c->mtype == M_NONE) {
-    if (c->idx16) launch_iteration<M_NONE, 1>(c, s);
-    else launch_iteration<M_NONE, 0>(c, s);
-  } else {
-    if (c->idx16) launch_iteration<M_JACOBI, 1>(c, s);
-    else launch_iteration<M_JACOBI, 0>(c, s);
+struct PhaseArgs {
+  Bufs B;
+  Sell A;
+  int64_t n;
+  DevState* st;
+  cudaGraphConditionalHandle h;
+  int has_next;
+  void* a_elem[3];
+  void* a_spmv[3];
+  void* a_upd[5];
+  PhaseArgs(const ampcg_ctx* c, cudaGraphConditionalHandle hn, int has)
+      : B(c->bufs()), A(c->sell()), n(c->n), st(c->st), h(hn), has_next(has) {
+    a_elem[0] = &B; a_elem[1] = &n; a_elem[2] = &st;
+    a_spmv[0] = &A; a_spmv[1] = &B; a_spmv[2] = &st;
+    a_upd[0] = &B; a_upd[1] = &n; a_upd[2] = &st; a_upd[3] = &h; a_upd[4] = &has_next;
   }
+  void** args(int j) { return j < 2 ? a_elem : (j == 2 ? a_spmv : a_upd); }
+};
+
+// One iteration of phase ph launched kernel by kernel on stream s, with an
+// event before each kernel and after the last (ev may be null).
+static cudaError_t launch_phase(ampcg_ctx* c, int ph, cudaStream_t s, cudaEvent_t* ev) {
+  PhaseArgs pa(c, 0, 0);
+  for (int j = 0; j < 4; ++j) {
+    if (ev) {
+      cudaError_t e = cudaEventRecord(ev[j], s);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaLaunchKernel(c->fn[ph][j], dim3(c->grid[ph][j]), dim3(kBlock), pa.args(j), 0, s);
+    if (e != cudaSuccess) return e;
+  }
+  return ev ? cudaEventRecord(ev[4], s) : cudaSuccess;
 }
 
+static cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* dep,
+                                   const void* fn, int grid, int block, void** args) {
+  cudaKernelNodeParams p;
+  memset(&p, 0, sizeof(p));
+  p.func = (void*)fn;
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &p);
+}
+
+// Loop graph: WHILE(!done) { k_phase; SWITCH_0 .. SWITCH_{chunk-1}; k_loop_ctl }.
+// SWITCH_i has six bodies, one per phase, each holding that phase's four
+// kernels; the update kernel of iteration i sets the value of SWITCH_{i+1}
+// (k_phase sets SWITCH_0).  After the stop every value is AMPCG_PHASE_NONE,
+// which matches no body, so the rest of the chunk launches nothing.
 static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
   if (c->gexec && c->graph_chunk == chunk) return AMPCG_OK;
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
   CUDA_TRY(cudaGraphCreate(&c->graph, 0));
-  cudaGraphConditionalHandle h;
-  CUDA_TRY(cudaGraphConditionalHandleCreate(&h, c->graph, 1u, cudaGraphCondAssignDefault));
+  cudaGraphConditionalHandle hw;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&hw, c->graph, 1u, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
   cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
+  cp.conditional.handle = hw;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  cudaGraphNode_t node;
-  CUDA_TRY(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &cp));
+  cudaGraphNode_t wnode;
+  CUDA_TRY(cudaGraphAddNode(&wnode, c->graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  cudaStream_t cs = c->cap_stream;
-  CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
-                                         cudaStreamCaptureModeThreadLocal));
-  for (int i = 0; i < chunk; ++i) launch_iteration_any(c, cs);
-  k_loop_ctl<<<1, 1, 0, cs>>>(c->st, h);
-  cudaError_t le = cudaGetLastError();
-  cudaGraph_t captured = nullptr;
-  cudaError_t ee = cudaStreamEndCapture(cs, &captured);
-  if (le != cudaSuccess || ee != cudaSuccess)
-    return fail(AMPCG_ERR_CUDA, "graph capture failed: %s / %s", cudaGetErrorString(le),
-                cudaGetErrorString(ee));
+  std::vector<cudaGraphConditionalHandle> hs(chunk);
+  for (int i = 0; i < chunk; ++i)
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&hs[i], body, AMPCG_PHASE_NONE, cudaGraphCondAssignDefault));
+  DevState* st = c->st;
+  cudaGraphConditionalHandle h0 = hs[0];
+  void* aphase[2] = {&st, &h0};
+  cudaGraphNode_t prev;
+  CUDA_TRY(add_kernel_node(&prev, body, nullptr, (const void*)k_phase, 1, 1, aphase));
+  for (int i = 0; i < chunk; ++i) {
+    cudaGraphNodeParams sp = {cudaGraphNodeTypeConditional};
+    sp.type = cudaGraphNodeTypeConditional;
+    sp.conditional.handle = hs[i];
+    sp.conditional.type = cudaGraphCondTypeSwitch;
+    sp.conditional.size = 6;
+    cudaGraphNode_t snode;
+    CUDA_TRY(cudaGraphAddNode(&snode, body, &prev, nullptr, 1, &sp));
+    bool has_next = i + 1 < chunk;
+    PhaseArgs pa(c, has_next ? hs[i + 1] : 0, has_next ? 1 : 0);
+    for (int ph = 0; ph < 6; ++ph) {
+      cudaGraph_t pg = sp.conditional.phGraph_out[ph];
+      cudaGraphNode_t kn = nullptr;
+      for (int j = 0; j < 4; ++j) {
+        cudaGraphNode_t nn;
+        CUDA_TRY(add_kernel_node(&nn, pg, j ? &kn : nullptr, c->fn[ph][j], c->grid[ph][j], kBlock,
+                                 pa.args(j)));
+        kn = nn;
+      }
+    }
+    prev = snode;
+  }
+  void* actl[2] = {&st, &hw};
+  cudaGraphNode_t cnode;
+  CUDA_TRY(add_kernel_node(&cnode, body, &prev, (const void*)k_loop_ctl, 1, 1, actl));
   CUDA_TRY(cudaGraphInstantiate(&c->gexec, c->graph, 0));
   c->graph_chunk = chunk;
   return AMPCG_OK;
@@ -514,55 +600,37 @@ static void init_state(DevState* h, const ampcg_policy* p, double tol, int maxit
   h->ur = P64;
   h->uz_p = h->uz;
   h->first = 1;
+  h->k_body = -1;
   h->switch_iter[0] = h->switch_iter[1] = h->switch_iter[2] = -1;
   h->delta_hist = c ? c->dhist : nullptr;
   h->relres_hist = c ? c->rhist : nullptr;
   h->prec_hist = c ? c->phist : nullptr;
 }
 
-// Eager loop with a CUDA event pair around every iteration kernel (timing
-// mode).  Runs chunks of iterations, then reads the iteration counter to learn
-// how many of the chunk's iterations did work; no-op launches after the stop
-// are not counted.
-template <int MT, int IT>
-static ampcg_status timed_loop(ampcg_ctx* c, ampcg_kernel_times* kt, cudaEvent_t* ev, int chunk) {
+// Launch-by-launch loop with a CUDA event pair around every iteration kernel
+// (timing mode).  The host reads the state after each iteration to pick the
+// next phase's kernels; an iteration counts when it advanced the counter.
+static ampcg_status timed_loop(ampcg_ctx* c, ampcg_kernel_times* kt, cudaEvent_t* ev,
+                               long long& launches) {
   cudaStream_t s = c->stream;
-  Sell A = c->sell();
-  Bufs B = c->bufs();
-  for (;;) {
+  while (!c->hst->done) {
     int k0 = c->hst->k;
-    for (int i = 0; i < chunk; ++i) {
-      cudaEvent_t* e = ev + i * 5;
-      CUDA_TRY(cudaEventRecord(e[0], s));
-      k_precond<MT><<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
-      CUDA_TRY(cudaEventRecord(e[1], s));
-      k_axpy<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
-      CUDA_TRY(cudaEventRecord(e[2], s));
-      k_spmv<IT><<<c->g_rows, kBlock, 0, s>>>(A, B, c->st);
-      CUDA_TRY(cudaEventRecord(e[3], s));
-      k_update<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
-      CUDA_TRY(cudaEventRecord(e[4], s));
-    }
-    CUDA_TRY(cudaGetLastError());
+    int ph = 2 * c->hst->uz + c->hst->ur;
+    if (ph < 0 || ph > 5) return fail(AMPCG_ERR_CUDA, "invalid phase %d in device state", ph);
+    CUDA_TRY(launch_phase(c, ph, s, ev));
+    launches += 4;
     CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    int done_iters = c->hst->k - k0;
-    // a chunk that stopped on breakdown ran part of one more iteration
-    if (done_iters > chunk) done_iters = chunk;
-    unsigned char ph[1024];
-    if (done_iters > 0)
-      CUDA_TRY(cudaMemcpy(ph, c->phist + k0, done_iters, cudaMemcpyDeviceToHost));
-    for (int i = 0; i < done_iters; ++i) {
-      int phase = (ph[i] >> 4) * 2 + (ph[i] & 15);
+    if (c->hst->k > k0) {
       for (int j = 0; j < 4; ++j) {
         float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, ev[i * 5 + j], ev[i * 5 + j + 1]));
-        kt->ms[j][phase] += ms;
-        kt->launches[j][phase] += 1;
+        CUDA_TRY(cudaEventElapsedTime(&ms, ev[j], ev[j + 1]));
+        kt->ms[j][ph] += ms;
+        kt->launches[j][ph] += 1;
       }
     }
-    if (c->hst->done) return AMPCG_OK;
   }
+  return AMPCG_OK;
 }
 
 static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double tol, int maxit,
@@ -609,18 +677,21 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
     hs = ensure_graph(c, chunk);
     if (hs != AMPCG_OK) return hs;
   }
-  if (kt && chunk > 64) chunk = 64;
-  cudaEvent_t ev[64 * 5];
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t e_first = nullptr, e_last = nullptr;
+  struct EvGuard {
+    cudaEvent_t* ev; cudaEvent_t* a; cudaEvent_t* b;
+    ~EvGuard() {
+      for (int i = 0; i < 5; ++i) if (ev[i]) cudaEventDestroy(ev[i]);
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } guard{ev, &e_first, &e_last};
   if (kt) {
-    for (int i = 0; i < chunk * 5; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
+    for (int i = 0; i < 5; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
     CUDA_TRY(cudaEventCreate(&e_first));
     CUDA_TRY(cudaEventCreate(&e_last));
   }
-  struct EvGuard {
-    cudaEvent_t* ev; int n; cudaEvent_t a, b;
-    ~EvGuard() { for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]); if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
-  } guard{ev, kt ? chunk * 5 : 0, e_first, e_last};
   Sell A = c->sell();
   Bufs B = c->bufs();
   int64_t rows_pad = c->nslices * 32;
@@ -638,9 +709,7 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   }
   for (;;) {
     if (kt) {
-      ampcg_status ts;
-      if (c->mtype == M_NONE) ts = c->idx16 ? timed_loop<M_NONE, 1>(c, kt, ev, chunk) : timed_loop<M_NONE, 0>(c, kt, ev, chunk);
-      else ts = c->idx16 ? timed_loop<M_JACOBI, 1>(c, kt, ev, chunk) : timed_loop<M_JACOBI, 0>(c, kt, ev, chunk);
+      ampcg_status ts = timed_loop(c, kt, ev, launches);
       if (ts != AMPCG_OK) return ts;
     } else {
       CUDA_TRY(cudaGraphLaunch(c->gexec, s));
@@ -652,14 +721,15 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
     CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     const DevState& h = *c->hst;
-    {
-      // bodies of the device loop that ran: the body in which `done` was set
-      // completes, and a body always runs once
+    if (!kt) {
+      // device loop: every body launches k_phase and k_loop_ctl; switch nodes
+      // launch their four kernels only for iterations that run (an iteration
+      // that stops on breakdown still launches its four)
       long long it = h.k - k_before + (h.status == ST_OK || h.status == ST_NOT_CONVERGED ? 0 : 1);
       long long bodies = it <= 0 ? 1 : (it + chunk - 1) / chunk;
-      launches += kt ? bodies * 4LL * chunk : bodies * (4LL * chunk + 1);
-      k_before = h.k;
+      launches += 2 * bodies + 4 * it;
     }
+    k_before = h.k;
     // reading R9: verify, and replace r when the true residual misses tol
     bool refresh = h.status == ST_OK && h.refreshes < pol.verify_refresh && h.k < maxit &&
                    h.true_relres * h.nb > h.tol_nb;
@@ -667,6 +737,10 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
     k_refresh<<<c->g_elem, kBlock, 0, s>>>(B, c->n, c->st);
     CUDA_TRY(cudaGetLastError());
     launches += 1;
+    if (kt) {
+      CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+    }
   }
   if (kt) {
     CUDA_TRY(cudaEventRecord(e_last, s));
@@ -697,6 +771,12 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
     for (int i = 0; i < 3; ++i) res->switch_iter[i] = h.switch_iter[i];
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     res->kernel_launches = launches;
+  }
+  if (h.status == ST_INTERNAL) {
+    st = AMPCG_ERR_CUDA;
+    if (res) res->status = st;
+    return fail(st, "internal error: device loop made no progress or ran a kernel for the wrong "
+                "precision pair (iteration %d)", iters);
   }
   if (st != AMPCG_OK && st != AMPCG_NOT_CONVERGED)
     fail(st, "solve stopped at iteration %d: %s", iters, ampcg_status_string(st));

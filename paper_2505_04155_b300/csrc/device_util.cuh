@@ -34,11 +34,23 @@ __device__ __forceinline__ double f2d_normal(float f) {
   return __hiloint2double((int)hi, (int)(a << 29));
 }
 
-// Any binary32 value; binary32 subnormals (rare) take the hardware path.
+// Any binary32 value, integer operations only.  A subnormal a * 2^-149 with
+// its leading one at bit p = 31 - clz(a) becomes 2^(p-149) (1 + fraction):
+// the fraction is a shifted left by clz(a) - 8, the biased binary64 exponent
+// is p - 149 + 1023 = 905 - clz(a).
 __device__ __forceinline__ double f2d(float f) {
-  unsigned a = __float_as_uint(f) & 0x7fffffffu;
-  if (a != 0u && a < 0x00800000u) return (double)f;
-  return f2d_normal(f);
+  unsigned u = __float_as_uint(f);
+  unsigned s = u & 0x80000000u, a = u & 0x7fffffffu;
+  unsigned hi = (a == 0u) ? s : (s | ((a >> 3) + (896u << 20)));
+  unsigned lo = a << 29;
+  if (a >= 0x7f800000u) hi = s | 0x7ff00000u | ((a >> 3) & 0x000fffffu);
+  if (a != 0u && a < 0x00800000u) {
+    int lz = __clz((int)a);
+    unsigned m = (a << (lz - 8)) & 0x007fffffu;
+    hi = s | ((unsigned)(905 - lz) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ float h2f(__half h) { return __half2float(h); }
@@ -155,6 +167,52 @@ __device__ __forceinline__ unsigned long long abs_key(float v) {
 }
 
 // ---------------------------------------------------------------------------
+// Inner products accumulated to FP64-level accuracy.
+//
+// Binary64 operand: one FP64 fma per term, FP64 reductions.  Binary32/binary16
+// operands: the product a*b is split exactly into h + l with an fma
+// (two-product), h is added to a binary32 running sum with its rounding error
+// captured exactly (two-sum), and the errors plus l are gathered in a binary32
+// correction -- the compensated dot product Dot2 of Ogita, Rump and Oishi
+// ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005).  A thread's
+// (sum, correction) pair is reduced across its warp with the same two-sum
+// step and converted to binary64 once per warp.  For a thread with n terms the
+// error is at most about (n eps32)^2 times the sum of |terms| (n <= 32 here:
+// <= 4e-12, typically ~1e-14), within the accuracy of a binary64 recursive sum
+// of the same vector, while the work stays on B300's binary32 pipes (its
+// binary64 pipe issues ~1/58 of the binary32 rate).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    float h = __fmul_rn(a, b);
+    float l = __fmaf_rn(a, b, -h);
+    float t, e;
+    two_sum(s, h, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, l));
+  }
+  // warp reduction of the pairs (all lanes take part); lane 0 gets the total
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float s2 = __shfl_down_sync(0xffffffffu, s, o);
+      float c2 = __shfl_down_sync(0xffffffffu, c, o);
+      float t, e;
+      two_sum(s, s2, t, e);
+      s = t;
+      c = __fadd_rn(__fadd_rn(c, c2), e);
+    }
+  }
+  __device__ __forceinline__ double to_f64() const { return __dadd_rn(f2d(s), f2d(c)); }
+};
+
+// ---------------------------------------------------------------------------
 // Reductions.  Fixed shapes, so results are reproducible run to run.
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -193,6 +251,20 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
       v[j] = warp_sum(t);
     }
   }
+}
+
+// Block total of per-thread Dot2 pairs, scaled by `scale` (a power of two);
+// valid in thread 0.  Binary64 work: one add per warp plus warp 0's tree.
+__device__ __forceinline__ double block_sum_dot2(Dot2 d, double scale) {
+  __shared__ double shd[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  d.warp_reduce();
+  __syncthreads();
+  if (lane == 0) shd[wid] = __dmul_rn(d.to_f64(), scale);
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) t = warp_sum(lane < nw ? shd[lane] : 0.0);
+  return t;
 }
 
 __device__ __forceinline__ unsigned long long block_max(unsigned long long v) {

@@ -11,8 +11,11 @@
 //                                   ||r||, max|r|; last block: stopping test
 //                                   (line 18), indicator and selector for the
 //                                   next iteration (lines 3-4), omega.
-// The per-iteration precisions (u_z, u_r) live in device memory; every kernel
-// reads them and branches uniformly into a template specialised for them.
+// Each kernel is specialised for one precision pair (u_z, u_r) (phase index
+// 2 u_z + u_r), so every variant gets its own register allocation.  The pair
+// of an iteration is decided on the device (last block of k_update / k_init)
+// and selects the variant through a conditional SWITCH node of the loop graph
+// (or through the host, in the launch-by-launch timing mode).
 #pragma once
 #include "device_util.cuh"
 
@@ -21,7 +24,13 @@ namespace ampcg {
 enum { CRIT_WINDOW = 0, CRIT_LINEAR = 1, CRIT_FIXED = 2 };
 enum { SCALE_NONE = 0, SCALE_L2 = 1, SCALE_LINF_POW2 = 2 };
 enum { M_NONE = 0, M_JACOBI = 1, M_CHEBYSHEV = 2 };
-enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = -3, ST_NONFINITE = -4 };
+enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = -3, ST_NONFINITE = -4, ST_INTERNAL = -5 };
+
+// Switch value for an iteration that must not run (solve finished): matches
+// no body of the SWITCH node, so nothing is launched.
+#define AMPCG_PHASE_NONE 6
+
+
 
 // Unit roundoff of binary32 (2^-24), the eps_32 of Eq. (eta_k).
 #define AMPCG_EPS32 5.9604644775390625e-08
@@ -36,13 +45,17 @@ struct DevState {
   int first;           // no search direction yet
   int refreshes;
   int switch_iter[3];
+  int k_body;          // iteration counter seen by the previous loop-body end
   // policy
   int criterion, u0, d, ell, scale, latch, fixed_uz, fixed_ur;
   double C, tau_zs, tau_zh, tol;
   // scalars (FP64, Sec. 4: all scalar work in double precision)
   double nb, tol_nb, delta, maxr, omega;
   int omega_pow2, omega_e;  // omega = 2^omega_e when omega_pow2
-  float omega_f, beta_f, alpha_f, pad_f;
+  float omega_f, beta_f, alpha_f;
+  float sig_f;              // 2^sig_e: exact scale of r in binary32 dot products
+  int sig_e;
+  double inv_sig, inv_sig2; // 2^-sig_e, 2^-2 sig_e
   double rho, rho_prev, beta, gamma, alpha, true_relres;
   unsigned int ticket[4];
   // histories (device)
@@ -50,6 +63,19 @@ struct DevState {
   double* relres_hist;       // [maxit + 2]
   unsigned char* prec_hist;  // [maxit + 1]
 };
+
+// Precision pair check at kernel entry: a variant launched for another pair
+// (which the dispatch never does) stops the solve with an internal error
+// instead of computing with the wrong types.  All blocks read the same state,
+// so all return together and no reduction ticket is taken.
+__device__ __forceinline__ bool phase_mismatch(DevState* st, int uz, int ur) {
+  if (st->uz == uz && (ur < 0 || st->ur == ur)) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->status = ST_INTERNAL;
+    st->done = 1;
+  }
+  return true;
+}
 
 // Matrix in sliced-ELL form: rows are grouped 32 per slice (one warp); the
 // entries of a slice are stored column-major (entry j of row lane at
@@ -59,6 +85,7 @@ struct DevState {
 // are int32 absolute or int16 offsets col - row (when every offset fits).
 struct Sell {
   int64_t n, nslices;
+  int maxw;              // largest slice width
   const long long* off;  // [nslices]
   const int* width;      // [nslices]
   const int* cabs;       // int32 absolute columns, or null
@@ -146,6 +173,20 @@ __device__ void decide(DevState* st) {
   st->omega_f = __double2float_rn(om);
   st->omega_pow2 = pow2;
   st->omega_e = e;
+  // sigma_k = 2^-ceil(log2 max|r_k|) (clamped to binary32's normal range):
+  // scales r in binary32 inner products so that their terms stay in range
+  int se = 0;
+  double mr = st->maxr;
+  if (mr > 0.0 && mr < __longlong_as_double(0x7ff0000000000000ll)) {
+    int E;
+    double f = frexp(mr, &E);
+    se = -((f == 0.5) ? E - 1 : E);
+    se = se < -126 ? -126 : (se > 126 ? 126 : se);
+  }
+  st->sig_e = se;
+  st->sig_f = __double2float_rn(ldexp(1.0, se));
+  st->inv_sig = ldexp(1.0, -se);
+  st->inv_sig2 = ldexp(1.0, -2 * se);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,7 +359,7 @@ __global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
 // Alg. 3 lines 5-7 (+ the storage conversions of readings R10 and line 11).
 template <int UZ, int UR, int MT, int V>
 __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const DevState* st,
-                                             double& rho) {
+                                             double& rho, Dot2& d2) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
   TZ* __restrict__ z = (TZ*)B.z;
@@ -326,6 +367,11 @@ __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const Dev
   const double om = st->omega;
   const float omf = st->omega_f;
   const int pow2 = st->omega_pow2, oe = st->omega_e;
+  const bool om_one = pow2 && oe == 0;
+  // rho: binary32 compensated products when neither operand is binary64
+  // (r scaled by the exact power of two sig_f; the block total is unscaled)
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+  const float sigf = st->sig_f;
   const int64_t nv = (n + V - 1) / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
@@ -368,7 +414,7 @@ __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const Dev
       TZ y;
       if constexpr (UR == P64) {
         if constexpr (UZ == P16) y = pow2 ? d2h_scaled(r[j], oe) : d2h(__dmul_rn(om, r[j]));
-        else y = round_from_f64<UZ>(__dmul_rn(om, r[j]));
+        else y = round_from_f64<UZ>(om_one ? r[j] : __dmul_rn(om, r[j]));
       } else {
         y = round_from_f32<UZ>(__fmul_rn(omf, r[j]));
       }
@@ -376,8 +422,11 @@ __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const Dev
       else if constexpr (UZ == P64) zz[j] = __dmul_rn(dv[j], y);
       else if constexpr (UZ == P32) zz[j] = __fmul_rn(dv[j], y);
       else zz[j] = __float2half_rn(__fmul_rn(h2f(dv[j]), h2f(y)));
-      // rho_k = r_k^T z_k accumulated in FP64
-      if (j < m) rho = fma(to_f64(r[j]), to_f64(zz[j]), rho);
+      // rho_k = r_k^T z_k accumulated to FP64 accuracy
+      if (j < m) {
+        if constexpr (kSmall) d2.add(__fmul_rn((float)r[j], sigf), (float)zz[j]);
+        else rho = fma(to_f64(r[j]), to_f64(zz[j]), rho);
+      }
     }
     vst<V>(z + i0, zz, m);
   }
@@ -404,27 +453,25 @@ __device__ __forceinline__ void cast_p(const Bufs& B, int64_t n, const DevState*
 
 template <int UZ, int UR, int MT, int V>
 __device__ __forceinline__ void precond_and_cast(const Bufs& B, int64_t n, const DevState* st,
-                                                 double& rho) {
-  precond_rows<UZ, UR, MT, V>(B, n, st, rho);
+                                                 double& rho, Dot2& d2) {
+  precond_rows<UZ, UR, MT, V>(B, n, st, rho, d2);
   if (st->p_cast) cast_p<UZ>(B, n, st);
 }
 
-template <int MT>
+template <int UZ, int UR, int MT>
 __global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st) {
   if (st->done) return;
-  const int uz = st->uz, ur = st->ur;
+  if (phase_mismatch(st, UZ, UR)) return;
   double rho = 0.0;
-  if (ur == P64) {
-    if (uz == P64) precond_and_cast<P64, P64, MT, 8>(B, n, st, rho);
-    else if (uz == P32) precond_and_cast<P32, P64, MT, 8>(B, n, st, rho);
-    else precond_and_cast<P16, P64, MT, 8>(B, n, st, rho);
+  Dot2 d2;
+  precond_and_cast<UZ, UR, MT, 8>(B, n, st, rho, d2);
+  double v[1];
+  if constexpr ((UR != P64) && (UZ != P64)) {
+    v[0] = block_sum_dot2(d2, st->inv_sig);
   } else {
-    if (uz == P64) precond_and_cast<P64, P32, MT, 8>(B, n, st, rho);
-    else if (uz == P32) precond_and_cast<P32, P32, MT, 8>(B, n, st, rho);
-    else precond_and_cast<P16, P32, MT, 8>(B, n, st, rho);
+    v[0] = rho;
+    block_sum<1>(v);
   }
-  double v[1] = {rho};
-  block_sum<1>(v);
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[0])) return;
   double tot[1];
@@ -482,53 +529,89 @@ __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevSta
   }
 }
 
+template <int UZ>
 __global__ void __launch_bounds__(256) k_axpy(Bufs B, int64_t n, DevState* st) {
   if (st->done) return;
-  const int uz = st->uz;
-  if (uz == P64) axpy_rows<P64, 8>(B, n, st);
-  else if (uz == P32) axpy_rows<P32, 8>(B, n, st);
-  else axpy_rows<P16, 8>(B, n, st);
+  if (phase_mismatch(st, UZ, -1)) return;
+  axpy_rows<UZ, 8>(B, n, st);
 }
 
 // ---------------------------------------------------------------------------
 // Alg. 3 lines 12-14: q_k = A p_k in u_r, gamma_k = q_k^T p_k (FP64),
 // alpha_k = rho_k / gamma_k.  One thread per row of a warp's slice.
+// Each warp owns a contiguous run of slices; it loads the headers (offset,
+// width) of up to 32 slices with one coalesced load and hands them out by
+// shuffle, so a slice costs two dependent memory round trips (entries, then
+// gathers) instead of three.
 template <int UZ, int UR, int IT>
 __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const DevState* st,
-                                          double& gam) {
+                                          double& gam, Dot2& d2) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
   const TZ* __restrict__ p = (const TZ*)(st->pcur ? B.p[0] : B.p[1]);
   TR* __restrict__ q = (TR*)B.q;
-  int lane = threadIdx.x & 31;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int s = warp; s < A.nslices; s += nwarps) {
-    int row = s * 32 + lane;
-    if (row < A.n) {
-      TR acc = sell_row<UZ, UR, IT>(A, s, lane, row, p);
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+  const TR* __restrict__ va = mat_vals<UR>(A);
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t spw = (A.nslices + nw - 1) / nw;
+  const int64_t s0 = gw * spw;
+  const int64_t s1 = s0 + spw < A.nslices ? s0 + spw : A.nslices;
+  for (int64_t sb = s0; sb < s1; sb += 32) {
+    const int64_t sh = sb + lane;
+    long long hoff = 0;
+    int hw = 0;
+    if (sh < s1) {
+      hoff = __ldg(A.off + sh);
+      hw = __ldg(A.width + sh);
+    }
+    const int cnt = (int)(s1 - sb < 32 ? s1 - sb : 32);
+    for (int i = 0; i < cnt; ++i) {
+      const long long base = __shfl_sync(0xffffffffu, hoff, i) + lane;
+      const int w = __shfl_sync(0xffffffffu, hw, i);
+      const int64_t row = (sb + i) * 32 + lane;
+      if (row >= A.n) continue;
+      TR acc = (TR)0;
+      if (w <= 8) {
+        TR a[8];
+        int c[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < w) {
+            a[j] = __ldg(va + base + 32 * j);
+            c[j] = col_at<IT>(A, base + 32 * j, (int)row);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j < w) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(p[c[j]]), acc);
+      } else {
+        for (int j = 0; j < w; ++j)
+          acc = fma_r<UR>(__ldg(va + base + 32 * j),
+                          PToR<UZ, UR>::cv(p[col_at<IT>(A, base + 32 * j, (int)row)]), acc);
+      }
       q[row] = acc;
-      gam = fma(to_f64(acc), to_f64(p[row]), gam);
+      if constexpr (kSmall) d2.add((float)acc, (float)p[row]);
+      else gam = fma(to_f64(acc), to_f64(p[row]), gam);
     }
   }
 }
 
-template <int IT>
+template <int UZ, int UR, int IT>
 __global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
   if (st->done) return;
-  const int uz = st->uz, ur = st->ur;
+  if (phase_mismatch(st, UZ, UR)) return;
   double gam = 0.0;
-  if (ur == P64) {
-    if (uz == P64) spmv_rows<P64, P64, IT>(A, B, st, gam);
-    else if (uz == P32) spmv_rows<P32, P64, IT>(A, B, st, gam);
-    else spmv_rows<P16, P64, IT>(A, B, st, gam);
+  Dot2 d2;
+  spmv_rows<UZ, UR, IT>(A, B, st, gam, d2);
+  double v[1];
+  if constexpr ((UR != P64) && (UZ != P64)) {
+    v[0] = block_sum_dot2(d2, 1.0);
   } else {
-    if (uz == P64) spmv_rows<P64, P32, IT>(A, B, st, gam);
-    else if (uz == P32) spmv_rows<P32, P32, IT>(A, B, st, gam);
-    else spmv_rows<P16, P32, IT>(A, B, st, gam);
+    v[0] = gam;
+    block_sum<1>(v);
   }
-  double v[1] = {gam};
-  block_sum<1>(v);
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[1])) return;
   double tot[1];
@@ -551,7 +634,7 @@ __global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
 // the decision for iteration k+1.
 template <int UZ, int UR, int V>
 __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevState* st,
-                                            double& rr, unsigned long long& mx) {
+                                            double& rr, Dot2& d2, unsigned long long& mx) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
   const TZ* __restrict__ p = (const TZ*)(st->pcur ? B.p[0] : B.p[1]);
@@ -559,6 +642,7 @@ __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevS
   TR* __restrict__ rv = UR == P64 ? (TR*)B.r64 : (TR*)B.r32;
   const double a = st->alpha;
   const float af = st->alpha_f;
+  const float sigf = st->sig_f;
   const int64_t nv = (n + V - 1) / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
@@ -575,41 +659,48 @@ __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevS
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       xx[j] = fma(a, to_f64(pp[j]), xx[j]);
-      double rd;
       if constexpr (UR == P64) {
         rr_[j] = fma(-a, qq[j], rr_[j]);
-        rd = rr_[j];
+        if (j < m) {
+          rr = fma(rr_[j], rr_[j], rr);
+          unsigned long long kk = abs_key(rr_[j]);
+          mx = kk > mx ? kk : mx;
+        }
       } else {
         rr_[j] = __fmaf_rn(-af, qq[j], rr_[j]);
-        rd = f2d(rr_[j]);
-      }
-      if (j < m) {
-        rr = fma(rd, rd, rr);
-        unsigned long long kk = abs_key(rd);
-        mx = kk > mx ? kk : mx;
+        if (j < m) {
+          float rs = __fmul_rn(rr_[j], sigf);
+          d2.add(rs, rs);
+          unsigned kk = __float_as_uint(rr_[j]) & 0x7fffffffu;   // order-preserving |r|
+          mx = kk > mx ? kk : mx;
+        }
       }
     }
     vst<V>(B.x + i0, xx, m);
     vst<V>(rv + i0, rr_, m);
   }
+  // the max was taken over binary32 bit patterns; return it as a binary64 key
+  if constexpr (UR != P64) mx = abs_key(__uint_as_float((unsigned)mx));
 }
 
-__global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st) {
+// h_next / has_next: the SWITCH handle of the next iteration in the loop
+// graph, set here to the phase the selector chose (or AMPCG_PHASE_NONE).
+template <int UZ, int UR>
+__global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st,
+                                                cudaGraphConditionalHandle h_next, int has_next) {
   if (st->done) return;
-  const int uz = st->uz, ur = st->ur;
+  if (phase_mismatch(st, UZ, UR)) return;
   double rr = 0.0;
+  Dot2 d2;
   unsigned long long mx = 0ull;
-  if (ur == P64) {
-    if (uz == P64) update_rows<P64, P64, 8>(B, n, st, rr, mx);
-    else if (uz == P32) update_rows<P32, P64, 8>(B, n, st, rr, mx);
-    else update_rows<P16, P64, 8>(B, n, st, rr, mx);
+  update_rows<UZ, UR, 8>(B, n, st, rr, d2, mx);
+  double v[1];
+  if constexpr (UR != P64) {
+    v[0] = block_sum_dot2(d2, st->inv_sig2);
   } else {
-    if (uz == P64) update_rows<P64, P32, 8>(B, n, st, rr, mx);
-    else if (uz == P32) update_rows<P32, P32, 8>(B, n, st, rr, mx);
-    else update_rows<P16, P32, 8>(B, n, st, rr, mx);
+    v[0] = rr;
+    block_sum<1>(v);
   }
-  double v[1] = {rr};
-  block_sum<1>(v);
   mx = block_max(mx);
   if (threadIdx.x == 0) {
     B.part[blockIdx.x] = v[0];
@@ -644,11 +735,25 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st)
     } else {
       decide(st);
     }
+    if (has_next) cudaGraphSetConditional(h_next, st->done ? AMPCG_PHASE_NONE : 2 * st->uz + st->ur);
   }
 }
 
-// Sets the while-loop condition of the device-side iteration loop.
+// Sets the SWITCH value of the first iteration of a loop-graph body.
+__global__ void k_phase(DevState* st, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, st->done ? AMPCG_PHASE_NONE : 2 * st->uz + st->ur);
+}
+
+// Sets the while-loop condition of the device-side iteration loop.  A body
+// that ends without the iteration counter having advanced (which the
+// dispatch never produces) stops the solve with an internal error, so the
+// loop always ends within maxit bodies.
 __global__ void k_loop_ctl(DevState* st, cudaGraphConditionalHandle h) {
+  if (!st->done && st->k == st->k_body) {
+    st->status = ST_INTERNAL;
+    st->done = 1;
+  }
+  st->k_body = st->k;
   cudaGraphSetConditional(h, st->done ? 0u : 1u);
 }
 
@@ -776,21 +881,35 @@ __global__ void k_slice_width(int64_t n, int64_t nslices, const int* rowlen, int
   width[s] = w;
 }
 
-// Exclusive scan of 32 * width into off (one block; chunked sequential scan).
+// Exclusive scan of 32 * width into off (one block; chunked sequential scan);
+// total[0] = stored entries, total[1] = largest width.
 __global__ void k_slice_offsets(int64_t nslices, const int* width, long long* off,
                                 long long* total) {
   __shared__ long long sh[1024];
+  __shared__ int shw[1024];
   int t = threadIdx.x, T = blockDim.x;
   int64_t chunk = (nslices + T - 1) / T;
   int64_t a = t * chunk, b = a + chunk < nslices ? a + chunk : nslices;
   long long s = 0;
-  for (int64_t i = a; i < b; ++i) s += 32ll * width[i];
+  int wmax = 0;
+  for (int64_t i = a; i < b; ++i) {
+    s += 32ll * width[i];
+    wmax = width[i] > wmax ? width[i] : wmax;
+  }
   sh[t] = s;
+  shw[t] = wmax;
   __syncthreads();
   if (t == 0) {
     long long run = 0;
-    for (int j = 0; j < T; ++j) { long long v = sh[j]; sh[j] = run; run += v; }
-    *total = run;
+    int m = 0;
+    for (int j = 0; j < T; ++j) {
+      long long v = sh[j];
+      sh[j] = run;
+      run += v;
+      m = shw[j] > m ? shw[j] : m;
+    }
+    total[0] = run;
+    total[1] = m;
   }
   __syncthreads();
   long long run = sh[t];
@@ -861,7 +980,8 @@ __global__ void __launch_bounds__(256) k_residual_step(Sell A, const double* b, 
 template <int UZ, int UR, int MT>
 __global__ void __launch_bounds__(256) k_precond_step(Bufs B, int64_t n, const DevState* st) {
   double rho = 0.0;
-  precond_rows<UZ, UR, MT, 1>(B, n, st, rho);
+  Dot2 d2;
+  precond_rows<UZ, UR, MT, 1>(B, n, st, rho, d2);
 }
 
 // Selector replay over a residual-norm sequence (one thread).
