@@ -103,6 +103,7 @@ struct ampcg_ctx {
   int g_elem = 1, g_rows = 1, g_max = 1;
   const void* fn[6][4] = {};  // iteration kernels per phase (2 u_z + u_r)
   int grid[6][4] = {};        // their grids (occupancy-limited, 8 elements per thread)
+  int smem[6][4] = {};        // their dynamic shared memory (staged SpMV)
   // device-side loop graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -156,9 +157,9 @@ static void release(ampcg_ctx* c) {
   delete c;
 }
 
-static int occ_grid(const void* kern, int sms, int64_t work_threads) {
+static int occ_grid(const void* kern, int sms, int64_t work_threads, int smem = 0) {
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem) != cudaSuccess) {
     cudaGetLastError();
     per_sm = 4;
   }
@@ -355,8 +356,16 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   if (c->mtype == M_NONE) { if (c->idx16) fill_phase_table<M_NONE, 1>(c); else fill_phase_table<M_NONE, 0>(c); }
   else { if (c->idx16) fill_phase_table<M_JACOBI, 1>(c); else fill_phase_table<M_JACOBI, 0>(c); }
   for (int ph = 0; ph < 6; ++ph)
-    for (int j = 0; j < 4; ++j)
-      c->grid[ph][j] = occ_grid(c->fn[ph][j], sms, j == 2 ? (c->nslices * 32 + 1) / 2 : nvec);
+    for (int j = 0; j < 4; ++j) {
+      if (c->smem[ph][j] > 0)  // static + dynamic may exceed the default 48 KB
+        CTRY(cudaFuncSetAttribute(c->fn[ph][j], cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem[ph][j]));
+      c->grid[ph][j] = occ_grid(c->fn[ph][j], sms, j == 2 ? c->nslices * 32 : nvec, c->smem[ph][j]);
+      // staged SpMV: a warp takes at most 32 slices, so at least nslices/32 warps
+      if (j == 2 && c->smem[ph][j] > 0) {
+        int need = (int)((c->nslices + 32 * 8 - 1) / (32 * 8));
+        if (c->grid[ph][j] < need) c->grid[ph][j] = need;
+      }
+    }
   c->g_elem = occ_grid((const void*)k_refresh, sms, n);
   c->g_rows = occ_grid(c->idx16 ? (const void*)k_true_residual<1> : (const void*)k_true_residual<0>, sms,
                        rows_pad);
@@ -462,6 +471,11 @@ static void fill_phase_table(ampcg_ctx* c) {
                          AMPCG_PHASE_FNS(P16, P64), AMPCG_PHASE_FNS(P16, P32)};
 #undef AMPCG_PHASE_FNS
   memcpy(c->fn, t, sizeof(t));
+  const int sm64 = staged_smem_bytes<P64, IT>(), sm32 = staged_smem_bytes<P32, IT>();
+  for (int ph = 0; ph < 6; ++ph) {
+    for (int j = 0; j < 4; ++j) c->smem[ph][j] = 0;
+    if (c->maxw <= kStageW) c->smem[ph][2] = (ph % 2 == P64) ? sm64 : sm32;
+  }
 }
 
 struct PhaseArgs {
@@ -492,20 +506,21 @@ static cudaError_t launch_phase(ampcg_ctx* c, int ph, cudaStream_t s, cudaEvent_
       cudaError_t e = cudaEventRecord(ev[j], s);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaLaunchKernel(c->fn[ph][j], dim3(c->grid[ph][j]), dim3(kBlock), pa.args(j), 0, s);
+    cudaError_t e = cudaLaunchKernel(c->fn[ph][j], dim3(c->grid[ph][j]), dim3(kBlock), pa.args(j),
+                                     (size_t)c->smem[ph][j], s);
     if (e != cudaSuccess) return e;
   }
   return ev ? cudaEventRecord(ev[4], s) : cudaSuccess;
 }
 
 static cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* dep,
-                                   const void* fn, int grid, int block, void** args) {
+                                   const void* fn, int grid, int block, void** args, int smem = 0) {
   cudaKernelNodeParams p;
   memset(&p, 0, sizeof(p));
   p.func = (void*)fn;
   p.gridDim = dim3(grid);
   p.blockDim = dim3(block);
-  p.sharedMemBytes = 0;
+  p.sharedMemBytes = (unsigned)smem;
   p.kernelParams = args;
   p.extra = nullptr;
   return cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &p);
@@ -555,7 +570,7 @@ static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
       for (int j = 0; j < 4; ++j) {
         cudaGraphNode_t nn;
         CUDA_TRY(add_kernel_node(&nn, pg, j ? &kn : nullptr, c->fn[ph][j], c->grid[ph][j], kBlock,
-                                 pa.args(j)));
+                                 pa.args(j), c->smem[ph][j]));
         kn = nn;
       }
     }

@@ -539,6 +539,113 @@ __global__ void __launch_bounds__(256) k_axpy(Bufs B, int64_t n, DevState* st) {
 // ---------------------------------------------------------------------------
 // Alg. 3 lines 12-14: q_k = A p_k in u_r, gamma_k = q_k^T p_k (FP64),
 // alpha_k = rho_k / gamma_k.  One thread per row of a warp's slice.
+// ---------------------------------------------------------------------------
+// Staged SpMV.  The matrix stream (values and column indices) is the bulk of
+// the bytes; a warp owns a contiguous run of at most 32 slices (the launch
+// guarantees it) whose data is one contiguous region, and copies it into
+// shared memory with a K-stage cp.async pipeline (16-byte copies through L2
+// only), so K-1 slices are in flight while the current slice's gathers and
+// fmas run.  cp.async.wait_group is a hardware wait, not a spin loop.  Every
+// copy is 16-byte aligned: slice offsets are multiples of 32 entries and a
+// slice holds 32 * width entries.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kStageW = 8;  // widest slice the staged path takes
+template <int UR> struct StageCfg { static constexpr int K = (UR == P64) ? 3 : 4; };
+template <int IT> struct IdxT;
+template <> struct IdxT<0> { using T = int; };
+template <> struct IdxT<1> { using T = short; };
+
+// Shared-memory bytes per block of 256 threads for the staged SpMV.
+template <int UR, int IT>
+constexpr int staged_smem_bytes() {
+  return 8 * StageCfg<UR>::K * 32 * kStageW *
+         (int)(sizeof(typename Store<UR>::T) + sizeof(typename IdxT<IT>::T));
+}
+
+template <int UZ, int UR, int IT>
+__device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, const DevState* st,
+                                                 double& gam, Dot2& d2, unsigned char* smem) {
+  using TZ = typename Store<UZ>::T;
+  using TR = typename Store<UR>::T;
+  using TI = typename IdxT<IT>::T;
+  constexpr int K = StageCfg<UR>::K;
+  constexpr int SE = 32 * kStageW;  // entries per stage
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+  const TZ* __restrict__ p = (const TZ*)(st->pcur ? B.p[0] : B.p[1]);
+  TR* __restrict__ q = (TR*)B.q;
+  const TR* __restrict__ va = mat_vals<UR>(A);
+  const TI* __restrict__ ia = IT ? (const TI*)A.coff : (const TI*)A.cabs;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  TR* sv = (TR*)(smem + (size_t)wib * K * SE * (sizeof(TR) + sizeof(TI)));
+  TI* si = (TI*)(sv + K * SE);
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t spw = (A.nslices + nw - 1) / nw;
+  const int64_t s0 = gw * spw;
+  const int cnt = (int)(s0 >= A.nslices ? 0 : (s0 + spw < A.nslices ? spw : A.nslices - s0));
+  if (cnt <= 0) return;
+  long long hoff = 0;
+  int hw = 0;
+  if (lane < cnt) {
+    hoff = __ldg(A.off + s0 + lane);
+    hw = __ldg(A.width + s0 + lane);
+  }
+  auto issue = [&](int t) {
+    if (t < cnt) {
+      const long long o = __shfl_sync(0xffffffffu, hoff, t);
+      const int w = __shfl_sync(0xffffffffu, hw, t);
+      const int stg = t % K;
+      const char* gv = (const char*)(va + o);
+      char* dv = (char*)(sv + stg * SE);
+      const int nv = (32 * w * (int)sizeof(TR)) / 16;
+      for (int c = lane; c < nv; c += 32) cp_async16(dv + 16 * c, gv + 16 * c);
+      const char* gi = (const char*)(ia + o);
+      char* di = (char*)(si + stg * SE);
+      const int ni = (32 * w * (int)sizeof(TI)) / 16;
+      for (int c = lane; c < ni; c += 32) cp_async16(di + 16 * c, gi + 16 * c);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int t = 0; t < K - 1; ++t) issue(t);
+  for (int t = 0; t < cnt; ++t) {
+    issue(t + K - 1);
+    cp_async_wait<K - 1>();
+    __syncwarp();
+    const int w = __shfl_sync(0xffffffffu, hw, t);
+    const int64_t row = (s0 + t) * 32 + lane;
+    if (row < A.n) {
+      const TR* sa = sv + (t % K) * SE + lane;
+      const TI* sc = si + (t % K) * SE + lane;
+      TR a[kStageW];
+      int c[kStageW];
+#pragma unroll
+      for (int j = 0; j < kStageW; ++j) {
+        if (j < w) {
+          a[j] = sa[32 * j];
+          c[j] = IT ? (int)row + (int)sc[32 * j] : (int)sc[32 * j];
+        }
+      }
+      TR acc = (TR)0;
+#pragma unroll
+      for (int j = 0; j < kStageW; ++j)
+        if (j < w) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(p[c[j]]), acc);
+      q[row] = acc;
+      if constexpr (kSmall) d2.add((float)acc, (float)p[row]);
+      else gam = fma(to_f64(acc), to_f64(p[row]), gam);
+    }
+    __syncwarp();  // the stage is refilled by the next trip's issue
+  }
+  cp_async_wait<0>();
+}
+
 // Each warp owns a contiguous run of slices; it loads the headers (offset,
 // width) of up to 32 slices with one coalesced load and hands them out by
 // shuffle, so a slice costs two dependent memory round trips (entries, then
@@ -598,13 +705,17 @@ __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const De
   }
 }
 
+// Launched with staged_smem_bytes<UR, IT>() of dynamic shared memory when
+// every slice is at most kStageW wide (staged path), else with none.
 template <int UZ, int UR, int IT>
 __global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   if (st->done) return;
   if (phase_mismatch(st, UZ, UR)) return;
   double gam = 0.0;
   Dot2 d2;
-  spmv_rows<UZ, UR, IT>(A, B, st, gam, d2);
+  if (A.maxw <= kStageW) spmv_rows_staged<UZ, UR, IT>(A, B, st, gam, d2, dsm);
+  else spmv_rows<UZ, UR, IT>(A, B, st, gam, d2);
   double v[1];
   if constexpr ((UR != P64) && (UZ != P64)) {
     v[0] = block_sum_dot2(d2, 1.0);
