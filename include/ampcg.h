@@ -132,6 +132,14 @@ ampcg_status ampcg_create_csr(ampcg_t* out, int64_t n, int64_t nnz, const int32_
 /* Releases every resource of the context (NULL is ignored). */
 void ampcg_destroy(ampcg_t ctx);
 
+/* Replaces the matrix values, keeping the sparsity pattern given at creation:
+ * vals[nnz] FP64 in the same CSR order (host or device).  Rebuilds the FP64
+ * and FP32 copies and the Jacobi inverse diagonal on the device.  Returns
+ * AMPCG_ERR_NONFINITE / AMPCG_ERR_NOT_SPD if a value is not finite or a
+ * diagonal entry is not positive (the context then holds the new values and
+ * must not be solved with).  Synchronises the context's stream. */
+ampcg_status ampcg_update_values(ampcg_t ctx, const double* vals);
+
 /* Solves A x = b with AMP-PCG (Alg. 3; Alg. 1 and Alg. 2 under the FIXED
  * criterion).  b[n] FP64 (device or host); x[n] FP64 (device or host), in:
  * x_0, out: the final iterate.  tol > 0: stop when ||r_{k+1}|| <= tol ||b||
@@ -163,6 +171,39 @@ typedef struct {
 ampcg_status ampcg_solve_timed(ampcg_t ctx, const double* b, double* x, double tol, int maxit,
                                const ampcg_policy* policy, ampcg_result* res,
                                ampcg_kernel_times* kt);
+
+/* Adjoint of the solve x = A^-1 b for a scalar loss L(x): given x (the
+ * forward solution) and g = dL/dx, solves A lambda = g (A is symmetric, Sec. 2)
+ * with the same AMP-PCG and policy, from lambda_0 = 0, so lambda = dL/db; and
+ * if dLdA_vals is not NULL writes dL/da_ij = -lambda_i x_j for every stored
+ * entry, in the CSR order given at creation (nnz values).  x, dLdx, lambda,
+ * dLdA_vals: FP64, host or device.  Status as ampcg_solve.  The paper has no
+ * adjoint; this is the standard adjoint identity dL/dA = -lambda x^T
+ * restricted to the pattern.  Synchronises the context's stream. */
+ampcg_status ampcg_adjoint(ampcg_t ctx, const double* x, const double* dLdx, double tol, int maxit,
+                           const ampcg_policy* policy, double* lambda, double* dLdA_vals,
+                           ampcg_result* res);
+
+/* Log-coefficient field on the matrix graph.  For a pattern whose stored
+ * off-diagonals are the faces (i, j) of a node graph, sets
+ *   a_ij = -exp((theta_i + theta_j)/2),
+ *   a_ii = sum_{j != i} exp((theta_i + theta_j)/2) + nbound_i exp(theta_i)
+ * (a 7-point diffusion operator with face coefficients exp of the mean log
+ * coefficient, nbound_i = number of Dirichlet boundary faces of node i), and
+ * rebuilds the value copies and the Jacobi diagonal.  theta[n] FP64,
+ * nbound[n] int32, host or device.  Every row must store its diagonal
+ * (AMPCG_ERR_INVALID_ARG otherwise).  Not from the paper (coefficient-field
+ * workloads for the adjoint).  Synchronises the context's stream. */
+ampcg_status ampcg_assemble_log_coeff(ampcg_t ctx, const double* theta, const int32_t* nbound);
+
+/* Chain rule to the log-coefficient field for the current values: with x
+ * the forward solution and lambda the adjoint solution (ampcg_adjoint),
+ * writes dL/dtheta_i = sum_{j != i} -(lambda_i - lambda_j)(x_i - x_j)(-a_ij)/2
+ * - lambda_i x_i (sum_j a_ij), which is dL/da_ij = -lambda_i x_j pushed
+ * through ampcg_assemble_log_coeff's formula.  FP64 arrays of length n, host
+ * or device.  Synchronises the context's stream. */
+ampcg_status ampcg_grad_log_coeff(ampcg_t ctx, const double* x, const double* lambda,
+                                  double* dLdtheta);
 
 /* --- Single steps of the iteration, on device arrays of length n ---------- */
 

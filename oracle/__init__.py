@@ -97,6 +97,7 @@ def _load():
         lib.oracle_scale_precond.restype = C.c_int
         lib.oracle_scale_precond.argtypes = [i64, ip, ip, dp, C.c_int, C.c_int, C.c_int, C.c_double,
                                              dp, dp]
+        lib.oracle_grad_log_coeff.argtypes = [i64, ip, ip, dp, dp, dp, dp]
         lib.oracle_cheb_apply_public.restype = C.c_int
         lib.oracle_cheb_apply_public.argtypes = [i64, i64, ip, ip, dp, dp, C.c_int, C.c_double,
                                                  C.c_double, C.c_int, dp, dp]
@@ -207,6 +208,15 @@ def scale_precond(rowptr, col, val, mtype, uz, ur, omega, r):
     st = _load().oracle_scale_precond(n, _i(rowptr), _i(col), _d(val), mtype, uz, ur, omega, _d(r), _d(z))
     assert st == 0
     return z
+
+
+def grad_log_coeff(rowptr, col, val, x, lam):
+    """dL/dtheta for the log-coefficient field from x and the adjoint lambda."""
+    rowptr, col, val, x, lam = _i32(rowptr), _i32(col), _f64(val), _f64(x), _f64(lam)
+    n = rowptr.size - 1
+    out = np.empty(n)
+    _load().oracle_grad_log_coeff(n, _i(rowptr), _i(col), _d(val), _d(x), _d(lam), _d(out))
+    return out
 
 
 def scale(mode, delta, maxabs):

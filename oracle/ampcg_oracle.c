@@ -660,3 +660,28 @@ void oracle_selector_trace(const double* delta, int m, double nb, double tol,
     uz_prev = uz; ur_prev = ur;
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint gradient for the log-coefficient field (coefficient-field
+ * workloads): with A x = b solved and A lambda = dL/dx, dL/da_ij = -lambda_i x_j;
+ * pushing it through a_ij = -exp((th_i+th_j)/2) (i != j) and
+ * a_ii = sum_{j != i} exp((th_i+th_j)/2) + nb_i exp(th_i) gives, per node,
+ *   dL/dth_i = sum_{j != i} dL/dk_ij * k_ij/2 + dL/da_ii * nb_i exp(th_i),
+ *   dL/dk_ij = dL/da_ii + dL/da_jj - dL/da_ij - dL/da_ji
+ *            = -(lambda_i - lambda_j)(x_i - x_j),
+ * with k_ij = -a_ij and nb_i exp(th_i) = sum_j a_ij.  Plain loops.          */
+void oracle_grad_log_coeff(int64_t n, const int32_t* rowptr, const int32_t* col,
+                           const double* val, const double* x, const double* lam,
+                           double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double g = 0.0, rowsum = 0.0;
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      int32_t j = col[k];
+      rowsum = rowsum + val[k];
+      if (j == i) continue;
+      double dk = -((lam[i] - lam[j]) * (x[i] - x[j]));
+      g = g + dk * (-val[k]) * 0.5;
+    }
+    out[i] = g + (-(lam[i] * x[i])) * rowsum;
+  }
+}

@@ -92,6 +92,15 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_solve_timed.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(PolicyC),
                                       C.POINTER(ResultC), C.POINTER(KernelTimesC)]
     lib.ampcg_solve_timed.restype = C.c_int
+    lib.ampcg_update_values.argtypes = [vp, vp]
+    lib.ampcg_update_values.restype = C.c_int
+    lib.ampcg_adjoint.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(PolicyC), vp, vp,
+                                  C.POINTER(ResultC)]
+    lib.ampcg_adjoint.restype = C.c_int
+    lib.ampcg_assemble_log_coeff.argtypes = [vp, vp, vp]
+    lib.ampcg_assemble_log_coeff.restype = C.c_int
+    lib.ampcg_grad_log_coeff.argtypes = [vp, vp, vp, vp]
+    lib.ampcg_grad_log_coeff.restype = C.c_int
     lib.ampcg_spmv.argtypes = [vp, C.c_int, vp, vp]
     lib.ampcg_spmv.restype = C.c_int
     lib.ampcg_precond_apply.argtypes = [vp, C.c_int, C.c_int, C.c_double, vp, vp]
@@ -273,6 +282,46 @@ class Solver:
                                     for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
             info.kernel_total_ms = kt.total_ms
         return x, info
+
+    def update_values(self, vals):
+        """New FP64 values on the same pattern, CSR order (ampcg_update_values)."""
+        _check(load_library().ampcg_update_values(self._h, _ptr(vals)))
+
+    def adjoint(self, x, dLdx, tol: float = 1e-10, maxit: int = 2000, policy: Policy | None = None,
+                want_dA: bool = True):
+        """Adjoint solve A lambda = dL/dx (ampcg_adjoint): returns (lambda = dL/db,
+        dL/dA on the pattern in CSR order or None, info)."""
+        like = dLdx
+        if isinstance(like, np.ndarray):
+            lam = np.zeros(self.n)
+            dA = np.zeros(self.nnz) if want_dA else None
+        else:
+            import torch
+            lam = torch.zeros_like(like)
+            dA = torch.zeros(self.nnz, dtype=like.dtype, device=like.device) if want_dA else None
+        pol = (policy or Policy()).to_c()
+        res = ResultC()
+        s = load_library().ampcg_adjoint(self._h, _ptr(x), _ptr(dLdx), tol, maxit, C.byref(pol),
+                                         _ptr(lam), _ptr(dA) if want_dA else None, C.byref(res))
+        _check(s, (OK, NOT_CONVERGED))
+        info = SolveInfo(res.status, res.iters, bool(res.converged), res.refreshes, res.true_relres,
+                         res.updated_relres, tuple(res.switch_iter), res.seconds, res.kernel_launches)
+        return lam, dA, info
+
+    def assemble_log_coeff(self, theta, nbound):
+        """Values from a log-coefficient field (ampcg_assemble_log_coeff)."""
+        _check(load_library().ampcg_assemble_log_coeff(self._h, _ptr(theta), _ptr(nbound)))
+
+    def grad_log_coeff(self, x, lam, out=None):
+        """dL/dtheta from the forward solution and the adjoint (ampcg_grad_log_coeff)."""
+        if out is None:
+            if isinstance(x, np.ndarray):
+                out = np.zeros(self.n)
+            else:
+                import torch
+                out = torch.zeros_like(x)
+        _check(load_library().ampcg_grad_log_coeff(self._h, _ptr(x), _ptr(lam), _ptr(out)))
+        return out
 
     def spmv(self, p, q, prec: int = FP64):
         """q = A p in FP64 or FP32 (device arrays)."""

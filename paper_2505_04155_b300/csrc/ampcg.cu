@@ -78,6 +78,7 @@ struct ampcg_ctx {
   int maxw = 0;   // largest slice width
   int mtype = M_JACOBI;
   // matrix
+  int* rowptr = nullptr;  // CSR row pointer (maps sliced entries to CSR order)
   long long* off = nullptr;
   int* width = nullptr;
   int* cabs = nullptr;
@@ -146,7 +147,7 @@ static void release(ampcg_ctx* c) {
   if (!c) return;
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
-  void* ptrs[] = {c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
+  void* ptrs[] = {c->rowptr, c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
                   c->dinv16, c->x, c->b, c->r64, c->t, c->r32, c->z, c->p0, c->p1, c->q,
                   c->part, c->pmax, c->st, c->dhist, c->rhist, c->phist};
   for (void* p : ptrs)
@@ -286,6 +287,8 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
     if (nnz) CTRY(cudaMemcpyAsync(t_v, vals, nnz * sizeof(double), cudaMemcpyHostToDevice, s));
     d_v = t_v;
   }
+  TRY(dalloc(&c->rowptr, n + 1));
+  CTRY(cudaMemcpyAsync(c->rowptr, d_rp, (n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, s));
   TRY(dalloc(&rowlen, n));
   TRY(dalloc(&diag, n));
   TRY(dalloc(&flags, 2));
@@ -1004,5 +1007,133 @@ extern "C" ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy,
   }
   if (e == cudaSuccess) e = cudaMemcpy(out, sc->out, (size_t)(m + 1), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "selector trace (no allocation): %s", cudaGetErrorString(e));
+  return AMPCG_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// New values on the same pattern, and the adjoint solve.
+
+extern "C" ampcg_status ampcg_update_values(ampcg_t c, const double* vals) {
+  if (!c || !vals) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = c->stream;
+  const double* d_v = vals;
+  double* t_v = nullptr;
+  int* flags = nullptr;
+  ampcg_status st = AMPCG_OK;
+  if (!is_device_ptr(vals)) {
+    if ((st = dalloc(&t_v, c->nnz)) != AMPCG_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(t_v, vals, c->nnz * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cudaFree(t_v); return fail(AMPCG_ERR_CUDA, "copy: %s", cudaGetErrorString(e)); }
+    d_v = t_v;
+  }
+  if ((st = dalloc(&flags, 1)) != AMPCG_OK) { if (t_v) cudaFree(t_v); return st; }
+  int hf = 0;
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int), s);
+  Sell A = c->sell();
+  if (e == cudaSuccess) {
+    if (c->idx16)
+      k_update_vals<1><<<c->g_rows, kBlock, 0, s>>>(A, c->rowptr, d_v, c->v64, c->v32, c->dinv64, c->dinv32, c->dinv16, flags);
+    else
+      k_update_vals<0><<<c->g_rows, kBlock, 0, s>>>(A, c->rowptr, d_v, c->v64, c->v32, c->dinv64, c->dinv32, c->dinv16, flags);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (t_v) cudaFree(t_v);
+  cudaFree(flags);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "update values: %s", cudaGetErrorString(e));
+  if (hf & 8) return fail(AMPCG_ERR_NONFINITE, "matrix has non-finite values (context now holds them)");
+  if (hf & 4) return fail(AMPCG_ERR_NOT_SPD, "a diagonal entry is not positive (context now holds it)");
+  return AMPCG_OK;
+}
+
+extern "C" ampcg_status ampcg_adjoint(ampcg_t c, const double* x, const double* dLdx, double tol,
+                                      int maxit, const ampcg_policy* policy, double* lambda,
+                                      double* dLdA_vals, ampcg_result* res) {
+  if (!c || !dLdx || !lambda) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  if (dLdA_vals && !x) return fail(AMPCG_ERR_INVALID_ARG, "x is needed for dL/dA");
+  cudaStream_t s = c->stream;
+  size_t vb = (size_t)c->n * sizeof(double);
+  // lambda starts from zero: A lambda = dL/dx with the same mixed-precision PCG (A = A^T)
+  bool l_dev = is_device_ptr(lambda);
+  if (l_dev) CUDA_TRY(cudaMemsetAsync(lambda, 0, vb, s));
+  else memset(lambda, 0, vb);
+  ampcg_status st = solve_impl(c, dLdx, lambda, tol, maxit, policy, res, nullptr);
+  if (st != AMPCG_OK && st != AMPCG_NOT_CONVERGED) return st;
+  if (!dLdA_vals) return st;
+  // the final iterate (lambda) is still in the context's x buffer; x goes to scratch t
+  bool x_dev = is_device_ptr(x), g_dev = is_device_ptr(dLdA_vals);
+  CUDA_TRY(cudaMemcpyAsync(c->t, x, vb, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  double* out = dLdA_vals;
+  double* tmp = nullptr;
+  if (!g_dev) {
+    ampcg_status as = dalloc(&tmp, c->nnz);
+    if (as != AMPCG_OK) return as;
+    out = tmp;
+  }
+  Sell A = c->sell();
+  if (c->idx16) k_grad_pattern<1><<<c->g_rows, kBlock, 0, s>>>(A, c->rowptr, c->x, c->t, out);
+  else k_grad_pattern<0><<<c->g_rows, kBlock, 0, s>>>(A, c->rowptr, c->x, c->t, out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && tmp)
+    e = cudaMemcpyAsync(dLdA_vals, tmp, c->nnz * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "adjoint gradient: %s", cudaGetErrorString(e));
+  return st;
+}
+
+
+// ---------------------------------------------------------------------------
+// Log-coefficient field: assembly A(theta) and the chain dL/dtheta.
+
+extern "C" ampcg_status ampcg_assemble_log_coeff(ampcg_t c, const double* theta, const int32_t* nbound) {
+  if (!c || !theta || !nbound) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = c->stream;
+  size_t vb = (size_t)c->n * sizeof(double);
+  double* d_t = nullptr;
+  int* d_nb = nullptr;
+  int* flags = nullptr;
+  ampcg_status st;
+  if ((st = dalloc(&d_t, c->n)) != AMPCG_OK) return st;
+  if ((st = dalloc(&d_nb, c->n)) != AMPCG_OK) { cudaFree(d_t); return st; }
+  if ((st = dalloc(&flags, 1)) != AMPCG_OK) { cudaFree(d_t); cudaFree(d_nb); return st; }
+  cudaError_t e = cudaMemcpyAsync(d_t, theta, vb, is_device_ptr(theta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_nb, nbound, c->n * sizeof(int), is_device_ptr(nbound) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), s);
+  Sell A = c->sell();
+  if (e == cudaSuccess) {
+    if (c->idx16) k_assemble_logcoeff<1><<<c->g_rows, kBlock, 0, s>>>(A, d_t, d_nb, c->v64, c->v32, c->dinv64, c->dinv32, c->dinv16, flags);
+    else k_assemble_logcoeff<0><<<c->g_rows, kBlock, 0, s>>>(A, d_t, d_nb, c->v64, c->v32, c->dinv64, c->dinv32, c->dinv16, flags);
+    e = cudaGetLastError();
+  }
+  int hf = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_t);
+  cudaFree(d_nb);
+  cudaFree(flags);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "assemble: %s", cudaGetErrorString(e));
+  if (hf & 4) return fail(AMPCG_ERR_INVALID_ARG, "a row has no stored diagonal entry");
+  return AMPCG_OK;
+}
+
+extern "C" ampcg_status ampcg_grad_log_coeff(ampcg_t c, const double* x, const double* lambda,
+                                             double* dLdtheta) {
+  if (!c || !x || !lambda || !dLdtheta) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = c->stream;
+  size_t vb = (size_t)c->n * sizeof(double);
+  // x -> scratch t, lambda -> scratch r64, result -> b-sized scratch (q buffer)
+  CUDA_TRY(cudaMemcpyAsync(c->t, x, vb, is_device_ptr(x) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->r64, lambda, vb, is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  double* out = (double*)c->q;
+  Sell A = c->sell();
+  if (c->idx16) k_grad_logcoeff<1><<<c->g_rows, kBlock, 0, s>>>(A, c->t, c->r64, out);
+  else k_grad_logcoeff<0><<<c->g_rows, kBlock, 0, s>>>(A, c->t, c->r64, out);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(dLdtheta, out, vb, is_device_ptr(dLdtheta) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
   return AMPCG_OK;
 }

@@ -1059,6 +1059,135 @@ __global__ void k_jacobi(int64_t n, const double* diag, double* d64, float* d32,
   d16[i] = d2h(v);
 }
 
+// New values on the same pattern: vals in CSR order (rowptr on the device),
+// written into the sliced layout (FP64 and FP32 copies) with the Jacobi
+// inverse diagonal.  flags bit 2: diagonal <= 0; bit 3: non-finite value.
+template <int IT>
+__global__ void k_update_vals(Sell A, const int* rowptr, const double* vals, double* v64, float* v32,
+                              double* d64, float* d32, __half* d16, int* flags) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row >= A.n) continue;
+    long long base = A.off[s] + lane;
+    int a = rowptr[row], len = rowptr[row + 1] - a;
+    double dg = 0.0;
+    int f = 0;
+    for (int j = 0; j < len; ++j) {
+      long long e = base + 32ll * j;
+      double v = vals[a + j];
+      if (!isfinite(v)) f |= 8;
+      v64[e] = v;
+      v32[e] = __double2float_rn(v);
+      if (col_at<IT>(A, e, row) == row) dg = v;
+    }
+    if (!(dg > 0.0)) f |= 4;
+    if (f) atomicOr(flags, f);
+    double di = 1.0 / dg;
+    d64[row] = di;
+    d32[row] = __double2float_rn(di);
+    d16[row] = d2h(di);
+  }
+}
+
+// dL/dA on the pattern (adjoint of A x = b): dLdA[rowptr[i] + j] = -lambda_i x_c
+// for the j-th stored entry (column c) of row i, in the caller's CSR order.
+template <int IT>
+__global__ void k_grad_pattern(Sell A, const int* rowptr, const double* lam, const double* x,
+                               double* dLdA) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row >= A.n) continue;
+    long long base = A.off[s] + lane;
+    int a = rowptr[row], len = rowptr[row + 1] - a;
+    double li = lam[row];
+    for (int j = 0; j < len; ++j) {
+      int c = col_at<IT>(A, base + 32ll * j, row);
+      dLdA[a + j] = -(li * x[c]);
+    }
+  }
+}
+
+// Log-coefficient field on the matrix graph:
+//   a_ij = -exp((theta_i + theta_j)/2) for each stored off-diagonal (i, j),
+//   a_ii = sum_{j != i} exp((theta_i + theta_j)/2) + nb_i exp(theta_i)
+// (nb_i = number of boundary faces of node i).  Writes the FP64/FP32 copies
+// and the Jacobi inverse diagonal.  flags bit 2: no stored diagonal.
+template <int IT>
+__global__ void k_assemble_logcoeff(Sell A, const double* theta, const int* nb, double* v64,
+                                    float* v32, double* d64, float* d32, __half* d16, int* flags) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row >= A.n) continue;
+    long long base = A.off[s] + lane;
+    int w = A.width[s];
+    double ti = theta[row], sum = 0.0;
+    long long ed = -1;
+    for (int j = 0; j < w; ++j) {
+      long long e = base + 32ll * j;
+      int c = col_at<IT>(A, e, row);
+      if (c == row) {
+        if (ed < 0) ed = e;   // padding repeats (0, row) after the real entries
+        continue;
+      }
+      double kf = exp(0.5 * (ti + theta[c]));
+      sum += kf;
+      v64[e] = -kf;
+      v32[e] = __double2float_rn(-kf);
+    }
+    if (ed < 0) { atomicOr(flags, 4); continue; }
+    double dg = sum + (double)nb[row] * exp(ti);
+    v64[ed] = dg;
+    v32[ed] = __double2float_rn(dg);
+    double di = 1.0 / dg;
+    d64[row] = di;
+    d32[row] = __double2float_rn(di);
+    d16[row] = d2h(di);
+  }
+}
+
+// dL/dtheta for the log-coefficient field, from the forward solution x and
+// the adjoint lambda (A lambda = dL/dx): with dL/da_ij = -lambda_i x_j,
+//   dL/dtheta_i = sum_{j != i} -(lambda_i - lambda_j)(x_i - x_j) k_ij / 2
+//                 - lambda_i x_i kb_i,
+// k_ij = -a_ij and kb_i = nb_i exp(theta_i) = sum_j a_ij (the row sum).
+// One thread per row, ascending column order: deterministic.
+template <int IT>
+__global__ void k_grad_logcoeff(Sell A, const double* x, const double* lam, double* dtheta) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row >= A.n) continue;
+    long long base = A.off[s] + lane;
+    int w = A.width[s];
+    double xi = x[row], li = lam[row], g = 0.0, rowsum = 0.0;
+    bool seen_diag = false;
+    for (int j = 0; j < w; ++j) {
+      long long e = base + 32ll * j;
+      int c = col_at<IT>(A, e, row);
+      double a = A.v64[e];
+      if (c == row) {
+        if (!seen_diag) rowsum += a;   // padding repeats (0, row)
+        seen_diag = true;
+        continue;
+      }
+      rowsum += a;
+      g += -((li - lam[c]) * (xi - x[c])) * (-a) * 0.5;
+    }
+    dtheta[row] = g - li * xi * rowsum;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step entry points (single launches, no reduction).
 

@@ -102,7 +102,9 @@ def diffusion3d_from_field(g: np.ndarray) -> CSR:
         vals.append(-k)
     a = _assemble(n, cols, vals)
     kk = -a.val[a.val < 0]
-    a.info = {"kind": "diffusion3d", "shape": (nx, ny, nz),
+    # boundary faces per node: the 6 faces minus the interior neighbours
+    nbound = (6 - (np.diff(a.rowptr) - 1)).astype(np.int32)
+    a.info = {"kind": "diffusion3d", "shape": (nx, ny, nz), "nbound": nbound,
               "coef_min": float(kk.min()) if kk.size else 1.0,
               "coef_max": float(kk.max()) if kk.size else 1.0}
     a.info["contrast"] = a.info["coef_max"] / a.info["coef_min"]
@@ -173,3 +175,16 @@ def eigs_limitation(n: int, rho: float) -> np.ndarray:
     lam = 1e-3 + (i - 1) / (n - 1) * rho ** (n - i)
     lam[-1] = 1.0
     return lam
+
+
+def log_coeff_problem(n: int, sigma: float = 1.0, seed: int = 0, perturb: float = 0.1,
+                      seed_perturb: int = 2, seed_rhs: int = 1):
+    """Coefficient-field workload: theta a smoothed Gaussian node field (std
+    sigma), a target field theta_t = theta + perturb * (same generator, other
+    seed), the operator of diffusion3d_from_field and b ~ U[-1, 1]."""
+    theta = smooth_gaussian_field((n, n, n), sigma, seed)
+    theta_t = theta + perturb * smooth_gaussian_field((n, n, n), 1.0, seed_perturb)
+    a = diffusion3d_from_field(theta)
+    a_t = diffusion3d_from_field(theta_t)
+    b = rhs_uniform(a.n, seed_rhs)
+    return theta.reshape(-1), theta_t.reshape(-1), a, a_t, b
