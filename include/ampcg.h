@@ -54,11 +54,17 @@ typedef enum {
 /* Preconditioner M (Alg. 3 line 6 applies M^-1). */
 typedef enum { AMPCG_M_NONE = 0, AMPCG_M_JACOBI = 1, AMPCG_M_CHEBYSHEV = 2 } ampcg_m_type;
 
+/* Jacobi: M = diag(A).  Chebyshev: M^-1 = D^-1/2 P(Ahat) D^-1/2 with
+ * Ahat = D^-1/2 A D^-1/2 and P the polynomial of `degree` steps of the
+ * Chebyshev iteration for Ahat (Saad, Alg. 12.1) from zero on [lmin, lmax]
+ * (degree - 1 products with the copy of Ahat in u_z per application). */
 typedef struct {
   int type;        /* ampcg_m_type */
-  int degree;      /* Chebyshev: number of Chebyshev iterations m (>= 1) */
-  double lmin;     /* Chebyshev: interval [lmin, lmax] of D^-1/2 A D^-1/2;  */
-  double lmax;     /*   lmax <= 0 asks the library to estimate it           */
+  int degree;      /* Chebyshev: number of Chebyshev steps m, 1..64 */
+  double lmin;     /* Chebyshev: interval [lmin, lmax] for Ahat.  lmax <= 0:  */
+  double lmax;     /*   lmax = Gershgorin bound max_i sum_j |ahat_ij| (an upper */
+                   /*   bound of the spectrum, so M stays SPD); lmin <= 0:      */
+                   /*   lmin = lmax / 30                                        */
 } ampcg_precond_spec;
 
 /* Criterion for the u_r switch (Sec. 4.1). */
@@ -123,11 +129,15 @@ void ampcg_policy_default(ampcg_policy* p);
  * (AMPCG_ERR_INVALID_ARG, AMPCG_ERR_NOT_SPD), then builds on the device the
  * FP64 and FP32 copies of A in its internal sliced layout, the Jacobi inverse
  * diagonal in FP64/FP32/FP16 and, for Chebyshev, the FP64/FP32/FP16 copies of
- * D^-1/2 A D^-1/2.  cuda_stream: a cudaStream_t or NULL.  On success *out
+ * D^-1/2 A D^-1/2 and of D^-1/2.  cuda_stream: a cudaStream_t or NULL.  On success *out
  * owns device memory until ampcg_destroy. */
 ampcg_status ampcg_create_csr(ampcg_t* out, int64_t n, int64_t nnz, const int32_t* rowptr,
                               const int32_t* colind, const double* vals,
                               const ampcg_precond_spec* M, void* cuda_stream);
+
+/* The Chebyshev interval in use (after automatic choice).  Returns
+ * AMPCG_ERR_INVALID_ARG for other preconditioners. */
+ampcg_status ampcg_precond_interval(ampcg_t ctx, double* lmin, double* lmax);
 
 /* Releases every resource of the context (NULL is ignored). */
 void ampcg_destroy(ampcg_t ctx);

@@ -98,6 +98,9 @@ def _load():
         lib.oracle_scale_precond.argtypes = [i64, ip, ip, dp, C.c_int, C.c_int, C.c_int, C.c_double,
                                              dp, dp]
         lib.oracle_grad_log_coeff.argtypes = [i64, ip, ip, dp, dp, dp, dp]
+        lib.oracle_scale_cheb.restype = C.c_int
+        lib.oracle_scale_cheb.argtypes = [i64, ip, ip, dp, C.c_int, C.c_double, C.c_double, C.c_int,
+                                          C.c_int, C.c_double, dp, dp]
         lib.oracle_cheb_apply_public.restype = C.c_int
         lib.oracle_cheb_apply_public.argtypes = [i64, i64, ip, ip, dp, dp, C.c_int, C.c_double,
                                                  C.c_double, C.c_int, dp, dp]
@@ -206,6 +209,17 @@ def scale_precond(rowptr, col, val, mtype, uz, ur, omega, r):
     n = rowptr.size - 1
     z = np.empty(n)
     st = _load().oracle_scale_precond(n, _i(rowptr), _i(col), _d(val), mtype, uz, ur, omega, _d(r), _d(z))
+    assert st == 0
+    return z
+
+
+def scale_cheb(rowptr, col, val, degree, lmin, lmax, uz, ur, omega, r):
+    """Alg. 3 lines 5-6 with the Chebyshev preconditioner (reading R8)."""
+    rowptr, col, val, r = _i32(rowptr), _i32(col), _f64(val), _f64(r)
+    n = rowptr.size - 1
+    z = np.empty(n)
+    st = _load().oracle_scale_cheb(n, _i(rowptr), _i(col), _d(val), degree, lmin, lmax, uz, ur,
+                                   omega, _d(r), _d(z))
     assert st == 0
     return z
 

@@ -416,6 +416,26 @@ int oracle_scale_precond(int64_t n, const int32_t* rowptr, const int32_t* col,
   return OR_OK;
 }
 
+/* Same with the Chebyshev preconditioner (reading R8) built from A as in
+ * oracle_ampcg: z = D^-1/2 P(Ahat) D^-1/2 round_uz(omega r).              */
+int oracle_scale_cheb(int64_t n, const int32_t* rowptr, const int32_t* col,
+                      const double* val, int degree, double lmin, double lmax, int uz,
+                      int ur, double omega, const double* r, double* z) {
+  int64_t nnz = rowptr[n];
+  double* w = (double*)malloc(sizeof(double) * (size_t)(n * 7 + nnz));
+  if (!w) return OR_ERR_INVALID;
+  double *dg = w, *dsi = w + n, *y = w + 2 * n, *ah = w + 7 * n;
+  csr_diag(n, rowptr, col, val, dg);
+  for (int64_t i = 0; i < n; ++i) dsi[i] = 1.0 / sqrt(dg[i]);
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t kk = rowptr[i]; kk < rowptr[i + 1]; ++kk)
+      ah[kk] = dsi[i] * val[kk] * dsi[col[kk]];
+  scale_to_y(n, uz, ur, omega, r, y);
+  int st = oracle_cheb_apply_public(n, nnz, rowptr, col, ah, dsi, degree, lmin, lmax, uz, y, z);
+  free(w);
+  return st;
+}
+
 /* ------------------------------------------------------------------------ */
 /* PCG, Algorithm 1, native FP64, Jacobi or identity M.  Stops on the updated
  * residual ||r_{k+1}|| <= tol ||b||.  Returns iterations in res->iters.     */

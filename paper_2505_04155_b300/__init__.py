@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_solve_timed.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(PolicyC),
                                       C.POINTER(ResultC), C.POINTER(KernelTimesC)]
     lib.ampcg_solve_timed.restype = C.c_int
+    lib.ampcg_precond_interval.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.ampcg_precond_interval.restype = C.c_int
     lib.ampcg_update_values.argtypes = [vp, vp]
     lib.ampcg_update_values.restype = C.c_int
     lib.ampcg_adjoint.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(PolicyC), vp, vp,
@@ -282,6 +284,12 @@ class Solver:
                                     for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
             info.kernel_total_ms = kt.total_ms
         return x, info
+
+    def interval(self):
+        """The Chebyshev interval (lmin, lmax) in use (ampcg_precond_interval)."""
+        lo, hi = C.c_double(), C.c_double()
+        _check(load_library().ampcg_precond_interval(self._h, C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
 
     def update_values(self, vals):
         """New FP64 values on the same pattern, CSR order (ampcg_update_values)."""

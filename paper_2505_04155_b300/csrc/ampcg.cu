@@ -68,6 +68,16 @@ ampcg_status dalloc(T** p, size_t count) {
 
 }  // namespace
 
+// One kernel launch of an iteration: function, launch shape, argument list
+// kind, timing slot (0 precondition, 1 search direction, 2 SpMV, 3 update)
+// and, for a Chebyshev step, its index and constants.
+enum { KA_ELEM = 0, KA_SPMV, KA_UPD, KA_CINIT, KA_CSTEP, KA_CFINAL };
+struct Launch {
+  const void* fn;
+  int grid, smem, kind, slot, j;
+  double c1, c2;
+};
+
 struct ampcg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -102,9 +112,28 @@ struct ampcg_ctx {
   int hist_cap = 0;
   // launch shapes
   int g_elem = 1, g_rows = 1, g_max = 1;
-  const void* fn[6][4] = {};  // iteration kernels per phase (2 u_z + u_r)
-  int grid[6][4] = {};        // their grids (occupancy-limited, 8 elements per thread)
-  int smem[6][4] = {};        // their dynamic shared memory (staged SpMV)
+  // iteration kernels per phase (2 u_z + u_r), in launch order
+  std::vector<Launch> seq[6];
+  // Chebyshev preconditioner data (reading R8)
+  int cheb_m = 0;
+  int cheb_auto = 0;            // interval from the Gershgorin bound
+  double cheb_lmin = 0.0, cheb_lmax = 0.0, cheb_inv_theta = 0.0;
+  std::vector<double> cheb_c1, cheb_c2;  // per step j = 1..m-1
+  double* ah64 = nullptr;
+  float* ah32 = nullptr;
+  __half* ah16 = nullptr;
+  double* ds64 = nullptr;
+  float* ds32 = nullptr;
+  __half* ds16 = nullptr;
+  void *cres = nullptr, *cd0 = nullptr, *cd1 = nullptr, *cu = nullptr;
+  Cheb cheb() const {
+    Cheb C;
+    C.ah64 = ah64; C.ah32 = ah32; C.ah16 = ah16;
+    C.ds64 = ds64; C.ds32 = ds32; C.ds16 = ds16;
+    C.res = cres; C.d[0] = cd0; C.d[1] = cd1; C.u = cu;
+    C.inv_theta = cheb_inv_theta;
+    return C;
+  }
   // device-side loop graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -147,7 +176,8 @@ static void release(ampcg_ctx* c) {
   if (!c) return;
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
-  void* ptrs[] = {c->rowptr, c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
+  void* ptrs[] = {c->ah64, c->ah32, c->ah16, c->ds64, c->ds32, c->ds16, c->cres, c->cd0, c->cd1, c->cu,
+                  c->rowptr, c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
                   c->dinv16, c->x, c->b, c->r64, c->t, c->r32, c->z, c->p0, c->p1, c->q,
                   c->part, c->pmax, c->st, c->dhist, c->rhist, c->phist};
   for (void* p : ptrs)
@@ -227,8 +257,8 @@ void ampcg_destroy(ampcg_t c) {
 // ---------------------------------------------------------------------------
 // create
 
-template <int MT, int IT>
-static void fill_phase_table(ampcg_ctx* c);
+static ampcg_status build_sequences(ampcg_ctx* c, int sms);
+static ampcg_status cheb_prepare(ampcg_ctx* c);
 
 static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int32_t* rowptr,
                                 const int32_t* colind, const double* vals) {
@@ -355,27 +385,27 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   // launch shapes
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  int64_t nvec = (n + 7) / 8;
-  if (c->mtype == M_NONE) { if (c->idx16) fill_phase_table<M_NONE, 1>(c); else fill_phase_table<M_NONE, 0>(c); }
-  else { if (c->idx16) fill_phase_table<M_JACOBI, 1>(c); else fill_phase_table<M_JACOBI, 0>(c); }
-  for (int ph = 0; ph < 6; ++ph)
-    for (int j = 0; j < 4; ++j) {
-      if (c->smem[ph][j] > 0)  // static + dynamic may exceed the default 48 KB
-        CTRY(cudaFuncSetAttribute(c->fn[ph][j], cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem[ph][j]));
-      c->grid[ph][j] = occ_grid(c->fn[ph][j], sms, j == 2 ? c->nslices * 32 : nvec, c->smem[ph][j]);
-      // staged SpMV: a warp takes at most 32 slices, so at least nslices/32 warps
-      if (j == 2 && c->smem[ph][j] > 0) {
-        int need = (int)((c->nslices + 32 * 8 - 1) / (32 * 8));
-        if (c->grid[ph][j] < need) c->grid[ph][j] = need;
-      }
-    }
+  if (c->mtype == M_CHEBYSHEV) {
+    TRY(dalloc(&c->ah64, stored));
+    TRY(dalloc(&c->ah32, stored));
+    TRY(dalloc(&c->ah16, stored));
+    TRY(dalloc(&c->ds64, npad));
+    TRY(dalloc(&c->ds32, npad));
+    TRY(dalloc(&c->ds16, npad));
+    TRY(dalloc(&tmp, npad)); c->cres = tmp;
+    TRY(dalloc(&tmp, npad)); c->cd0 = tmp;
+    TRY(dalloc(&tmp, npad)); c->cd1 = tmp;
+    TRY(dalloc(&tmp, npad)); c->cu = tmp;
+    TRY(cheb_prepare(c));
+  }
+  TRY(build_sequences(c, sms));
   c->g_elem = occ_grid((const void*)k_refresh, sms, n);
   c->g_rows = occ_grid(c->idx16 ? (const void*)k_true_residual<1> : (const void*)k_true_residual<0>, sms,
                        rows_pad);
   c->g_max = c->g_elem > c->g_rows ? c->g_elem : c->g_rows;
   for (int ph = 0; ph < 6; ++ph)
-    for (int j = 0; j < 4; ++j)
-      if (c->grid[ph][j] > c->g_max) c->g_max = c->grid[ph][j];
+    for (const Launch& L : c->seq[ph])
+      if (L.grid > c->g_max) c->g_max = L.grid;
   int gi = occ_grid((const void*)k_init<0>, sms, rows_pad);
   if (gi > c->g_max) c->g_max = gi;
   TRY(dalloc(&c->part, (size_t)c->g_max * 4));
@@ -407,16 +437,24 @@ extern "C" ampcg_status ampcg_create_csr(ampcg_t* out, int64_t n, int64_t nnz,
   if (!rowptr || (nnz > 0 && (!colind || !vals)))
     return fail(AMPCG_ERR_INVALID_ARG, "NULL CSR array");
   int mtype = M ? M->type : AMPCG_M_JACOBI;
-  if (mtype != AMPCG_M_NONE && mtype != AMPCG_M_JACOBI) {
-    if (mtype == AMPCG_M_CHEBYSHEV)
-      return fail(AMPCG_ERR_UNSUPPORTED, "Chebyshev preconditioner is not available in this build");
+  if (mtype != AMPCG_M_NONE && mtype != AMPCG_M_JACOBI && mtype != AMPCG_M_CHEBYSHEV)
     return fail(AMPCG_ERR_INVALID_ARG, "unknown preconditioner type %d", mtype);
+  if (mtype == AMPCG_M_CHEBYSHEV) {
+    if (M->degree < 1 || M->degree > 64) return fail(AMPCG_ERR_INVALID_ARG, "Chebyshev degree must be in [1, 64]");
+    if (M->lmax > 0.0 && !(M->lmin > 0.0 && M->lmin < M->lmax) && M->lmin != 0.0)
+      return fail(AMPCG_ERR_INVALID_ARG, "Chebyshev interval needs 0 < lmin < lmax (or lmin = 0)");
   }
   ampcg_ctx* c = new ampcg_ctx();
   cudaGetDevice(&c->device);
   c->n = n;
   c->nnz = nnz;
   c->mtype = mtype;
+  if (mtype == M_CHEBYSHEV) {
+    c->cheb_m = M->degree;
+    c->cheb_auto = !(M->lmax > 0.0);
+    c->cheb_lmax = M->lmax;
+    c->cheb_lmin = (M->lmin > 0.0) ? M->lmin : M->lmax / 30.0;
+  }
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -461,56 +499,153 @@ static ampcg_status ensure_hist(ampcg_ctx* c, int maxit) {
   return AMPCG_OK;
 }
 
-// The four iteration kernels of a phase (2 u_z + u_r): precond, axpy, spmv,
-// update.  Argument lists: (Bufs, n, state) for precond/axpy, (Sell, Bufs,
-// state) for spmv, (Bufs, n, state, next switch handle, has_next) for update.
-template <int MT, int IT>
-static void fill_phase_table(ampcg_ctx* c) {
-#define AMPCG_PHASE_FNS(UZ, UR)                                                             \
-  {(const void*)k_precond<UZ, UR, MT>, (const void*)k_axpy<UZ>, (const void*)k_spmv<UZ, UR, IT>, \
-   (const void*)k_update<UZ, UR>}
-  const void* t[6][4] = {AMPCG_PHASE_FNS(P64, P64), AMPCG_PHASE_FNS(P64, P32),
-                         AMPCG_PHASE_FNS(P32, P64), AMPCG_PHASE_FNS(P32, P32),
-                         AMPCG_PHASE_FNS(P16, P64), AMPCG_PHASE_FNS(P16, P32)};
-#undef AMPCG_PHASE_FNS
-  memcpy(c->fn, t, sizeof(t));
-  const int sm64 = staged_smem_bytes<P64, IT>(), sm32 = staged_smem_bytes<P32, IT>();
-  for (int ph = 0; ph < 6; ++ph) {
-    for (int j = 0; j < 4; ++j) c->smem[ph][j] = 0;
-    if (c->maxw <= kStageW) c->smem[ph][2] = (ph % 2 == P64) ? sm64 : sm32;
+// Launch sequence of each phase (2 u_z + u_r): the precondition step (one
+// kernel, or init + m-1 steps + final for Chebyshev), then search direction,
+// SpMV, update.
+template <int MT, int IT, int UZ, int UR>
+static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
+  const int64_t n = c->n, nvec = (n + 7) / 8;
+  auto add = [&](const void* fn, int kind, int slot, int64_t work, int smem, int j = 0, double c1 = 0,
+                 double c2 = 0) {
+    Launch L;
+    L.fn = fn; L.kind = kind; L.slot = slot; L.j = j; L.c1 = c1; L.c2 = c2; L.smem = smem;
+    if (smem > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    L.grid = occ_grid(fn, sms, work, smem);
+    v.push_back(L);
+  };
+  v.clear();
+  if constexpr (MT == M_CHEBYSHEV) {
+    add((const void*)k_cheb_init<UZ, UR>, KA_CINIT, 0, n, 0);
+    for (int j = 1; j < c->cheb_m; ++j)
+      add((const void*)k_cheb_step<UZ, IT>, KA_CSTEP, 0, c->nslices * 32, 0, j, c->cheb_c1[j - 1],
+          c->cheb_c2[j - 1]);
+    add((const void*)k_cheb_final<UZ, UR>, KA_CFINAL, 0, n, 0);
+  } else {
+    add((const void*)k_precond<UZ, UR, MT>, KA_ELEM, 0, nvec, 0);
   }
+  add((const void*)k_axpy<UZ>, KA_ELEM, 1, nvec, 0);
+  const int sm = c->maxw <= kStageW ? staged_smem_bytes<UR, IT>() : 0;
+  add((const void*)k_spmv<UZ, UR, IT>, KA_SPMV, 2, c->nslices * 32, sm);
+  if (sm > 0) {
+    // staged SpMV: a warp takes at most 32 slices, so at least nslices/32 warps
+    int need = (int)((c->nslices + 32 * 8 - 1) / (32 * 8));
+    if (v.back().grid < need) v.back().grid = need;
+  }
+  add((const void*)k_update<UZ, UR>, KA_UPD, 3, nvec, 0);
 }
 
-struct PhaseArgs {
+template <int MT, int IT>
+static void build_sequences_t(ampcg_ctx* c, int sms) {
+  phase_seq<MT, IT, P64, P64>(c, sms, c->seq[0]);
+  phase_seq<MT, IT, P64, P32>(c, sms, c->seq[1]);
+  phase_seq<MT, IT, P32, P64>(c, sms, c->seq[2]);
+  phase_seq<MT, IT, P32, P32>(c, sms, c->seq[3]);
+  phase_seq<MT, IT, P16, P64>(c, sms, c->seq[4]);
+  phase_seq<MT, IT, P16, P32>(c, sms, c->seq[5]);
+}
+
+static ampcg_status build_sequences(ampcg_ctx* c, int sms) {
+  if (c->mtype == M_NONE) { if (c->idx16) build_sequences_t<M_NONE, 1>(c, sms); else build_sequences_t<M_NONE, 0>(c, sms); }
+  else if (c->mtype == M_JACOBI) { if (c->idx16) build_sequences_t<M_JACOBI, 1>(c, sms); else build_sequences_t<M_JACOBI, 0>(c, sms); }
+  else { if (c->idx16) build_sequences_t<M_CHEBYSHEV, 1>(c, sms); else build_sequences_t<M_CHEBYSHEV, 0>(c, sms); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  return AMPCG_OK;
+}
+
+// Ahat, D^-1/2 (three precisions each), the interval and the Chebyshev
+// constants (reading R8; the same FP64 expressions as the oracle).  With an
+// automatic interval, lmax is the Gershgorin bound max_i sum_j |ahat_ij| (an
+// upper bound of the spectrum, so M stays SPD) and lmin = lmax / 30.
+static ampcg_status cheb_prepare(ampcg_ctx* c) {
+  cudaStream_t s = c->stream;
+  unsigned long long* gk = nullptr;
+  ampcg_status st = dalloc(&gk, 1);
+  if (st != AMPCG_OK) return st;
+  Sell A = c->sell();
+  const int gs = (int)((c->nslices * 32 + kBlock - 1) / kBlock < 148 * 8 ? (c->nslices * 32 + kBlock - 1) / kBlock : 148 * 8);
+  cudaError_t e = cudaMemsetAsync(gk, 0, sizeof(*gk), s);
+  if (e == cudaSuccess) {
+    if (c->idx16) {
+      k_cheb_setup<1><<<gs, kBlock, 0, s>>>(A, c->ah64, c->ah32, c->ah16, c->ds64, c->ds32, c->ds16, gk);
+      k_cheb_setup2<1><<<gs, kBlock, 0, s>>>(A, c->ds64, c->ah64, c->ah32, c->ah16, gk);
+    } else {
+      k_cheb_setup<0><<<gs, kBlock, 0, s>>>(A, c->ah64, c->ah32, c->ah16, c->ds64, c->ds32, c->ds16, gk);
+      k_cheb_setup2<0><<<gs, kBlock, 0, s>>>(A, c->ds64, c->ah64, c->ah32, c->ah16, gk);
+    }
+    e = cudaGetLastError();
+  }
+  unsigned long long hk = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hk, gk, sizeof(hk), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(gk);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "Chebyshev setup: %s", cudaGetErrorString(e));
+  if (c->cheb_auto) {
+    double g;
+    memcpy(&g, &hk, sizeof(g));
+    c->cheb_lmax = g;
+    c->cheb_lmin = g / 30.0;
+  }
+  double a = c->cheb_lmin, bb = c->cheb_lmax;
+  double theta = (bb + a) / 2.0, delt = (bb - a) / 2.0;
+  double sigma = theta / delt;
+  double rho = 1.0 / sigma;
+  c->cheb_inv_theta = 1.0 / theta;
+  c->cheb_c1.assign(c->cheb_m > 1 ? c->cheb_m - 1 : 0, 0.0);
+  c->cheb_c2.assign(c->cheb_m > 1 ? c->cheb_m - 1 : 0, 0.0);
+  for (int j = 1; j < c->cheb_m; ++j) {
+    double rho_next = 1.0 / (2.0 * sigma - rho);
+    c->cheb_c1[j - 1] = rho_next * rho;
+    c->cheb_c2[j - 1] = 2.0 * rho_next / delt;
+    rho = rho_next;
+  }
+  return AMPCG_OK;
+}
+
+// Argument storage for one launch (kernel parameters are copied at launch or
+// graph-node creation, so one pack is reused).
+struct ArgPack {
   Bufs B;
   Sell A;
+  Cheb C;
   int64_t n;
   DevState* st;
   cudaGraphConditionalHandle h;
-  int has_next;
-  void* a_elem[3];
-  void* a_spmv[3];
-  void* a_upd[5];
-  PhaseArgs(const ampcg_ctx* c, cudaGraphConditionalHandle hn, int has)
-      : B(c->bufs()), A(c->sell()), n(c->n), st(c->st), h(hn), has_next(has) {
-    a_elem[0] = &B; a_elem[1] = &n; a_elem[2] = &st;
-    a_spmv[0] = &A; a_spmv[1] = &B; a_spmv[2] = &st;
-    a_upd[0] = &B; a_upd[1] = &n; a_upd[2] = &st; a_upd[3] = &h; a_upd[4] = &has_next;
+  int has_next, j;
+  double c1, c2;
+  void* a[8];
+  ArgPack(const ampcg_ctx* c, cudaGraphConditionalHandle hn, int has)
+      : B(c->bufs()), A(c->sell()), C(c->cheb()), n(c->n), st(c->st), h(hn), has_next(has), j(0),
+        c1(0), c2(0) {}
+  void** args(const Launch& L) {
+    switch (L.kind) {
+      case KA_ELEM: a[0] = &B; a[1] = &n; a[2] = &st; break;
+      case KA_SPMV: a[0] = &A; a[1] = &B; a[2] = &st; break;
+      case KA_UPD: a[0] = &B; a[1] = &n; a[2] = &st; a[3] = &h; a[4] = &has_next; break;
+      case KA_CINIT:
+      case KA_CFINAL: a[0] = &B; a[1] = &C; a[2] = &n; a[3] = &st; break;
+      case KA_CSTEP:
+        j = L.j; c1 = L.c1; c2 = L.c2;
+        a[0] = &A; a[1] = &C; a[2] = &st; a[3] = &j; a[4] = &c1; a[5] = &c2;
+        break;
+    }
+    return a;
   }
-  void** args(int j) { return j < 2 ? a_elem : (j == 2 ? a_spmv : a_upd); }
 };
 
-// One iteration of phase ph launched kernel by kernel on stream s, with an
-// event before each kernel and after the last (ev may be null).
+// One iteration of phase ph launched kernel by kernel on stream s; with ev,
+// ev[slot] is recorded before the first kernel of each slot and ev[4] after
+// the last kernel.
 static cudaError_t launch_phase(ampcg_ctx* c, int ph, cudaStream_t s, cudaEvent_t* ev) {
-  PhaseArgs pa(c, 0, 0);
-  for (int j = 0; j < 4; ++j) {
-    if (ev) {
-      cudaError_t e = cudaEventRecord(ev[j], s);
+  ArgPack pa(c, 0, 0);
+  int slot = -1;
+  for (const Launch& L : c->seq[ph]) {
+    if (ev && L.slot != slot) {
+      slot = L.slot;
+      cudaError_t e = cudaEventRecord(ev[slot], s);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaLaunchKernel(c->fn[ph][j], dim3(c->grid[ph][j]), dim3(kBlock), pa.args(j),
-                                     (size_t)c->smem[ph][j], s);
+    cudaError_t e = cudaLaunchKernel(L.fn, dim3(L.grid), dim3(kBlock), pa.args(L), (size_t)L.smem, s);
     if (e != cudaSuccess) return e;
   }
   return ev ? cudaEventRecord(ev[4], s) : cudaSuccess;
@@ -530,8 +665,8 @@ static cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const c
 }
 
 // Loop graph: WHILE(!done) { k_phase; SWITCH_0 .. SWITCH_{chunk-1}; k_loop_ctl }.
-// SWITCH_i has six bodies, one per phase, each holding that phase's four
-// kernels; the update kernel of iteration i sets the value of SWITCH_{i+1}
+// SWITCH_i has six bodies, one per phase, each holding that phase's launch
+// sequence; the update kernel of iteration i sets the value of SWITCH_{i+1}
 // (k_phase sets SWITCH_0).  After the stop every value is AMPCG_PHASE_NONE,
 // which matches no body, so the rest of the chunk launches nothing.
 static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
@@ -566,14 +701,13 @@ static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
     cudaGraphNode_t snode;
     CUDA_TRY(cudaGraphAddNode(&snode, body, &prev, nullptr, 1, &sp));
     bool has_next = i + 1 < chunk;
-    PhaseArgs pa(c, has_next ? hs[i + 1] : 0, has_next ? 1 : 0);
+    ArgPack pa(c, has_next ? hs[i + 1] : 0, has_next ? 1 : 0);
     for (int ph = 0; ph < 6; ++ph) {
       cudaGraph_t pg = sp.conditional.phGraph_out[ph];
       cudaGraphNode_t kn = nullptr;
-      for (int j = 0; j < 4; ++j) {
+      for (const Launch& L : c->seq[ph]) {
         cudaGraphNode_t nn;
-        CUDA_TRY(add_kernel_node(&nn, pg, j ? &kn : nullptr, c->fn[ph][j], c->grid[ph][j], kBlock,
-                                 pa.args(j), c->smem[ph][j]));
+        CUDA_TRY(add_kernel_node(&nn, pg, kn ? &kn : nullptr, L.fn, L.grid, kBlock, pa.args(L), L.smem));
         kn = nn;
       }
     }
@@ -636,7 +770,7 @@ static ampcg_status timed_loop(ampcg_ctx* c, ampcg_kernel_times* kt, cudaEvent_t
     int ph = 2 * c->hst->uz + c->hst->ur;
     if (ph < 0 || ph > 5) return fail(AMPCG_ERR_CUDA, "invalid phase %d in device state", ph);
     CUDA_TRY(launch_phase(c, ph, s, ev));
-    launches += 4;
+    launches += (long long)c->seq[ph].size();
     CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (c->hst->k > k0) {
@@ -745,7 +879,7 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
       // that stops on breakdown still launches its four)
       long long it = h.k - k_before + (h.status == ST_OK || h.status == ST_NOT_CONVERGED ? 0 : 1);
       long long bodies = it <= 0 ? 1 : (it + chunk - 1) / chunk;
-      launches += 2 * bodies + 4 * it;
+      launches += 2 * bodies + (long long)c->seq[0].size() * it;
     }
     k_before = h.k;
     // reading R9: verify, and replace r when the true residual misses tol
@@ -860,6 +994,17 @@ extern "C" ampcg_status ampcg_precond_apply(ampcg_t c, int uz, int ur, double om
   B.r64 = (double*)r;
   B.r32 = (float*)r;
   B.z = z;
+  if (c->mtype == M_CHEBYSHEV) {
+    // the precondition part of the phase's launch sequence on the caller's r, z
+    ArgPack pa(c, 0, 0);
+    pa.B = B;
+    for (const Launch& L : c->seq[2 * uz + ur]) {
+      if (L.slot != 0) break;
+      CUDA_TRY(cudaLaunchKernel(L.fn, dim3(L.grid), dim3(kBlock), pa.args(L), (size_t)L.smem, c->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return AMPCG_OK;
+  }
   if (ur == P64) {
     if (uz == P64) launch_precond_step<P64, P64>(c, B, c->st);
     else if (uz == P32) launch_precond_step<P32, P64>(c, B, c->st);
@@ -1014,6 +1159,31 @@ extern "C" ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy,
 // ---------------------------------------------------------------------------
 // New values on the same pattern, and the adjoint solve.
 
+// After new matrix values: the Chebyshev data follow A; with an automatic
+// interval the constants change, so the launch sequences and the loop graph
+// are rebuilt.
+static ampcg_status refresh_precond(ampcg_ctx* c) {
+  if (c->mtype != M_CHEBYSHEV) return AMPCG_OK;
+  ampcg_status st = cheb_prepare(c);
+  if (st != AMPCG_OK) return st;
+  if (c->cheb_auto) {
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    if ((st = build_sequences(c, sms)) != AMPCG_OK) return st;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  }
+  return AMPCG_OK;
+}
+
+extern "C" ampcg_status ampcg_precond_interval(ampcg_t c, double* lmin, double* lmax) {
+  if (!c || !lmin || !lmax) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  if (c->mtype != M_CHEBYSHEV) return fail(AMPCG_ERR_INVALID_ARG, "not a Chebyshev preconditioner");
+  *lmin = c->cheb_lmin;
+  *lmax = c->cheb_lmax;
+  return AMPCG_OK;
+}
+
 extern "C" ampcg_status ampcg_update_values(ampcg_t c, const double* vals) {
   if (!c || !vals) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = c->stream;
@@ -1045,7 +1215,7 @@ extern "C" ampcg_status ampcg_update_values(ampcg_t c, const double* vals) {
   if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "update values: %s", cudaGetErrorString(e));
   if (hf & 8) return fail(AMPCG_ERR_NONFINITE, "matrix has non-finite values (context now holds them)");
   if (hf & 4) return fail(AMPCG_ERR_NOT_SPD, "a diagonal entry is not positive (context now holds it)");
-  return AMPCG_OK;
+  return refresh_precond(c);
 }
 
 extern "C" ampcg_status ampcg_adjoint(ampcg_t c, const double* x, const double* dLdx, double tol,
@@ -1117,7 +1287,7 @@ extern "C" ampcg_status ampcg_assemble_log_coeff(ampcg_t c, const double* theta,
   cudaFree(flags);
   if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "assemble: %s", cudaGetErrorString(e));
   if (hf & 4) return fail(AMPCG_ERR_INVALID_ARG, "a row has no stored diagonal entry");
-  return AMPCG_OK;
+  return refresh_precond(c);
 }
 
 extern "C" ampcg_status ampcg_grad_log_coeff(ampcg_t c, const double* x, const double* lambda,

@@ -1188,6 +1188,263 @@ __global__ void k_grad_logcoeff(Sell A, const double* x, const double* lam, doub
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Chebyshev polynomial preconditioner (reading R8): M^-1 = D^-1/2 P(Ahat)
+// D^-1/2, Ahat = D^-1/2 A D^-1/2, applied as m steps of the Chebyshev
+// iteration for Ahat u = v (Saad, Iterative Methods for Sparse Linear
+// Systems, Alg. 12.1) from u_0 = 0 on [lmin, lmax]:
+//   v = D^-1/2 y, res = v, d_0 = v / theta, u = d_0;
+//   step j = 1..m-1: t = Ahat d_{j-1}; res -= t;
+//                    d_j = c1_j d_{j-1} + c2_j res; u += d_j;
+//   z = D^-1/2 u.
+// All vectors in u_z (FP16/FP32 ones computed in FP32 and rounded once); the
+// product uses the copy of Ahat in u_z.  c1_j, c2_j, 1/theta are FP64
+// constants computed once on the host.
+struct Cheb {
+  const double* ah64;
+  const float* ah32;
+  const __half* ah16;
+  const double* ds64;
+  const float* ds32;
+  const __half* ds16;
+  void* res;
+  void* d[2];
+  void* u;
+  double inv_theta;
+};
+
+template <int UZ> __device__ __forceinline__ typename Store<UZ>::T cheb_ds(const Cheb& C, int64_t i);
+template <> __device__ __forceinline__ double cheb_ds<P64>(const Cheb& C, int64_t i) { return C.ds64[i]; }
+template <> __device__ __forceinline__ float cheb_ds<P32>(const Cheb& C, int64_t i) { return C.ds32[i]; }
+template <> __device__ __forceinline__ __half cheb_ds<P16>(const Cheb& C, int64_t i) { return C.ds16[i]; }
+
+// a * b in u_z: FP64 multiply, or the FP32 product rounded once.
+template <int UZ>
+__device__ __forceinline__ typename Store<UZ>::T mul_u(typename Store<UZ>::T a, typename Store<UZ>::T b) {
+  if constexpr (UZ == P64) return __dmul_rn(a, b);
+  else if constexpr (UZ == P32) return __fmul_rn(a, b);
+  else return __float2half_rn(__fmul_rn(__half2float(a), __half2float(b)));
+}
+template <int UZ>
+__device__ __forceinline__ typename Store<UZ>::T add_u(typename Store<UZ>::T a, typename Store<UZ>::T b) {
+  if constexpr (UZ == P64) return __dadd_rn(a, b);
+  else if constexpr (UZ == P32) return __fadd_rn(a, b);
+  else return __float2half_rn(__fadd_rn(__half2float(a), __half2float(b)));
+}
+template <int UZ>
+__device__ __forceinline__ typename Store<UZ>::T sub_u(typename Store<UZ>::T a, typename Store<UZ>::T b) {
+  if constexpr (UZ == P64) return __dsub_rn(a, b);
+  else if constexpr (UZ == P32) return __fsub_rn(a, b);
+  else return __float2half_rn(__fsub_rn(__half2float(a), __half2float(b)));
+}
+
+// y = omega r (as in precond_rows), v = D^-1/2 y, res = v, d_0 = v/theta, u = d_0.
+template <int UZ, int UR>
+__global__ void __launch_bounds__(256) k_cheb_init(Bufs B, Cheb C, int64_t n, DevState* st) {
+  using TZ = typename Store<UZ>::T;
+  using TR = typename Store<UR>::T;
+  if (st->done) return;
+  if (phase_mismatch(st, UZ, UR)) return;
+  const int r_cast = st->r_cast;
+  const double om = st->omega;
+  const float omf = st->omega_f;
+  const int pow2 = st->omega_pow2, oe = st->omega_e;
+  const bool om_one = pow2 && oe == 0;
+  TZ* res = (TZ*)C.res;
+  TZ* d0 = (TZ*)C.d[0];
+  TZ* u = (TZ*)C.u;
+  TZ it;
+  if constexpr (UZ == P64) it = C.inv_theta;
+  else if constexpr (UZ == P32) it = __double2float_rn(C.inv_theta);
+  else it = __float2half_rn(__double2float_rn(C.inv_theta));   // unused for FP16 (FP32 constant below)
+  const float itf = __double2float_rn(C.inv_theta);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    TR r;
+    if constexpr (UR == P64) {
+      if (r_cast) { r = f2d(B.r32[i]); B.r64[i] = r; } else r = B.r64[i];
+    } else {
+      if (r_cast) { r = __double2float_rn(B.r64[i]); B.r32[i] = r; } else r = B.r32[i];
+    }
+    TZ y;
+    if constexpr (UR == P64) {
+      if constexpr (UZ == P16) y = pow2 ? d2h_scaled(r, oe) : d2h(__dmul_rn(om, r));
+      else y = round_from_f64<UZ>(om_one ? r : __dmul_rn(om, r));
+    } else {
+      y = round_from_f32<UZ>(__fmul_rn(omf, r));
+    }
+    TZ v = mul_u<UZ>(cheb_ds<UZ>(C, i), y);
+    TZ dd;
+    if constexpr (UZ == P64) dd = __dmul_rn(v, it);
+    else if constexpr (UZ == P32) dd = __fmul_rn(v, itf);
+    else dd = __float2half_rn(__fmul_rn(__half2float(v), itf));
+    res[i] = v;
+    d0[i] = dd;
+    u[i] = dd;
+  }
+  if (st->p_cast) cast_p<UZ>(B, n, st);
+}
+
+// One Chebyshev step j >= 1: t = Ahat d_{j-1} (accumulated in u_z's compute
+// precision), res -= t, d_j = c1 d_{j-1} + c2 res, u += d_j.  Thread per row.
+template <int UZ, int IT>
+__global__ void __launch_bounds__(256) k_cheb_step(Sell A, Cheb C, DevState* st, int j, double c1,
+                                                   double c2) {
+  using TZ = typename Store<UZ>::T;
+  if (st->done) return;
+  if (phase_mismatch(st, UZ, -1)) return;
+  const TZ* __restrict__ dp = (const TZ*)C.d[(j - 1) & 1];
+  TZ* dn = (TZ*)C.d[j & 1];
+  TZ* res = (TZ*)C.res;
+  TZ* u = (TZ*)C.u;
+  const float c1f = __double2float_rn(c1), c2f = __double2float_rn(c2);
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row >= A.n) continue;
+    long long base = __ldg(A.off + s) + lane;
+    int w = __ldg(A.width + s);
+    TZ t;
+    if constexpr (UZ == P64) {
+      double acc = 0.0;
+      for (int k = 0; k < w; ++k) {
+        long long e = base + 32ll * k;
+        acc = fma(__ldg(C.ah64 + e), dp[col_at<IT>(A, e, row)], acc);
+      }
+      t = acc;
+    } else if constexpr (UZ == P32) {
+      float acc = 0.f;
+      for (int k = 0; k < w; ++k) {
+        long long e = base + 32ll * k;
+        acc = __fmaf_rn(__ldg(C.ah32 + e), dp[col_at<IT>(A, e, row)], acc);
+      }
+      t = acc;
+    } else {
+      float acc = 0.f;
+      for (int k = 0; k < w; ++k) {
+        long long e = base + 32ll * k;
+        acc = __fmaf_rn(__half2float(C.ah16[e]), __half2float(dp[col_at<IT>(A, e, row)]), acc);
+      }
+      t = __float2half_rn(acc);
+    }
+    TZ rs = sub_u<UZ>(res[row], t);
+    TZ dd;
+    if constexpr (UZ == P64) dd = fma(c1, dp[row], __dmul_rn(c2, rs));
+    else if constexpr (UZ == P32) dd = __fmaf_rn(c1f, dp[row], __fmul_rn(c2f, rs));
+    else dd = __float2half_rn(__fmaf_rn(c1f, __half2float(dp[row]), __fmul_rn(c2f, __half2float(rs))));
+    res[row] = rs;
+    dn[row] = dd;
+    u[row] = add_u<UZ>(u[row], dd);
+  }
+}
+
+// z = D^-1/2 u, rho = r^T z (as k_precond), last block: beta.
+template <int UZ, int UR>
+__global__ void __launch_bounds__(256) k_cheb_final(Bufs B, Cheb C, int64_t n, DevState* st) {
+  using TZ = typename Store<UZ>::T;
+  using TR = typename Store<UR>::T;
+  if (st->done) return;
+  if (phase_mismatch(st, UZ, UR)) return;
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+  const TZ* u = (const TZ*)C.u;
+  TZ* z = (TZ*)B.z;
+  const float sigf = st->sig_f;
+  double rho = 0.0;
+  Dot2 d2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    TZ zi = mul_u<UZ>(cheb_ds<UZ>(C, i), u[i]);
+    z[i] = zi;
+    TR r;
+    if constexpr (UR == P64) r = B.r64[i];
+    else r = B.r32[i];
+    if constexpr (kSmall) d2.add(__fmul_rn((float)r, sigf), (float)zi);
+    else rho = fma(to_f64(r), to_f64(zi), rho);
+  }
+  double v[1];
+  if constexpr (kSmall) {
+    v[0] = block_sum_dot2(d2, st->inv_sig);
+  } else {
+    v[0] = rho;
+    block_sum<1>(v);
+  }
+  if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
+  if (!last_block(&st->ticket[0])) return;
+  double tot[1];
+  final_sum<1>(B.part, gridDim.x, 1, tot);
+  if (threadIdx.x == 0) {
+    st->ticket[0] = 0u;
+    double r = tot[0];
+    st->rho = r;
+    if (!isfinite(r)) { st->status = ST_NONFINITE; st->done = 1; return; }
+    if (!(r > 0.0)) { st->status = ST_BREAKDOWN; st->done = 1; return; }
+    double beta = st->first ? 0.0 : r / st->rho_prev;
+    st->beta = beta;
+    st->beta_f = __double2float_rn(beta);
+    st->r_cast = 0;
+    if (st->p_cast) {
+      st->pcur ^= 1;
+      st->uz_p = st->uz;
+      st->p_cast = 0;
+    }
+  }
+}
+
+// Ahat = D^-1/2 A D^-1/2 in the sliced layout ((dsi_i a_ij) dsi_j in FP64,
+// rounded to FP32/FP16), D^-1/2 in three precisions, and the Gershgorin bound
+// max_i sum_j |ahat_ij| (as an order-preserving key) for the interval.
+template <int IT>
+__global__ void k_cheb_setup(Sell A, double* ah64, float* ah32, __half* ah16, double* ds64,
+                             float* ds32, __half* ds16, unsigned long long* gersh) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  // pass 1: D^-1/2
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row >= A.n) continue;
+    long long base = A.off[s] + lane;
+    int w = A.width[s];
+    double dg = 0.0;
+    for (int j = 0; j < w; ++j) {
+      long long e = base + 32ll * j;
+      if (col_at<IT>(A, e, row) == row) { dg = A.v64[e]; break; }
+    }
+    double di = 1.0 / sqrt(dg);
+    ds64[row] = di;
+    ds32[row] = __double2float_rn(di);
+    ds16[row] = d2h(di);
+  }
+}
+
+template <int IT>
+__global__ void k_cheb_setup2(Sell A, const double* ds64, double* ah64, float* ah32, __half* ah16,
+                              unsigned long long* gersh) {
+  int lane = threadIdx.x & 31;
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp; s < A.nslices; s += nwarps) {
+    int row = s * 32 + lane;
+    if (row >= A.n) continue;
+    long long base = A.off[s] + lane;
+    int w = A.width[s];
+    double di = ds64[row], sum = 0.0;
+    for (int j = 0; j < w; ++j) {
+      long long e = base + 32ll * j;
+      int c = col_at<IT>(A, e, row);
+      double ah = __dmul_rn(__dmul_rn(di, A.v64[e]), ds64[c]);
+      ah64[e] = ah;
+      ah32[e] = __double2float_rn(ah);
+      ah16[e] = d2h(ah);
+      sum += fabs(ah);
+    }
+    atomicMax(gersh, abs_key(sum));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step entry points (single launches, no reduction).
 
