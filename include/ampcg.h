@@ -135,6 +135,18 @@ ampcg_status ampcg_create_csr(ampcg_t* out, int64_t n, int64_t nnz, const int32_
                               const int32_t* colind, const double* vals,
                               const ampcg_precond_spec* M, void* cuda_stream);
 
+/* Creates a context from block CSR: nb block rows of bs x bs blocks (1 <= bs
+ * <= 16), browptr[nb+1] (0 .. nnzb), bcolind[nnzb] (block columns in
+ * [0, nb), strictly increasing within a block row), bvals[nnzb * bs * bs]
+ * (each block row-major).  The blocks are expanded on the device into the
+ * scalar matrix of n = nb * bs rows (row I*bs + r takes row r of every block
+ * of block row I), which then goes through the same validation and
+ * preparation as ampcg_create_csr; all other calls see the scalar system
+ * (vectors of length nb * bs, dL/dA in the expanded CSR order). */
+ampcg_status ampcg_create_bsr(ampcg_t* out, int64_t nb, int bs, int64_t nnzb, const int32_t* browptr,
+                              const int32_t* bcolind, const double* bvals,
+                              const ampcg_precond_spec* M, void* cuda_stream);
+
 /* The Chebyshev interval in use (after automatic choice).  Returns
  * AMPCG_ERR_INVALID_ARG for other preconditioners. */
 ampcg_status ampcg_precond_interval(ampcg_t ctx, double* lmin, double* lmax);

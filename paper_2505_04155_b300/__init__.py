@@ -85,6 +85,9 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_policy_default.restype = None
     lib.ampcg_create_csr.argtypes = [C.POINTER(vp), i64, i64, vp, vp, vp, C.POINTER(PrecondSpec), vp]
     lib.ampcg_create_csr.restype = C.c_int
+    lib.ampcg_create_bsr.argtypes = [C.POINTER(vp), i64, C.c_int, i64, vp, vp, vp,
+                                     C.POINTER(PrecondSpec), vp]
+    lib.ampcg_create_bsr.restype = C.c_int
     lib.ampcg_destroy.argtypes = [vp]
     lib.ampcg_destroy.restype = None
     lib.ampcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(PolicyC), C.POINTER(ResultC)]
@@ -232,6 +235,29 @@ class Solver:
         _check(lib.ampcg_create_csr(C.byref(h), self.n, self.nnz, _ptr(rowptr), _ptr(col), _ptr(val),
                                     C.byref(spec), st))
         self._h = h
+
+    @classmethod
+    def from_bsr(cls, browptr, bcol, bval, bs: int, precond: int = M_JACOBI, degree: int = 0,
+                 lmin: float = 0.0, lmax: float = 0.0, stream=None) -> "Solver":
+        """Context from block CSR (ampcg_create_bsr): bval holds nnzb row-major
+        bs x bs blocks; the solver works on the scalar system of nb*bs rows."""
+        lib = load_library()
+        if isinstance(browptr, np.ndarray):
+            browptr = np.ascontiguousarray(browptr, dtype=np.int32)
+            bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+            bval = np.ascontiguousarray(bval, dtype=np.float64)
+        self = cls.__new__(cls)
+        nb = int(browptr.shape[0]) - 1
+        nnzb = int(bcol.shape[0])
+        self.n = nb * bs
+        self.nnz = nnzb * bs * bs
+        spec = PrecondSpec(precond, degree, lmin, lmax)
+        h = C.c_void_p()
+        st = _torch_stream() if stream is None else stream
+        _check(lib.ampcg_create_bsr(C.byref(h), nb, bs, nnzb, _ptr(browptr), _ptr(bcol), _ptr(bval),
+                                    C.byref(spec), st))
+        self._h = h
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

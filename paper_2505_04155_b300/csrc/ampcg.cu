@@ -1307,3 +1307,63 @@ extern "C" ampcg_status ampcg_grad_log_coeff(ampcg_t c, const double* x, const d
   CUDA_TRY(cudaStreamSynchronize(s));
   return AMPCG_OK;
 }
+
+
+// ---------------------------------------------------------------------------
+// Block CSR input: expanded on the device into scalar CSR, then the same
+// preparation as ampcg_create_csr.
+
+extern "C" ampcg_status ampcg_create_bsr(ampcg_t* out, int64_t nb, int bs, int64_t nnzb,
+                                         const int32_t* browptr, const int32_t* bcolind,
+                                         const double* bvals, const ampcg_precond_spec* M,
+                                         void* cuda_stream) {
+  if (!out) return fail(AMPCG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nb <= 0 || bs < 1 || bs > 16 || nnzb < 0 || !browptr || (nnzb > 0 && (!bcolind || !bvals)))
+    return fail(AMPCG_ERR_INVALID_ARG, "need nb > 0, 1 <= bs <= 16, nnzb >= 0 and the three arrays");
+  int64_t n = nb * bs, nnz = nnzb * bs * bs;
+  if (n > (int64_t)0x7fffffe0 || nnz > (int64_t)0x7fffffff)
+    return fail(AMPCG_ERR_INVALID_ARG, "expanded matrix too large for int32 indices");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(AMPCG_ERR_NO_DEVICE, "no CUDA device visible");
+  }
+  // block row pointer validation on the host side of the copy
+  std::vector<int32_t> hb(nb + 1);
+  cudaError_t e = cudaMemcpy(hb.data(), browptr, (nb + 1) * sizeof(int32_t),
+                             is_device_ptr(browptr) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+  if (hb[0] != 0 || hb[nb] != nnzb) return fail(AMPCG_ERR_INVALID_ARG, "browptr must run from 0 to nnzb");
+  for (int64_t i = 0; i < nb; ++i)
+    if (hb[i + 1] < hb[i]) return fail(AMPCG_ERR_INVALID_ARG, "browptr must be nondecreasing");
+  int *d_bp = nullptr, *d_bc = nullptr, *d_rp = nullptr, *d_c = nullptr;
+  double *d_bv = nullptr, *d_v = nullptr;
+  ampcg_status st = AMPCG_OK;
+  auto cleanup = [&]() {
+    cudaFree(d_bp); cudaFree(d_bc); cudaFree(d_rp); cudaFree(d_c); cudaFree(d_bv); cudaFree(d_v);
+  };
+  if ((st = dalloc(&d_bp, nb + 1)) != AMPCG_OK || (st = dalloc(&d_bc, nnzb)) != AMPCG_OK ||
+      (st = dalloc(&d_bv, nnzb * bs * bs)) != AMPCG_OK || (st = dalloc(&d_rp, n + 1)) != AMPCG_OK ||
+      (st = dalloc(&d_c, nnz)) != AMPCG_OK || (st = dalloc(&d_v, nnz)) != AMPCG_OK) {
+    cleanup();
+    return st;
+  }
+  e = cudaMemcpy(d_bp, hb.data(), (nb + 1) * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnzb)
+    e = cudaMemcpy(d_bc, bcolind, nnzb * sizeof(int), is_device_ptr(bcolind) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nnzb)
+    e = cudaMemcpy(d_bv, bvals, nnzb * bs * bs * sizeof(double), is_device_ptr(bvals) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_bsr_expand<<<(int)((n + kBlock - 1) / kBlock), kBlock>>>(nb, bs, d_bp, d_bc, d_bv, d_rp, d_c, d_v);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(AMPCG_ERR_CUDA, "block expansion: %s", cudaGetErrorString(e));
+  }
+  st = ampcg_create_csr(out, n, nnz, d_rp, d_c, d_v, M, cuda_stream);
+  cleanup();
+  return st;
+}

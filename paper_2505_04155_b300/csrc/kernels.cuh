@@ -1059,6 +1059,30 @@ __global__ void k_jacobi(int64_t n, const double* diag, double* d64, float* d32,
   d16[i] = d2h(v);
 }
 
+// Block CSR (nb block rows of bs x bs blocks, row-major blocks, ascending
+// block columns) expanded to scalar CSR: scalar row I*bs + r holds, for each
+// block k of block row I, the bs entries of the block's row r.
+__global__ void k_bsr_expand(int64_t nb, int bs, const int* browptr, const int* bcol,
+                             const double* bval, int* rowptr, int* col, double* val) {
+  int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nb * bs) return;
+  int64_t I = row / bs;
+  int r = (int)(row % bs);
+  int k0 = browptr[I], k1 = browptr[I + 1];
+  int64_t start = (int64_t)k0 * bs * bs + (int64_t)r * (k1 - k0) * bs;
+  rowptr[row] = (int)start;
+  if (row == nb * bs - 1) rowptr[row + 1] = browptr[nb] * bs * bs;
+  int64_t o = start;
+  for (int k = k0; k < k1; ++k) {
+    int J = bcol[k];
+    for (int c = 0; c < bs; ++c) {
+      col[o] = J * bs + c;
+      val[o] = bval[(int64_t)k * bs * bs + (int64_t)r * bs + c];
+      ++o;
+    }
+  }
+}
+
 // New values on the same pattern: vals in CSR order (rowptr on the device),
 // written into the sliced layout (FP64 and FP32 copies) with the Jacobi
 // inverse diagonal.  flags bit 2: diagonal <= 0; bit 3: non-finite value.

@@ -188,3 +188,106 @@ def log_coeff_problem(n: int, sigma: float = 1.0, seed: int = 0, perturb: float 
     a_t = diffusion3d_from_field(theta_t)
     b = rhs_uniform(a.n, seed_rhs)
     return theta.reshape(-1), theta_t.reshape(-1), a, a_t, b
+
+
+# --- Linear elasticity, trilinear hexahedra (Q1), block CSR 3x3 ------------
+
+def q1_element_stiffness(h: float, nu: float) -> np.ndarray:
+    """24x24 stiffness of a cube element of side h for E = 1, Poisson ratio nu,
+    trilinear shape functions, 2x2x2 Gauss quadrature; dof order
+    (node a, component c) -> 3a + c, nodes a = x + 2y + 4z over {0,1}^3."""
+    lam = nu / ((1 + nu) * (1 - 2 * nu))
+    mu = 1.0 / (2 * (1 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] += 2 * mu
+    D[3:, 3:] = np.eye(3) * mu
+    corners = np.array([[(a >> 0) & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)]) * 2 - 1
+    g = 1.0 / np.sqrt(3.0)
+    K = np.zeros((24, 24))
+    for gp in np.array(np.meshgrid([-g, g], [-g, g], [-g, g], indexing="ij")).reshape(3, -1).T:
+        dN = np.zeros((8, 3))
+        for a in range(8):
+            xi = corners[a]
+            f = 1 + xi * gp
+            dN[a] = xi * np.array([f[1] * f[2], f[0] * f[2], f[0] * f[1]]) / 8.0
+        dN *= 2.0 / h                      # d/dx = (2/h) d/dxi
+        B = np.zeros((6, 24))
+        for a in range(8):
+            dx, dy, dz = dN[a]
+            B[0, 3 * a] = dx
+            B[1, 3 * a + 1] = dy
+            B[2, 3 * a + 2] = dz
+            B[3, 3 * a] = dy; B[3, 3 * a + 1] = dx
+            B[4, 3 * a + 1] = dz; B[4, 3 * a + 2] = dy
+            B[5, 3 * a] = dz; B[5, 3 * a + 2] = dx
+        K += B.T @ D @ B * (h / 2) ** 3
+    return 0.5 * (K + K.T)
+
+
+@dataclass
+class BSR:
+    nb: int
+    bs: int
+    browptr: np.ndarray  # int32 [nb+1]
+    bcol: np.ndarray     # int32 [nnzb]
+    bval: np.ndarray     # float64 [nnzb, bs, bs]
+    info: dict
+
+    def to_csr(self) -> CSR:
+        nb, bs = self.nb, self.bs
+        nblk = np.diff(self.browptr)
+        n = nb * bs
+        rowlen = np.repeat(nblk * bs, bs)
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(rowlen, out=rowptr[1:])
+        col = np.empty(rowptr[-1], dtype=np.int32)
+        val = np.empty(rowptr[-1])
+        for I in range(nb):
+            k0, k1 = self.browptr[I], self.browptr[I + 1]
+            J = self.bcol[k0:k1]
+            for r in range(bs):
+                s = rowptr[I * bs + r]
+                col[s:s + (k1 - k0) * bs] = (J[:, None] * bs + np.arange(bs)[None, :]).reshape(-1)
+                val[s:s + (k1 - k0) * bs] = self.bval[k0:k1, r, :].reshape(-1)
+        return CSR(n, rowptr.astype(np.int32), col, val, dict(self.info))
+
+
+def elasticity_q1(n: int, seed: int = 0, nu: float = 0.3, e_lo: float = 1.0, e_hi: float = 1e3) -> BSR:
+    """Q1 elasticity on n^3 nodes ((n-1)^3 cube elements, h = 1/(n-1)), Young's
+    modulus log-uniform in [e_lo, e_hi] per element (seed), Poisson ratio nu,
+    nodes on the x = 0 face clamped (removed).  Block CSR with 3x3 blocks."""
+    ne = n - 1
+    h = 1.0 / ne
+    Kr = q1_element_stiffness(h, nu).reshape(8, 3, 8, 3).transpose(0, 2, 1, 3)  # [a, b, 3, 3]
+    rng = np.random.default_rng(seed)
+    E = np.exp(rng.uniform(np.log(e_lo), np.log(e_hi), ne ** 3))
+    ex, ey, ez = np.meshgrid(np.arange(ne), np.arange(ne), np.arange(ne), indexing="ij")
+    ex, ey, ez = ex.reshape(-1), ey.reshape(-1), ez.reshape(-1)
+    eidx = ex + ne * (ey + ne * ez)
+    E = E[eidx]
+    node = lambda x, y, z: x + n * (y + n * z)
+    enodes = np.stack([node(ex + ((a >> 0) & 1), ey + ((a >> 1) & 1), ez + ((a >> 2) & 1)) for a in range(8)], 1)
+    free = np.ones(n ** 3, dtype=bool)
+    free[np.arange(n ** 3) % n == 0] = False               # x = 0 face
+    newid = -np.ones(n ** 3, dtype=np.int64)
+    newid[free] = np.arange(free.sum())
+    nb = int(free.sum())
+    keys, blocks = [], []
+    for a in range(8):
+        for b in range(8):
+            I, J = newid[enodes[:, a]], newid[enodes[:, b]]
+            ok = (I >= 0) & (J >= 0)
+            keys.append(I[ok] * nb + J[ok])
+            blocks.append(E[ok, None, None] * Kr[a, b][None])
+    keys = np.concatenate(keys)
+    blocks = np.concatenate(blocks)
+    uk, inv = np.unique(keys, return_inverse=True)
+    bval = np.zeros((uk.size, 3, 3))
+    np.add.at(bval, inv, blocks)
+    brow = (uk // nb).astype(np.int64)
+    bcol = (uk % nb).astype(np.int32)
+    browptr = np.zeros(nb + 1, dtype=np.int64)
+    np.add.at(browptr, brow + 1, 1)
+    browptr = np.cumsum(browptr).astype(np.int32)
+    return BSR(nb, 3, browptr, bcol, bval, {"kind": "elasticity_q1", "n": n, "nu": nu, "dof": nb * 3})
