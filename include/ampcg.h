@@ -174,6 +174,19 @@ ampcg_status ampcg_update_values(ampcg_t ctx, const double* vals);
 ampcg_status ampcg_solve(ampcg_t ctx, const double* b, double* x, double tol, int maxit,
                          const ampcg_policy* policy, ampcg_result* res);
 
+/* Solves nsys independent systems (distinct contexts, each with its own
+ * b[i] and in/out x[i], host or device) with the same tol, maxit and policy.
+ * The systems run concurrently on library-owned streams (up to 16 at a
+ * time), after all work already queued on their contexts' streams and
+ * before any work queued there later; each system keeps its own device-side
+ * loop and stops on its own test (per-system convergence).  results[i] (may
+ * be NULL) as in ampcg_solve.  Returns AMPCG_OK if every system converged,
+ * AMPCG_NOT_CONVERGED if some reached maxit, else the first system's error
+ * (ampcg_last_error names the system).  Synchronous.  Not from the paper. */
+ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, const double* const* b,
+                                 double* const* x, double tol, int maxit,
+                                 const ampcg_policy* policy, ampcg_result* results);
+
 /* Per-kernel device time of one solve, split by the precision pair of the
  * iteration, as the paper reports per-kernel time for each phase of
  * AMP-PCG (Sec. 5.5).  Index [kernel][phase]: kernel 0 = scale+precondition

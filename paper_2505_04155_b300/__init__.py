@@ -106,6 +106,9 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_assemble_log_coeff.restype = C.c_int
     lib.ampcg_grad_log_coeff.argtypes = [vp, vp, vp, vp]
     lib.ampcg_grad_log_coeff.restype = C.c_int
+    lib.ampcg_solve_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                        C.c_double, C.c_int, C.POINTER(PolicyC), C.POINTER(ResultC)]
+    lib.ampcg_solve_batched.restype = C.c_int
     lib.ampcg_spmv.argtypes = [vp, C.c_int, vp, vp]
     lib.ampcg_spmv.restype = C.c_int
     lib.ampcg_precond_apply.argtypes = [vp, C.c_int, C.c_int, C.c_double, vp, vp]
@@ -395,3 +398,20 @@ def selector_trace_noalloc(delta, nb: float, tol: float, policy: Policy | None =
         C.byref(pol), delta.ctypes.data_as(C.POINTER(C.c_double)), delta.size - 1, nb, tol,
         out.ctypes.data_as(C.POINTER(C.c_uint8))))
     return out
+
+
+def solve_batched(solvers, bs, xs, tol: float = 1e-10, maxit: int = 2000,
+                  policy: Policy | None = None):
+    """Solve independent systems in one call (ampcg_solve_batched); xs hold
+    the initial guesses and receive the solutions.  Returns a list of SolveInfo."""
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s._h.value for s in solvers])
+    bp = (C.c_void_p * n)(*[_ptr(b) for b in bs])
+    xp = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    res = (ResultC * n)()
+    pol = (policy or Policy()).to_c()
+    st = load_library().ampcg_solve_batched(n, hs, bp, xp, tol, maxit, C.byref(pol), res)
+    _check(st, (OK, NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE))
+    return [SolveInfo(r.status, r.iters, bool(r.converged), r.refreshes, r.true_relres,
+                      r.updated_relres, tuple(r.switch_iter), r.seconds, r.kernel_launches)
+            for r in res]

@@ -15,7 +15,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -787,7 +789,7 @@ static ampcg_status timed_loop(ampcg_ctx* c, ampcg_kernel_times* kt, cudaEvent_t
 
 static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double tol, int maxit,
                                const ampcg_policy* policy, ampcg_result* res,
-                               ampcg_kernel_times* kt);
+                               ampcg_kernel_times* kt, cudaStream_t s_override = nullptr);
 
 extern "C" ampcg_status ampcg_solve(ampcg_t c, const double* b, double* x, double tol, int maxit,
                                     const ampcg_policy* policy, ampcg_result* res) {
@@ -804,7 +806,7 @@ extern "C" ampcg_status ampcg_solve_timed(ampcg_t c, const double* b, double* x,
 
 static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double tol, int maxit,
                                const ampcg_policy* policy, ampcg_result* res,
-                               ampcg_kernel_times* kt) {
+                               ampcg_kernel_times* kt, cudaStream_t s_override) {
   auto t0 = std::chrono::steady_clock::now();
   if (!c) return fail(AMPCG_ERR_INVALID_ARG, "NULL context");
   if (!b || !x) return fail(AMPCG_ERR_INVALID_ARG, "NULL b or x");
@@ -816,7 +818,7 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   if (ps != AMPCG_OK) return ps;
   int chunk = pol.graph_chunk > 0 ? pol.graph_chunk : 16;
   cudaSetDevice(c->device);
-  cudaStream_t s = c->stream;
+  cudaStream_t s = s_override ? s_override : c->stream;
   ampcg_status hs = ensure_hist(c, maxit);
   if (hs != AMPCG_OK) return hs;
   bool b_dev = is_device_ptr(b), x_dev = is_device_ptr(x);
@@ -1365,5 +1367,79 @@ extern "C" ampcg_status ampcg_create_bsr(ampcg_t* out, int64_t nb, int bs, int64
   }
   st = ampcg_create_csr(out, n, nnz, d_rp, d_c, d_v, M, cuda_stream);
   cleanup();
+  return st;
+}
+
+
+// ---------------------------------------------------------------------------
+// Many independent systems in one call.
+
+extern "C" ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, const double* const* b,
+                                            double* const* x, double tol, int maxit,
+                                            const ampcg_policy* policy, ampcg_result* results) {
+  if (nsys < 0 || (nsys > 0 && (!systems || !b || !x)))
+    return fail(AMPCG_ERR_INVALID_ARG, "bad batched arguments");
+  if (nsys == 0) return AMPCG_OK;
+  for (int i = 0; i < nsys; ++i) {
+    if (!systems[i] || !b[i] || !x[i]) return fail(AMPCG_ERR_INVALID_ARG, "NULL entry %d", i);
+    for (int j = 0; j < i; ++j)
+      if (systems[j] == systems[i]) return fail(AMPCG_ERR_INVALID_ARG, "system %d appears twice", i);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int W = nsys < 16 ? nsys : 16;
+  std::vector<cudaStream_t> ws(W, nullptr);
+  cudaEvent_t ev = nullptr;
+  ampcg_status st = AMPCG_OK;
+  auto cleanup = [&]() {
+    for (cudaStream_t s : ws)
+      if (s) cudaStreamDestroy(s);
+    if (ev) cudaEventDestroy(ev);
+  };
+  for (int w = 0; w < W; ++w) {
+    if (cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking) != cudaSuccess) {
+      cleanup();
+      return fail(AMPCG_ERR_CUDA, "stream creation failed");
+    }
+  }
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cleanup();
+    return fail(AMPCG_ERR_CUDA, "event creation failed");
+  }
+  // work queued on the systems' own streams (their inputs) comes first
+  for (int i = 0; i < nsys; ++i) {
+    cudaEventRecord(ev, systems[i]->stream);
+    for (int w = 0; w < W; ++w) cudaStreamWaitEvent(ws[w], ev, 0);
+  }
+  std::atomic<int> next(0);
+  std::vector<ampcg_status> sts(nsys, AMPCG_OK);
+  std::vector<std::string> errs(nsys);
+  auto worker = [&](int w) {
+    cudaSetDevice(dev);
+    for (;;) {
+      int i = next.fetch_add(1);
+      if (i >= nsys) break;
+      ampcg_result* r = results ? &results[i] : nullptr;
+      sts[i] = solve_impl(systems[i], b[i], x[i], tol, maxit, policy, r, nullptr, ws[w]);
+      if (sts[i] != AMPCG_OK && sts[i] != AMPCG_NOT_CONVERGED) errs[i] = g_err;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < W; ++w) th.emplace_back(worker, w);
+  worker(0);
+  for (auto& t : th) t.join();
+  // later work on the systems' streams waits for the batch
+  for (int w = 0; w < W; ++w) {
+    cudaEventRecord(ev, ws[w]);
+    for (int i = 0; i < nsys; ++i) cudaStreamWaitEvent(systems[i]->stream, ev, 0);
+  }
+  cleanup();
+  for (int i = 0; i < nsys; ++i) {
+    if (sts[i] == AMPCG_NOT_CONVERGED && st == AMPCG_OK) st = AMPCG_NOT_CONVERGED;
+    if (sts[i] != AMPCG_OK && sts[i] != AMPCG_NOT_CONVERGED) {
+      g_err = "system " + std::to_string(i) + ": " + errs[i];
+      return sts[i];
+    }
+  }
   return st;
 }

@@ -44,3 +44,17 @@ def test_elasticity_assembly_spd_and_blocks():
     assert np.allclose(dense, dense.T, rtol=0, atol=1e-12 * np.abs(dense).max())
     assert np.linalg.eigvalsh(dense).min() > 0
     assert np.diff(B.browptr).max() == 27
+
+
+def test_batched_2d_cells_structure():
+    a = W.diffusion2d_cells(6, 1000)
+    A = a.to_dense()
+    assert np.array_equal(A, A.T) and np.linalg.eigvalsh(A).min() > 0
+    c = np.exp(np.random.default_rng(1000).standard_normal((6, 6))).reshape(-1)
+    # interior face between cells 0 and 1: geometric mean; corner row sum: its 2 boundary faces
+    assert A[0, 1] == -np.sqrt(c[0] * c[1])
+    assert np.isclose(A[0].sum(), 2 * c[0])
+    mats, rhs = W.batch_2d(16, seed=0)
+    sides = [int(round(np.sqrt(m.n))) for m in mats]
+    assert all(32 <= s <= 256 for s in sides) and len(set(sides)) > 8
+    assert all(len(r) == m.n for m, r in zip(mats, rhs))

@@ -291,3 +291,40 @@ def elasticity_q1(n: int, seed: int = 0, nu: float = 0.3, e_lo: float = 1.0, e_h
     np.add.at(browptr, brow + 1, 1)
     browptr = np.cumsum(browptr).astype(np.int32)
     return BSR(nb, 3, browptr, bcol, bval, {"kind": "elasticity_q1", "n": n, "nu": nu, "dof": nb * 3})
+
+
+def diffusion2d_cells(s: int, seed: int) -> CSR:
+    """2D 5-point diffusion on an s x s grid of cells, Dirichlet: cell
+    coefficients exp(N(0,1)) (seed), interior faces the geometric mean of the
+    two cells, boundary faces the cell's coefficient; a_ii = sum of faces."""
+    c = np.exp(np.random.default_rng(seed).standard_normal((s, s)))
+    n = s * s
+    idx = np.arange(n)
+    x, y = idx % s, idx // s
+    cf = c.reshape(-1)
+    neg = -np.ones(n, dtype=np.int64)
+    diag = np.zeros(n)
+    cols, vals = [], []
+    for nb in [(y > 0, -s), (x > 0, -1), None, (x < s - 1, 1), (y < s - 1, s)]:
+        if nb is None:
+            cols.append(idx)
+            vals.append(diag)  # filled below (same array object)
+            continue
+        inside, off = nb
+        j = np.where(inside, idx + off, idx)
+        k = np.where(inside, np.sqrt(cf * cf[j]), cf)
+        diag += k
+        cols.append(np.where(inside, idx + off, neg))
+        vals.append(-k)
+    a = _assemble(n, cols, vals)
+    a.info = {"kind": "diffusion2d_cells", "s": s, "seed": seed}
+    return a
+
+
+def batch_2d(nsys: int, seed: int = 0, smin: int = 32, smax: int = 256):
+    """Batched workload: nsys systems with sides uniform in {smin..smax} (seed),
+    system i from diffusion2d_cells(side_i, 1000 + i), b_i ~ U[-1,1] (seed i)."""
+    sides = np.random.default_rng(seed).integers(smin, smax + 1, nsys)
+    mats = [diffusion2d_cells(int(s), 1000 + i) for i, s in enumerate(sides)]
+    rhs = [rhs_uniform(m.n, i) for i, m in enumerate(mats)]
+    return mats, rhs
