@@ -84,8 +84,8 @@ typedef enum {
 typedef struct {
   int u0;             /* initial (maximum) u_z precision, ampcg_prec */
   int criterion;      /* ampcg_criterion */
-  int d;              /* window delay d of Eq. (eta_k); paper: 10 */
-  int ell;            /* rate window ell of Eq. (linear criterion); paper: 5 */
+  int d;              /* window delay d of Eq. (eta_k); paper: 10; 0..62 */
+  int ell;            /* rate window ell of Eq. (linear criterion); paper: 5; 1..63 */
   double C;           /* Assumption 1 constant; paper: 1 */
   double tau_zs;      /* nu_k threshold for u_z -> FP32; paper: 1e-4 */
   double tau_zh;      /* nu_k threshold for u_z -> FP16; paper: 1e-6 */

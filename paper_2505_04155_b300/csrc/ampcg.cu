@@ -109,7 +109,6 @@ struct ampcg_ctx {
   DevState* st = nullptr;       // device
   DevState* hst = nullptr;      // pinned host mirror
   double* dhist = nullptr;      // delta history
-  double* rhist = nullptr;      // relres history
   unsigned char* phist = nullptr;
   int hist_cap = 0;
   // launch shapes
@@ -181,7 +180,7 @@ static void release(ampcg_ctx* c) {
   void* ptrs[] = {c->ah64, c->ah32, c->ah16, c->ds64, c->ds32, c->ds16, c->cres, c->cd0, c->cd1, c->cu,
                   c->rowptr, c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
                   c->dinv16, c->x, c->b, c->r64, c->t, c->r32, c->z, c->p0, c->p1, c->q,
-                  c->part, c->pmax, c->st, c->dhist, c->rhist, c->phist};
+                  c->part, c->pmax, c->st, c->dhist, c->phist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hst) cudaFreeHost(c->hst);
@@ -487,15 +486,12 @@ static ampcg_status ensure_hist(ampcg_ctx* c, int maxit) {
   int need = maxit + 2;
   if (need <= c->hist_cap) return AMPCG_OK;
   if (c->dhist) cudaFree(c->dhist);
-  if (c->rhist) cudaFree(c->rhist);
   if (c->phist) cudaFree(c->phist);
   c->dhist = nullptr;
-  c->rhist = nullptr;
   c->phist = nullptr;
   c->hist_cap = 0;
   ampcg_status s;
   if ((s = dalloc(&c->dhist, need)) != AMPCG_OK) return s;
-  if ((s = dalloc(&c->rhist, need)) != AMPCG_OK) return s;
   if ((s = dalloc(&c->phist, need)) != AMPCG_OK) return s;
   c->hist_cap = need;
   return AMPCG_OK;
@@ -729,7 +725,8 @@ static ampcg_status check_policy(const ampcg_policy* p) {
     return fail(AMPCG_ERR_INVALID_ARG, "precision codes: u0/fixed_uz in {0,1,2}, fixed_ur in {0,1}");
   if (p->criterion < 0 || p->criterion > 2) return fail(AMPCG_ERR_INVALID_ARG, "bad criterion");
   if (p->scale < 0 || p->scale > 2) return fail(AMPCG_ERR_INVALID_ARG, "bad scale mode");
-  if (p->d < 0 || p->ell < 1) return fail(AMPCG_ERR_INVALID_ARG, "need d >= 0 and ell >= 1");
+  if (p->d < 0 || p->ell < 1 || p->d > kRing - 2 || p->ell > kRing - 1)
+    return fail(AMPCG_ERR_INVALID_ARG, "need 0 <= d <= %d and 1 <= ell <= %d", kRing - 2, kRing - 1);
   if (p->verify_refresh < 0 || p->graph_chunk < 0)
     return fail(AMPCG_ERR_INVALID_ARG, "verify_refresh and graph_chunk must be >= 0");
   return AMPCG_OK;
@@ -757,7 +754,6 @@ static void init_state(DevState* h, const ampcg_policy* p, double tol, int maxit
   h->k_body = -1;
   h->switch_iter[0] = h->switch_iter[1] = h->switch_iter[2] = -1;
   h->delta_hist = c ? c->dhist : nullptr;
-  h->relres_hist = c ? c->rhist : nullptr;
   h->prec_hist = c ? c->phist : nullptr;
 }
 
@@ -907,8 +903,8 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   CUDA_TRY(cudaMemcpyAsync(x, c->x, vb, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   int iters = h.k;
   if (res) {
-    if (res->relres_hist)
-      CUDA_TRY(cudaMemcpyAsync(res->relres_hist, c->rhist, (iters + 1) * sizeof(double),
+    if (res->relres_hist)   // delta_k, divided by ||b|| below
+      CUDA_TRY(cudaMemcpyAsync(res->relres_hist, c->dhist, (iters + 1) * sizeof(double),
                                cudaMemcpyDeviceToHost, s));
     if (res->prec_hist && iters > 0)
       CUDA_TRY(cudaMemcpyAsync(res->prec_hist, c->phist, iters, cudaMemcpyDeviceToHost, s));
@@ -922,6 +918,8 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
     res->status = h.status;
     res->true_relres = h.true_relres;
     res->updated_relres = h.delta / h.nb;
+    if (res->relres_hist)
+      for (int i = 0; i <= iters; ++i) res->relres_hist[i] /= h.nb;
     for (int i = 0; i < 3; ++i) res->switch_iter[i] = h.switch_iter[i];
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     res->kernel_launches = launches;
@@ -1046,7 +1044,6 @@ extern "C" ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const d
   if (e == cudaSuccess) e = cudaMalloc(&d_st, sizeof(DevState));
   if (e == cudaSuccess) {
     h.delta_hist = d_delta;
-    h.relres_hist = nullptr;
     h.prec_hist = d_ph;
     e = cudaMemcpy(d_delta, delta, (m + 1) * sizeof(double), cudaMemcpyHostToDevice);
   }
@@ -1144,7 +1141,6 @@ extern "C" ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy,
   h.tol_nb = tol * nb;
   h.maxr = 1.0;
   h.delta_hist = sc->delta;
-  h.relres_hist = nullptr;
   h.prec_hist = sc->prec;
   cudaError_t e = cudaMemcpy(sc->delta, delta, (size_t)(m + 1) * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(&sc->st, &h, sizeof(DevState), cudaMemcpyHostToDevice);

@@ -295,24 +295,75 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
 }
 
 // Fixed-order sum of G partials (block g's value j at part[g*stride + j]) in
-// the last block; thread 0 gets the totals.
+// the last block; thread 0 gets the totals.  Thread t adds partials t, t + B,
+// t + 2B, ... in that order; the loads of up to four of them are issued
+// before the first add, so the tail pays one memory round trip, not G / B.
 template <int NV>
 __device__ __forceinline__ void final_sum(const double* part, int G, int stride, double (&out)[NV]) {
 #pragma unroll
   for (int j = 0; j < NV; ++j) out[j] = 0.0;
-  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+  const int B = blockDim.x;
+  for (int g0 = threadIdx.x; g0 < G; g0 += 4 * B) {
+    double v[4][NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) out[j] += __ldcg(part + (size_t)g * stride + j);
+    for (int u = 0; u < 4; ++u) {
+      const int g = g0 + u * B;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[u][j] = (g < G) ? __ldcg(part + (size_t)g * stride + j) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (g0 + u * B < G) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] += v[u][j];
+      }
+    }
   }
   block_sum<NV>(out);
 }
 
 __device__ __forceinline__ unsigned long long final_max(const unsigned long long* part, int G) {
   unsigned long long m = 0ull;
-  for (int g = threadIdx.x; g < G; g += blockDim.x) {
-    unsigned long long v = __ldcg(part + g);
-    m = v > m ? v : m;
+  const int B = blockDim.x;
+  for (int g0 = threadIdx.x; g0 < G; g0 += 4 * B) {
+    unsigned long long v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (g0 + u * B < G) ? __ldcg(part + g0 + u * B) : 0ull;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m = v[u] > m ? v[u] : m;
   }
+  return block_max(m);
+}
+
+// final_sum<NV> and final_max together: all loads issued before any use.
+template <int NV>
+__device__ __forceinline__ unsigned long long final_sum_max(const double* part, int stride,
+                                                            const unsigned long long* pmax, int G,
+                                                            double (&out)[NV]) {
+#pragma unroll
+  for (int j = 0; j < NV; ++j) out[j] = 0.0;
+  unsigned long long m = 0ull;
+  const int B = blockDim.x;
+  for (int g0 = threadIdx.x; g0 < G; g0 += 4 * B) {
+    double v[4][NV];
+    unsigned long long w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int g = g0 + u * B;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[u][j] = (g < G) ? __ldcg(part + (size_t)g * stride + j) : 0.0;
+      w[u] = (g < G) ? __ldcg(pmax + g) : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (g0 + u * B < G) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) out[j] += v[u][j];
+      }
+      m = w[u] > m ? w[u] : m;
+    }
+  }
+  block_sum<NV>(out);
   return block_max(m);
 }
 

@@ -35,7 +35,13 @@ enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = -3, ST_NONFINITE = -4, ST
 // Unit roundoff of binary32 (2^-24), the eps_32 of Eq. (eta_k).
 #define AMPCG_EPS32 5.9604644775390625e-08
 
-struct DevState {
+// The last kRing residual norms delta_t live in the state itself (dring[t %
+// kRing]), so the selector's indicator window arrives with the one
+// cooperative load of the state in a reduction tail (d <= kRing - 2,
+// ell <= kRing - 1).
+constexpr int kRing = 64;
+
+struct __align__(16) DevState {
   // iteration control
   int k, done, status, maxit;
   int uz, ur;          // precisions of the current iteration
@@ -56,12 +62,42 @@ struct DevState {
   float sig_f;              // 2^sig_e: exact scale of r in binary32 dot products
   int sig_e;
   double inv_sig, inv_sig2; // 2^-sig_e, 2^-2 sig_e
+  // selector brackets (prep_selector)
+  double inv_tol_nb, tzs_lo, tzs_hi, tzh_lo, tzh_hi, c_lin;
   double rho, rho_prev, beta, gamma, alpha, true_relres;
   unsigned int ticket[4];
   // histories (device)
   double* delta_hist;        // [maxit + 2]
-  double* relres_hist;       // [maxit + 2]
   unsigned char* prec_hist;  // [maxit + 1]
+  double dring[kRing];       // delta_t at t % kRing
+};
+static_assert(sizeof(DevState) % 16 == 0, "state is copied in 16-byte words");
+
+// Reduction tails work on a shared-memory copy of the state: the block loads
+// it with one round of 16-byte loads (issued together with the partials'
+// loads), thread 0 runs the scalar step at shared-memory latency, and the
+// block writes it back.  Only the last block of a kernel touches the state
+// after the kernel's start, so the copy is not raced.
+__device__ __forceinline__ void state_load(DevState* s, const DevState* st) {
+  const int4* src = reinterpret_cast<const int4*>(st);
+  int4* dst = reinterpret_cast<int4*>(s);
+  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 16); i += blockDim.x) dst[i] = __ldcg(src + i);
+}
+__device__ __forceinline__ void state_store(DevState* st, const DevState* s) {
+  __syncthreads();
+  const int4* src = reinterpret_cast<const int4*>(s);
+  int4* dst = reinterpret_cast<int4*>(st);
+  for (int i = threadIdx.x; i < (int)(sizeof(DevState) / 16); i += blockDim.x) dst[i] = src[i];
+}
+
+// delta_t from the ring, or from a full history array (selector replay)
+struct RingHist {
+  const DevState* s;
+  __device__ __forceinline__ double operator()(int t) const { return s->dring[t & (kRing - 1)]; }
+};
+struct ArrayHist {
+  const double* d;
+  __device__ __forceinline__ double operator()(int t) const { return d[t]; }
 };
 
 // Precision pair check at kernel entry: a variant launched for another pair
@@ -97,49 +133,145 @@ struct Sell {
 // Scalar-side pieces of the algorithm, evaluated by one thread -------------
 
 // Eq. (eta_k) with reading R3 (no estimate before k >= d; ||r_{-1}|| := ||r_0||).
-__device__ __forceinline__ double eta_window_dev(const double* delta, int k, int d, double C) {
+template <class H>
+__device__ __forceinline__ double eta_window_dev(H delta, int k, int d, double C) {
   if (k < d) return __longlong_as_double(0x7ff0000000000000ll);
   double eta = 0.0;
   double c3 = __dadd_rn(3.0, C), c2 = __dadd_rn(2.0, C);
   for (int t = k - d; t <= k; ++t) {
-    double prev = (t >= 1) ? delta[t - 1] : delta[0];
-    double term = __dmul_rn(AMPCG_EPS32, __dadd_rn(__dmul_rn(c3, prev), __dmul_rn(c2, delta[t])));
+    double prev = (t >= 1) ? delta(t - 1) : delta(0);
+    double term = __dmul_rn(AMPCG_EPS32, __dadd_rn(__dmul_rn(c3, prev), __dmul_rn(c2, delta(t))));
     eta = __dadd_rn(eta, term);
   }
   return eta;
 }
 
 // Eq. (linear criterion) with reading R3 and +inf when the rate is >= 1.
-__device__ __forceinline__ double eta_linear_dev(const double* delta, int k, int ell, double C) {
+template <class H>
+__device__ __forceinline__ double eta_linear_dev(H delta, int k, int ell, double C) {
   const double inf = __longlong_as_double(0x7ff0000000000000ll);
   if (k < ell || k < 1) return inf;
-  double rho = pow(delta[k] / delta[k - ell], 1.0 / (double)ell);
+  double rho = pow(delta(k) / delta(k - ell), 1.0 / (double)ell);
   if (!(rho < 1.0)) return inf;
   double c = __dmul_rn(AMPCG_EPS32, __dadd_rn(5.0, __dmul_rn(2.0, C)));
-  return __dmul_rn(c, delta[k - 1]) / __dadd_rn(1.0, -rho);
+  return __dmul_rn(c, delta(k - 1)) / __dadd_rn(1.0, -rho);
 }
 
-// Eq. (precision_selector): u_z from nu_k and u0, u_r from eta_k (reading R2).
-__device__ __forceinline__ void select_dev(double nu, int u0, double tzs, double tzh, double eta,
-                                           double tol_nb, int& uz, int& ur) {
-  if (nu >= tzs) uz = u0;
-  else if (nu >= tzh) uz = (u0 > P32) ? u0 : P32;
-  else uz = (u0 > P16) ? u0 : P16;
-  ur = (eta <= tol_nb) ? P32 : P64;
+// ---------------------------------------------------------------------------
+// The selector's comparisons without the slow scalar path.
+//
+// On B300 a dependent binary64 operation costs ~64 cycles, a division ~550
+// and pow ~5800, and this scalar step sits on the critical path of every
+// iteration (one thread of the last block).  Each comparison the selector
+// makes is therefore first tried against precomputed brackets that settle it
+// whenever the two sides differ by more than 1e-12 (u_z tests) or 1e-9
+// (u_r test) relative -- margins far above the rounding errors of both the
+// bracket and the binary64 evaluation -- and only a comparison inside the
+// margin evaluates Eq. (precision_selector) / Eq. (linear criterion) in
+// binary64 exactly as written.  The outcome is always that of the binary64
+// evaluation; the brackets only skip work.
+
+constexpr double kNuMargin = 1e-12;
+constexpr double kEtaMargin = 1e-9;
+
+// Brackets from nb, tol_nb, tau_zs, tau_zh, C (once per solve).
+__device__ __forceinline__ void prep_selector(DevState* s) {
+  s->inv_tol_nb = 1.0 / s->tol_nb;
+  double zs = __dmul_rn(s->tau_zs, s->nb), zh = __dmul_rn(s->tau_zh, s->nb);
+  s->tzs_lo = __dmul_rn(zs, 1.0 - kNuMargin);
+  s->tzs_hi = __dmul_rn(zs, 1.0 + kNuMargin);
+  s->tzh_lo = __dmul_rn(zh, 1.0 - kNuMargin);
+  s->tzh_hi = __dmul_rn(zh, 1.0 + kNuMargin);
+  s->c_lin = __dmul_rn(AMPCG_EPS32, __dadd_rn(5.0, __dmul_rn(2.0, s->C)));
+}
+
+// fl(delta / nb) >= tau
+__device__ __forceinline__ bool nu_at_least(double delta, double nb, double tau, double lo, double hi) {
+  if (delta > hi) return true;
+  if (delta < lo) return false;
+  return __ddiv_rn(delta, nb) >= tau;
+}
+
+// y^e for e >= 1 by repeated squaring
+__device__ __forceinline__ double ipow(double y, int e) {
+  double r = 1.0;
+  while (e) {
+    if (e & 1) r = __dmul_rn(r, y);
+    y = __dmul_rn(y, y);
+    e >>= 1;
+  }
+  return r;
+}
+
+// eta_k <= tol ||b|| for Eq. (linear criterion).  In exact arithmetic, with
+// t = c delta_{k-1} / T and rho = (delta_k / delta_{k-ell})^(1/ell):
+// eta_k <= T  <=>  rho <= 1 - t  <=>  delta_k <= (1 - t)^ell delta_{k-ell};
+// and eta_k >= c delta_{k-1} > T whenever t > 1.
+template <class H>
+__device__ __forceinline__ bool linear_switch(const DevState* s, H delta, int k) {
+  const int ell = s->ell;
+  if (k < ell || k < 1) return false;   // eta_k = +inf (reading R3)
+  double t = __dmul_rn(__dmul_rn(s->c_lin, delta(k - 1)), s->inv_tol_nb);
+  if (t > 1.0 + kEtaMargin) return false;
+  if (t < 1.0 - 1e-3) {
+    double rhs = __dmul_rn(ipow(__dadd_rn(1.0, -t), ell), delta(k - ell));
+    double dk = delta(k);
+    if (dk < __dmul_rn(rhs, 1.0 - kEtaMargin)) return true;
+    if (dk > __dmul_rn(rhs, 1.0 + kEtaMargin)) return false;
+  }
+  return eta_linear_dev(delta, k, ell, s->C) <= s->tol_nb;
+}
+
+// 2^e as binary64 / binary32 (round-to-nearest-even of the exact power),
+// built from the bit pattern.
+__device__ __forceinline__ double pow2_f64(int e) {
+  if (e > 1023) return __longlong_as_double(0x7ff0000000000000ll);
+  if (e >= -1022) return __longlong_as_double((long long)(e + 1023) << 52);
+  if (e >= -1074) return __longlong_as_double(1ll << (e + 1074));
+  return 0.0;
+}
+__device__ __forceinline__ float pow2_f32(int e) {
+  if (e > 127) return __uint_as_float(0x7f800000u);
+  if (e >= -126) return __uint_as_float((unsigned)(e + 127) << 23);
+  if (e >= -149) return __uint_as_float(1u << (e + 149));
+  return 0.f;
+}
+
+// ceil(log2 m) for a positive finite binary64 m, from its bit pattern.
+__device__ __forceinline__ int ceil_log2(double m) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(m);
+  int eb = (int)(b >> 52);
+  unsigned long long f = b & 0x000FFFFFFFFFFFFFull;
+  if (eb == 0) {                                  // subnormal: m = f 2^-1074
+    int p = 63 - __clzll((long long)f);
+    return p - 1074 + ((f & (f - 1ull)) ? 1 : 0);
+  }
+  return eb - 1023 + (f ? 1 : 0);
 }
 
 // Decide the precisions of iteration st->k (Alg. 3 lines 3-4), the storage
-// conversions they imply, and omega_k (reading R5).  Thread 0 of one block.
-__device__ void decide(DevState* st) {
+// conversions they imply, and omega_k (reading R5).  Thread 0 of one block;
+// hist(t) gives delta_t.  Eq. (precision_selector): u_z from nu_k and u0, u_r
+// from eta_k (reading R2).  With the latch on, a u_r already at FP32 cannot
+// change and eta_k is not evaluated.
+template <class H>
+__device__ void decide(DevState* st, H hist) {
   int k = st->k;
   int uz, ur;
   if (st->criterion == CRIT_FIXED) {
     uz = st->fixed_uz;
     ur = st->fixed_ur;
   } else {
-    double eta = (st->criterion == CRIT_WINDOW) ? eta_window_dev(st->delta_hist, k, st->d, st->C)
-                                                : eta_linear_dev(st->delta_hist, k, st->ell, st->C);
-    select_dev(st->delta_hist[k] / st->nb, st->u0, st->tau_zs, st->tau_zh, eta, st->tol_nb, uz, ur);
+    const double dk = hist(k);
+    const int u0 = st->u0;
+    if (nu_at_least(dk, st->nb, st->tau_zs, st->tzs_lo, st->tzs_hi)) uz = u0;
+    else if (nu_at_least(dk, st->nb, st->tau_zh, st->tzh_lo, st->tzh_hi)) uz = (u0 > P32) ? u0 : P32;
+    else uz = (u0 > P16) ? u0 : P16;
+    bool sw;
+    if (st->latch && st->ur == P32) sw = true;
+    else if (st->criterion == CRIT_WINDOW) sw = eta_window_dev(hist, k, st->d, st->C) <= st->tol_nb;
+    else sw = linear_switch(st, hist, k);
+    ur = sw ? P32 : P64;
     if (st->latch) {
       if (uz < st->uz) uz = st->uz;
       if (ur < st->ur) ur = st->ur;
@@ -153,40 +285,32 @@ __device__ void decide(DevState* st) {
   st->uz = uz;
   st->ur = ur;
   st->prec_hist[k] = (unsigned char)((uz << 4) | ur);
+  // c = ceil(log2 max|r_k|) (none for max|r_k| = 0 or non-finite)
+  const double mr = st->maxr;
+  const bool have_c = mr > 0.0 && mr < __longlong_as_double(0x7ff0000000000000ll);
+  const int cl = have_c ? ceil_log2(mr) : 0;
   // omega_k
   double om = 1.0;
   int pow2 = 1, e = 0;
   if (st->scale == SCALE_L2) {
     om = 1.0 / st->delta;
     pow2 = 0;
-  } else if (st->scale == SCALE_LINF_POW2) {
-    double m = st->maxr;
-    if (m > 0.0 && m < __longlong_as_double(0x7ff0000000000000ll)) {
-      int E;
-      double f = frexp(m, &E);
-      int c = (f == 0.5) ? E - 1 : E;
-      e = -c;
-      om = ldexp(1.0, e);
-    }
+  } else if (st->scale == SCALE_LINF_POW2 && have_c) {
+    e = -cl;
+    om = pow2_f64(e);
   }
   st->omega = om;
-  st->omega_f = __double2float_rn(om);
+  st->omega_f = pow2 ? pow2_f32(e) : __double2float_rn(om);
   st->omega_pow2 = pow2;
   st->omega_e = e;
   // sigma_k = 2^-ceil(log2 max|r_k|) (clamped to binary32's normal range):
   // scales r in binary32 inner products so that their terms stay in range
-  int se = 0;
-  double mr = st->maxr;
-  if (mr > 0.0 && mr < __longlong_as_double(0x7ff0000000000000ll)) {
-    int E;
-    double f = frexp(mr, &E);
-    se = -((f == 0.5) ? E - 1 : E);
-    se = se < -126 ? -126 : (se > 126 ? 126 : se);
-  }
+  int se = have_c ? -cl : 0;
+  se = se < -126 ? -126 : (se > 126 ? 126 : se);
   st->sig_e = se;
-  st->sig_f = __double2float_rn(ldexp(1.0, se));
-  st->inv_sig = ldexp(1.0, -se);
-  st->inv_sig2 = ldexp(1.0, -2 * se);
+  st->sig_f = pow2_f32(se);
+  st->inv_sig = pow2_f64(-se);
+  st->inv_sig2 = pow2_f64(-2 * se);
 }
 
 // ---------------------------------------------------------------------------
@@ -289,6 +413,23 @@ struct Bufs {
   unsigned long long* pmax; // per-block partial maxima [G]
 };
 
+// Alg. 3 lines 7-10 on the state copy: rho_k, its checks (reading R12) and
+// beta_{k-1} = rho_k / rho_{k-1}; completes the storage conversions.
+__device__ __forceinline__ void rho_step(DevState* s, double r) {
+  s->rho = r;
+  if (!isfinite(r)) { s->status = ST_NONFINITE; s->done = 1; return; }
+  if (!(r > 0.0)) { s->status = ST_BREAKDOWN; s->done = 1; return; }
+  double beta = s->first ? 0.0 : r / s->rho_prev;
+  s->beta = beta;
+  s->beta_f = __double2float_rn(beta);
+  s->r_cast = 0;
+  if (s->p_cast) {
+    s->pcur ^= 1;
+    s->uz_p = s->uz;
+    s->p_cast = 0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Initial residual r_0 = b - A x_0 (FP64), ||b||, ||r_0||, max|r_0|; the last
 // block stores delta_0 and decides iteration 0.  One thread per row.
@@ -320,33 +461,39 @@ __global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
     B.pmax[blockIdx.x] = mx;
   }
   if (!last_block(&st->ticket[0])) return;
+  __shared__ DevState S;
+  state_load(&S, st);
   double vv[2];
-  final_sum<2>(B.part, gridDim.x, 4, vv);
-  unsigned long long m = final_max(B.pmax, gridDim.x);
+  unsigned long long m = final_sum_max<2>(B.part, 4, B.pmax, gridDim.x, vv);
+  double d0 = 0.0, nb = 0.0;
   if (threadIdx.x == 0) {
-    st->ticket[0] = 0u;
-    double nb = sqrt(vv[0]);
-    double d0 = sqrt(vv[1]);
-    st->nb = nb;
-    st->tol_nb = st->tol * nb;
-    st->delta = d0;
-    st->maxr = __longlong_as_double((long long)m);
-    st->delta_hist[0] = d0;
-    st->relres_hist[0] = d0 / nb;
-    st->k = 0;
-    st->done = 0;
-    st->status = ST_NOT_CONVERGED;
+    S.ticket[0] = 0u;
+    nb = sqrt(vv[0]);
+    d0 = sqrt(vv[1]);
+    S.nb = nb;
+    S.tol_nb = S.tol * nb;
+    prep_selector(&S);
+    S.delta = d0;
+    S.maxr = __longlong_as_double((long long)m);
+    S.dring[0] = d0;
+    S.k = 0;
+    S.done = 0;
+    S.status = ST_NOT_CONVERGED;
     if (!isfinite(nb) || !isfinite(d0)) {
-      st->status = ST_NONFINITE;
-      st->done = 1;
-    } else if (d0 <= st->tol_nb) {
-      st->status = ST_OK;
-      st->done = 1;
-    } else if (st->maxit <= 0) {
-      st->done = 1;
+      S.status = ST_NONFINITE;
+      S.done = 1;
+    } else if (d0 <= S.tol_nb) {
+      S.status = ST_OK;
+      S.done = 1;
+    } else if (S.maxit <= 0) {
+      S.done = 1;
     } else {
-      decide(st);
+      decide(&S, RingHist{&S});
     }
+  }
+  state_store(st, &S);
+  if (threadIdx.x == 0) {
+    S.delta_hist[0] = d0;
   }
 }
 
@@ -474,24 +621,15 @@ __global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st
   }
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[0])) return;
+  __shared__ DevState S;
+  state_load(&S, st);
   double tot[1];
   final_sum<1>(B.part, gridDim.x, 1, tot);
   if (threadIdx.x == 0) {
-    st->ticket[0] = 0u;
-    double r = tot[0];
-    st->rho = r;
-    if (!isfinite(r)) { st->status = ST_NONFINITE; st->done = 1; return; }
-    if (!(r > 0.0)) { st->status = ST_BREAKDOWN; st->done = 1; return; }
-    double beta = st->first ? 0.0 : r / st->rho_prev;
-    st->beta = beta;
-    st->beta_f = __double2float_rn(beta);
-    st->r_cast = 0;
-    if (st->p_cast) {
-      st->pcur ^= 1;
-      st->uz_p = st->uz;
-      st->p_cast = 0;
-    }
+    S.ticket[0] = 0u;
+    rho_step(&S, tot[0]);
   }
+  state_store(st, &S);
 }
 
 // ---------------------------------------------------------------------------
@@ -725,18 +863,27 @@ __global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
   }
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[1])) return;
+  __shared__ DevState S;
+  state_load(&S, st);
   double tot[1];
   final_sum<1>(B.part, gridDim.x, 1, tot);
   if (threadIdx.x == 0) {
-    st->ticket[1] = 0u;
+    S.ticket[1] = 0u;
     double g = tot[0];
-    st->gamma = g;
-    if (!isfinite(g)) { st->status = ST_NONFINITE; st->done = 1; return; }
-    if (!(g > 0.0)) { st->status = ST_BREAKDOWN; st->done = 1; return; }
-    double a = st->rho / g;
-    st->alpha = a;
-    st->alpha_f = __double2float_rn(a);
+    S.gamma = g;
+    if (!isfinite(g)) {
+      S.status = ST_NONFINITE;
+      S.done = 1;
+    } else if (!(g > 0.0)) {
+      S.status = ST_BREAKDOWN;
+      S.done = 1;
+    } else {
+      double a = S.rho / g;
+      S.alpha = a;
+      S.alpha_f = __double2float_rn(a);
+    }
   }
+  state_store(st, &S);
 }
 
 // ---------------------------------------------------------------------------
@@ -818,35 +965,43 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st,
     B.pmax[blockIdx.x] = mx;
   }
   if (!last_block(&st->ticket[2])) return;
+  __shared__ DevState S;
+  state_load(&S, st);
   double tot[1];
-  final_sum<1>(B.part, gridDim.x, 1, tot);
-  unsigned long long m = final_max(B.pmax, gridDim.x);
+  unsigned long long m = final_sum_max<1>(B.part, 1, B.pmax, gridDim.x, tot);
+  double d = 0.0;
+  int k1 = 0;
+  unsigned next = AMPCG_PHASE_NONE;
   if (threadIdx.x == 0) {
-    st->ticket[2] = 0u;
-    double d = sqrt(tot[0]);
-    int k1 = st->k + 1;
-    st->delta = d;
-    st->maxr = __longlong_as_double((long long)m);
-    st->delta_hist[k1] = d;
-    st->relres_hist[k1] = d / st->nb;
-    st->rho_prev = st->rho;
-    st->first = 0;
-    st->pcur ^= 1;        // p_k is now the previous direction
-    st->uz_p = st->uz;
-    st->k = k1;
+    S.ticket[2] = 0u;
+    d = sqrt(tot[0]);
+    k1 = S.k + 1;
+    S.delta = d;
+    S.maxr = __longlong_as_double((long long)m);
+    S.dring[k1 & (kRing - 1)] = d;
+    S.rho_prev = S.rho;
+    S.first = 0;
+    S.pcur ^= 1;        // p_k is now the previous direction
+    S.uz_p = S.uz;
+    S.k = k1;
     if (!isfinite(d)) {
-      st->status = ST_NONFINITE;
-      st->done = 1;
-    } else if (d <= st->tol_nb) {
-      st->status = ST_OK;
-      st->done = 1;
-    } else if (k1 >= st->maxit) {
-      st->status = ST_NOT_CONVERGED;
-      st->done = 1;
+      S.status = ST_NONFINITE;
+      S.done = 1;
+    } else if (d <= S.tol_nb) {
+      S.status = ST_OK;
+      S.done = 1;
+    } else if (k1 >= S.maxit) {
+      S.status = ST_NOT_CONVERGED;
+      S.done = 1;
     } else {
-      decide(st);
+      decide(&S, RingHist{&S});
     }
-    if (has_next) cudaGraphSetConditional(h_next, st->done ? AMPCG_PHASE_NONE : 2 * st->uz + st->ur);
+    if (!S.done) next = 2 * S.uz + S.ur;
+  }
+  state_store(st, &S);
+  if (threadIdx.x == 0) {
+    S.delta_hist[k1] = d;
+    if (has_next) cudaGraphSetConditional(h_next, next);
   }
 }
 
@@ -887,12 +1042,15 @@ __global__ void __launch_bounds__(256) k_true_residual(Sell A, Bufs B, DevState*
   block_sum<1>(v);
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[3])) return;
+  __shared__ DevState S;
+  state_load(&S, st);
   double tot[1];
   final_sum<1>(B.part, gridDim.x, 1, tot);
   if (threadIdx.x == 0) {
-    st->ticket[3] = 0u;
-    st->true_relres = sqrt(tot[0]) / st->nb;
+    S.ticket[3] = 0u;
+    S.true_relres = sqrt(tot[0]) / S.nb;
   }
+  state_store(st, &S);
 }
 
 // Residual replacement (reading R9): r <- round_ur(t), delta, max|r|; the
@@ -919,26 +1077,32 @@ __global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st
     B.pmax[blockIdx.x] = mx;
   }
   if (!last_block(&st->ticket[3])) return;
+  __shared__ DevState S;
+  state_load(&S, st);
   double tot[1];
-  final_sum<1>(B.part, gridDim.x, 1, tot);
-  unsigned long long m = final_max(B.pmax, gridDim.x);
+  unsigned long long m = final_sum_max<1>(B.part, 1, B.pmax, gridDim.x, tot);
+  double d = 0.0;
+  int k = 0;
   if (threadIdx.x == 0) {
-    st->ticket[3] = 0u;
-    double d = sqrt(tot[0]);
-    int k = st->k;
-    st->delta = d;
-    st->maxr = __longlong_as_double((long long)m);
-    st->delta_hist[k] = d;
-    st->relres_hist[k] = d / st->nb;
-    st->refreshes += 1;
-    if (d <= st->tol_nb) {
-      st->status = ST_OK;
-      st->done = 1;
+    S.ticket[3] = 0u;
+    d = sqrt(tot[0]);
+    k = S.k;
+    S.delta = d;
+    S.maxr = __longlong_as_double((long long)m);
+    S.dring[k & (kRing - 1)] = d;
+    S.refreshes += 1;
+    if (d <= S.tol_nb) {
+      S.status = ST_OK;
+      S.done = 1;
     } else {
-      st->status = ST_NOT_CONVERGED;
-      st->done = 0;
-      decide(st);
+      S.status = ST_NOT_CONVERGED;
+      S.done = 0;
+      decide(&S, RingHist{&S});
     }
+  }
+  state_store(st, &S);
+  if (threadIdx.x == 0) {
+    S.delta_hist[k] = d;
   }
 }
 
@@ -1397,24 +1561,15 @@ __global__ void __launch_bounds__(256) k_cheb_final(Bufs B, Cheb C, int64_t n, D
   }
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[0])) return;
+  __shared__ DevState S;
+  state_load(&S, st);
   double tot[1];
   final_sum<1>(B.part, gridDim.x, 1, tot);
   if (threadIdx.x == 0) {
-    st->ticket[0] = 0u;
-    double r = tot[0];
-    st->rho = r;
-    if (!isfinite(r)) { st->status = ST_NONFINITE; st->done = 1; return; }
-    if (!(r > 0.0)) { st->status = ST_BREAKDOWN; st->done = 1; return; }
-    double beta = st->first ? 0.0 : r / st->rho_prev;
-    st->beta = beta;
-    st->beta_f = __double2float_rn(beta);
-    st->r_cast = 0;
-    if (st->p_cast) {
-      st->pcur ^= 1;
-      st->uz_p = st->uz;
-      st->p_cast = 0;
-    }
+    S.ticket[0] = 0u;
+    rho_step(&S, tot[0]);
   }
+  state_store(st, &S);
 }
 
 // Ahat = D^-1/2 A D^-1/2 in the sliced layout ((dsi_i a_ij) dsi_j in FP64,
@@ -1508,10 +1663,11 @@ __global__ void __launch_bounds__(256) k_precond_step(Bufs B, int64_t n, const D
 // Selector replay over a residual-norm sequence (one thread).
 __global__ void k_selector_trace(DevState* st, int m, unsigned char* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  prep_selector(st);
   for (int k = 0; k <= m; ++k) {
     st->k = k;
     st->delta = st->delta_hist[k];
-    decide(st);
+    decide(st, ArrayHist{st->delta_hist});
     out[k] = st->prec_hist[k];
     st->first = 0;
   }

@@ -159,3 +159,24 @@ def test_selector_matches_oracle(name, crit, u0, latch):
     assert np.array_equal(got, want)
     if name == "geometric":
         assert (got[-1] & 0xF) == P.FP32   # the u_r switch happened
+
+
+@pytest.mark.parametrize("crit", [P.CRIT_WINDOW, P.CRIT_LINEAR])
+@pytest.mark.parametrize("side", [-1, 0, 1])
+@pytest.mark.parametrize("latch", [0, 1])
+def test_selector_threshold_edges(crit, side, latch):
+    # T = tol ||b|| placed exactly on (side 0) or one ulp either side of the
+    # oracle's eta_40, and nu_k landing exactly on tau_zs and one ulp below it:
+    # the device decides these comparisons as the binary64 evaluation does
+    delta = 1e-4 * 0.95 ** (np.arange(120) - 25.0)
+    delta[25] = 1e-4                      # nu_25 = tau_zs exactly (nb = 1)
+    delta[26] = np.nextafter(1e-4, 0.0)
+    eta = (oracle.eta_window(delta, 40, 10, 1.0) if crit == P.CRIT_WINDOW
+           else oracle.eta_linear(delta, 40, 5, 1.0))
+    tol = {0: eta, 1: np.nextafter(eta, np.inf), -1: np.nextafter(eta, 0.0)}[side]
+    gp = P.Policy(u0=P.FP64, criterion=crit, latch=latch)
+    op = oracle.Policy(u0=oracle.FP64, criterion=crit, latch=latch)
+    got = P.selector_trace(delta, 1.0, tol, gp)
+    want = oracle.selector_trace(delta, 1.0, tol, op)
+    assert np.array_equal(got, want)
+    assert (want[25] >> 4) == P.FP64 and (want[26] >> 4) == P.FP32
