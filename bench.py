@@ -11,6 +11,15 @@ FP64 verification), inputs resident in HBM.  L2 is flushed between steps.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
 host cores instead (bounded sample, scaled to the same metric).
+
+--workload selects one of the further workloads instead (one JSON line each,
+AMP-PCG against PCG(FP64) on the same kernels):
+  elasticity96  Q1 hex elasticity, 96^3 nodes (2,626,560 dof), block CSR 3x3,
+                Chebyshev degree 8, tol 1e-8
+  batch512      512 independent 2D 5-point systems (sides 32..256), one
+                ampcg_solve_batched call against a host loop of single solves
+  adjoint64     forward + adjoint solve and dL/dtheta on the 64^3
+                log-coefficient problem (L = 0.5 ||x(theta) - x_t||^2)
 """
 from __future__ import annotations
 
@@ -296,6 +305,132 @@ def run_ours(args, rank, world):
     return out
 
 
+def _event_ms(fn, k, flush):
+    """Mean device time of k calls of fn (L2 flushed before each)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ms, out = [], None
+    for _ in range(k):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.mean(ms), out
+
+
+def run_workload(args):
+    """The further workloads (--workload); rank 0, one GPU."""
+    import torch
+    import paper_2505_04155_b300 as P
+    import workloads as W
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    amp = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3)
+    f64 = P.Policy.pcg64(verify_refresh=3)
+    base = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic"}
+    if args.workload == "elasticity96":
+        t0 = time.time()
+        a = W.elasticity_q1(96, seed=0)
+        b = W.rhs_uniform(a.nb * 3, seed=1)
+        gen_s = time.time() - t0
+        s = P.Solver.from_bsr(a.browptr, a.bcol, a.bval, 3, precond=P.M_CHEBYSHEV, degree=8)
+        bd = torch.as_tensor(b, device="cuda")
+        run = lambda pol: s.solve(bd, torch.zeros_like(bd), tol=1e-8, maxit=MAXIT, policy=pol, history=False)
+        for _ in range(args.warmup):
+            run(amp), run(f64)
+        ta, (_, ia) = _event_ms(lambda: run(amp), args.steps, flush)
+        t6, (_, i6) = _event_ms(lambda: run(f64), args.steps, flush)
+        lmin, lmax = s.interval()
+        s.close()
+        out = {"metric": "time-to-1e-8 rel. residual, Q1 elasticity (block CSR 3x3, Chebyshev degree 8), "
+                         "AMP-PCG vs FP64 PCG on 1 B300",
+               "value": round(ta, 3), "unit": "ms", "ms_per_step": round(ta, 3),
+               "config": {"workload": "Q1 hex elasticity 96^3 nodes, x=0 face clamped, E log-uniform "
+                                      "[1,1e3] per element (seed 0), nu=0.3; b~U[-1,1] seed 1; x0=0",
+                          "dof": int(a.nb * 3), "nnzb": int(len(a.bcol)), "cheb_interval": [lmin, lmax],
+                          "generator_s": round(gen_s, 1), "l2_flush": True},
+               "fp64_pcg_ms": round(t6, 3), "speedup_vs_fp64_pcg": round(t6 / ta, 3),
+               "iters_amp": ia.iters, "iters_fp64": i6.iters, "switch_iter_amp": list(ia.switch_iter),
+               "true_relres_amp": ia.true_relres, "true_relres_fp64": i6.true_relres,
+               "refreshes_amp": ia.refreshes}
+    elif args.workload == "batch512":
+        mats, rhs = W.batch_2d(512, seed=0)
+        ss = [P.Solver(m.rowptr, m.col, m.val) for m in mats]
+        bs = [torch.as_tensor(r, device="cuda") for r in rhs]
+        xs = [torch.zeros_like(b) for b in bs]
+
+        def batched(pol):
+            for x in xs:
+                x.zero_()
+            return P.solve_batched(ss, bs, xs, tol=1e-10, maxit=MAXIT, policy=pol)
+
+        def loop(pol):
+            return [s.solve(b, torch.zeros_like(b), tol=1e-10, maxit=MAXIT, policy=pol, history=False)[1]
+                    for s, b in zip(ss, bs)]
+
+        for _ in range(args.warmup):
+            batched(amp), loop(amp), batched(f64)
+        tb, ib = _event_ms(lambda: batched(amp), args.steps, flush)
+        tl, il = _event_ms(lambda: loop(amp), args.steps, flush)
+        tb6, ib6 = _event_ms(lambda: batched(f64), args.steps, flush)
+        same = all(i.iters == j.iters for i, j in zip(ib, il))
+        for s in ss:
+            s.close()
+        n_tot = int(sum(m.n for m in mats))
+        out = {"metric": "time to solve 512 independent 2D systems to 1e-10 (FP64-verified), "
+                         "one batched call vs a host loop of single solves, 1 B300",
+               "value": round(tb, 3), "unit": "ms", "ms_per_step": round(tb, 3),
+               "config": {"workload": "512 systems, 2D 5-point, side ~ U{32..256} (seed 0), cell coeffs "
+                                      "exp(N(0,1)) (seed 1000+i), faces geometric mean; b_i~U[-1,1]",
+                          "sum_n": n_tot, "sum_nnz": int(sum(m.nnz for m in mats)),
+                          "solver": "AMP-PCG(FP16) linear criterion, Jacobi", "l2_flush": True},
+               "host_loop_ms": round(tl, 3), "speedup_vs_host_loop": round(tl / tb, 3),
+               "fp64_batched_ms": round(tb6, 3), "speedup_vs_fp64_batched": round(tb6 / tb, 3),
+               "iters_max": max(i.iters for i in ib), "iters_mean": round(statistics.mean(i.iters for i in ib), 1),
+               "all_converged": all(i.converged for i in ib), "batched_iters_equal_single": same,
+               "unknowns_per_s": round(n_tot / (tb * 1e-3), 1)}
+    else:  # adjoint64
+        from paper_2505_04155_b300 import autograd as AG
+        theta, theta_t, a, a_t, b = W.log_coeff_problem(64, sigma=1.0, seed=0)
+        s = P.Solver(a.rowptr, a.col, a.val)
+        st = P.Solver(a_t.rowptr, a_t.col, a_t.val)
+        nb = torch.as_tensor(a.info["nbound"], device="cuda")
+        bd = torch.as_tensor(b, device="cuda")
+        x_t, _ = st.solve(bd, tol=1e-13, maxit=MAXIT, policy=P.Policy.pcg64())
+        st.close()
+        th0 = torch.as_tensor(theta, device="cuda")
+
+        def grad(pol):
+            th = th0.clone().requires_grad_(True)
+            x = AG.solve_log_coeff(th, bd, s, nb, tol=1e-10, maxit=MAXIT, policy=pol)
+            L = 0.5 * torch.sum((x - x_t) ** 2)
+            L.backward()
+            return th.grad
+
+        for _ in range(args.warmup):
+            grad(amp), grad(f64)
+        ta, ga = _event_ms(lambda: grad(amp), args.steps, flush)
+        t6, g6 = _event_ms(lambda: grad(f64), args.steps, flush)
+        rel = float(torch.linalg.norm(ga - g6) / torch.linalg.norm(g6))
+        s.close()
+        out = {"metric": "time of one dL/dtheta evaluation (forward solve + adjoint solve + gradient "
+                         "assembly) to 1e-10, AMP-PCG vs FP64 PCG on 1 B300",
+               "value": round(ta, 3), "unit": "ms", "ms_per_step": round(ta, 3),
+               "config": {"workload": "64^3 7-point log-coefficient diffusion, theta = 3x box-filtered "
+                                      "N(0,1) field, sigma=1 (seed 0); theta_t = theta + 0.1 field (seed 2); "
+                                      "b~U[-1,1] seed 1; L = 0.5||x(theta) - x_t||^2",
+                          "n": int(a.n), "nnz": int(a.nnz), "l2_flush": True},
+               "fp64_ms": round(t6, 3), "speedup_vs_fp64": round(t6 / ta, 3),
+               "grad_rel_diff_amp_vs_fp64": rel}
+    out.update(base)
+    print(json.dumps(out), flush=True)
+
+
 def run_profile(args):
     """One solve of the benchmark system for a profiler, with the iteration
     kernels launched one by one (ampcg_solve_timed: the same kernels and
@@ -333,9 +468,15 @@ def main():
     ap.add_argument("--profile", choices=["amp", "p1", "p2", "fp64"], default=None,
                     help="run one solve for a profiler and exit")
     ap.add_argument("--profile-iters", type=int, default=0, help="maxit of the profiled solve (0: converge)")
+    ap.add_argument("--workload", choices=["diffusion128", "elasticity96", "batch512", "adjoint64"],
+                    default="diffusion128", help="diffusion128: the headline benchmark")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+        return
+    if args.workload != "diffusion128":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_workload(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
