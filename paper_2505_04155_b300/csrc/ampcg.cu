@@ -638,15 +638,18 @@ static cudaError_t launch_phase(ampcg_ctx* c, int ph, cudaStream_t s, cudaEvent_
   ArgPack pa(c, 0, 0);
   int slot = -1;
   for (const Launch& L : c->seq[ph]) {
-    if (ev && L.slot != slot) {
-      slot = L.slot;
-      cudaError_t e = cudaEventRecord(ev[slot], s);
+    while (ev && slot < L.slot) {   // slots without a kernel in this phase get an empty interval
+      cudaError_t e = cudaEventRecord(ev[++slot], s);
       if (e != cudaSuccess) return e;
     }
     cudaError_t e = cudaLaunchKernel(L.fn, dim3(L.grid), dim3(kBlock), pa.args(L), (size_t)L.smem, s);
     if (e != cudaSuccess) return e;
   }
-  return ev ? cudaEventRecord(ev[4], s) : cudaSuccess;
+  while (ev && slot < 4) {
+    cudaError_t e = cudaEventRecord(ev[++slot], s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 static cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const cudaGraphNode_t* dep,
@@ -773,6 +776,9 @@ static ampcg_status timed_loop(ampcg_ctx* c, ampcg_kernel_times* kt, cudaEvent_t
     CUDA_TRY(cudaStreamSynchronize(s));
     if (c->hst->k > k0) {
       for (int j = 0; j < 4; ++j) {
+        bool has = false;
+        for (const Launch& L : c->seq[ph]) has = has || L.slot == j;
+        if (!has) continue;
         float ms = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&ms, ev[j], ev[j + 1]));
         kt->ms[j][ph] += ms;
@@ -852,6 +858,7 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   CUDA_TRY(cudaGetLastError());
   long long launches = 1;  // k_init
   int k_before = 0;
+  int runs_before[6] = {0, 0, 0, 0, 0, 0};
   if (kt) {
     CUDA_TRY(cudaEventRecord(e_first, s));
     CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -877,7 +884,11 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
       // that stops on breakdown still launches its four)
       long long it = h.k - k_before + (h.status == ST_OK || h.status == ST_NOT_CONVERGED ? 0 : 1);
       long long bodies = it <= 0 ? 1 : (it + chunk - 1) / chunk;
-      launches += 2 * bodies + (long long)c->seq[0].size() * it;
+      launches += 2 * bodies;
+      for (int ph = 0; ph < 6; ++ph) {
+        launches += (long long)c->seq[ph].size() * (h.phase_runs[ph] - runs_before[ph]);
+        runs_before[ph] = h.phase_runs[ph];
+      }
     }
     k_before = h.k;
     // reading R9: verify, and replace r when the true residual misses tol

@@ -66,6 +66,7 @@ struct __align__(16) DevState {
   double inv_tol_nb, tzs_lo, tzs_hi, tzh_lo, tzh_hi, c_lin;
   double rho, rho_prev, beta, gamma, alpha, true_relres;
   unsigned int ticket[4];
+  int phase_runs[8];         // iterations started per phase 2 u_z + u_r
   // histories (device)
   double* delta_hist;        // [maxit + 2]
   unsigned char* prec_hist;  // [maxit + 1]
@@ -609,6 +610,7 @@ template <int UZ, int UR, int MT>
 __global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st) {
   if (st->done) return;
   if (phase_mismatch(st, UZ, UR)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->phase_runs[2 * UZ + UR] += 1;
   double rho = 0.0;
   Dot2 d2;
   precond_and_cast<UZ, UR, MT, 8>(B, n, st, rho, d2);
@@ -634,6 +636,15 @@ __global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st
 
 // ---------------------------------------------------------------------------
 // Alg. 3 line 11: p_k = z_k + beta_{k-1} p_{k-1} in u_z (p_0 = z_0).
+// One element of p_k = z_k + beta p_{k-1} for binary32/binary16 storage:
+// binary32 fma, rounded once into u_z (reading R7).
+template <int UZ>
+__device__ __forceinline__ typename Store<UZ>::T axpy_one(float bf, typename Store<UZ>::T pp,
+                                                         typename Store<UZ>::T zz) {
+  if constexpr (UZ == P32) return __fmaf_rn(bf, pp, zz);
+  else return __float2half_rn(__fmaf_rn(bf, h2f(pp), h2f(zz)));
+}
+
 template <int UZ, int V>
 __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevState* st) {
   using TZ = typename Store<UZ>::T;
@@ -660,8 +671,7 @@ __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevSta
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       if constexpr (UZ == P64) pp[j] = fma(beta, pp[j], zz[j]);
-      else if constexpr (UZ == P32) pp[j] = __fmaf_rn(bf, pp[j], zz[j]);
-      else pp[j] = __float2half_rn(__fmaf_rn(bf, h2f(pp[j]), h2f(zz[j])));
+      else pp[j] = axpy_one<UZ>(bf, pp[j], zz[j]);
     }
     vst<V>(pn + i0, pp, m);
   }
@@ -1434,6 +1444,7 @@ __global__ void __launch_bounds__(256) k_cheb_init(Bufs B, Cheb C, int64_t n, De
   using TR = typename Store<UR>::T;
   if (st->done) return;
   if (phase_mismatch(st, UZ, UR)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->phase_runs[2 * UZ + UR] += 1;
   const int r_cast = st->r_cast;
   const double om = st->omega;
   const float omf = st->omega_f;
