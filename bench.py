@@ -441,6 +441,24 @@ def run_profile(args):
     import torch
     import paper_2505_04155_b300 as P
     torch.cuda.set_device(0)
+    if args.profile.startswith("batch"):
+        # persistent batched kernel: 16 systems of 256 x 256 (the batch's largest
+        # size), Phase 1 or Phase 2 precisions, profile_iters iterations
+        import workloads as W
+        mats = [W.diffusion2d_cells(256, 1000 + i) for i in range(16)]
+        ss = [P.Solver(m.rowptr, m.col, m.val) for m in mats]
+        bs = [torch.as_tensor(W.rhs_uniform(m.n, i), device="cuda") for i, m in enumerate(mats)]
+        xs = [torch.zeros_like(v) for v in bs]
+        ur = P.FP64 if args.profile == "batch_p1" else P.FP32
+        pol = P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=ur)
+        t0 = time.perf_counter()
+        infos = P.solve_batched(ss, bs, xs, tol=TOL, maxit=args.profile_iters or 40, policy=pol)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "iters": infos[0].iters,
+                          "ms": round((time.perf_counter() - t0) * 1e3, 3)}), flush=True)
+        for s in ss:
+            s.close()
+        return
     a, b = workload()
     s = P.Solver(a.rowptr, a.col, a.val)
     pol = {"amp": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3),
@@ -465,7 +483,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--profile", choices=["amp", "p1", "p2", "fp64"], default=None,
+    ap.add_argument("--profile", choices=["amp", "p1", "p2", "fp64", "batch_p1", "batch_p2"], default=None,
                     help="run one solve for a profiler and exit")
     ap.add_argument("--profile-iters", type=int, default=0, help="maxit of the profiled solve (0: converge)")
     ap.add_argument("--workload", choices=["diffusion128", "elasticity96", "batch512", "adjoint64"],

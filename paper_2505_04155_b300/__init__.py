@@ -401,17 +401,30 @@ def selector_trace_noalloc(delta, nb: float, tol: float, policy: Policy | None =
 
 
 def solve_batched(solvers, bs, xs, tol: float = 1e-10, maxit: int = 2000,
-                  policy: Policy | None = None):
+                  policy: Policy | None = None, history: bool = False):
     """Solve independent systems in one call (ampcg_solve_batched); xs hold
-    the initial guesses and receive the solutions.  Returns a list of SolveInfo."""
+    the initial guesses and receive the solutions.  Returns a list of
+    SolveInfo (with relres/precision histories when history=True)."""
     n = len(solvers)
     hs = (C.c_void_p * n)(*[s._h.value for s in solvers])
     bp = (C.c_void_p * n)(*[_ptr(b) for b in bs])
     xp = (C.c_void_p * n)(*[_ptr(x) for x in xs])
     res = (ResultC * n)()
+    hist = []
+    if history:
+        for r in res:
+            rh, ph = np.zeros(maxit + 2), np.zeros(max(maxit, 1), dtype=np.uint8)
+            r.relres_hist = rh.ctypes.data_as(C.POINTER(C.c_double))
+            r.prec_hist = ph.ctypes.data_as(C.POINTER(C.c_uint8))
+            hist.append((rh, ph))
     pol = (policy or Policy()).to_c()
     st = load_library().ampcg_solve_batched(n, hs, bp, xp, tol, maxit, C.byref(pol), res)
     _check(st, (OK, NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE))
-    return [SolveInfo(r.status, r.iters, bool(r.converged), r.refreshes, r.true_relres,
-                      r.updated_relres, tuple(r.switch_iter), r.seconds, r.kernel_launches)
-            for r in res]
+    out = []
+    for j, r in enumerate(res):
+        rh, ph = hist[j] if history else (None, None)
+        out.append(SolveInfo(r.status, r.iters, bool(r.converged), r.refreshes, r.true_relres,
+                             r.updated_relres, tuple(r.switch_iter), r.seconds, r.kernel_launches,
+                             rh[: r.iters + 1].copy() if history else None,
+                             ph[: r.iters].copy() if history else None))
+    return out

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <thread>
@@ -22,7 +23,7 @@
 #include <vector>
 
 #include "../../include/ampcg.h"
-#include "kernels.cuh"
+#include "batched.cuh"
 
 using namespace ampcg;
 
@@ -1381,21 +1382,167 @@ extern "C" ampcg_status ampcg_create_bsr(ampcg_t* out, int64_t nb, int bs, int64
 // ---------------------------------------------------------------------------
 // Many independent systems in one call.
 
+// Systems the persistent batched kernel takes (one block per system): at most
+// kBatchRows rows, Jacobi or no preconditioner.  Larger systems and Chebyshev
+// contexts run as independent device loops on library streams.
+constexpr int64_t kBatchRows = 1 << 17;
+
+static bool batch_eligible(const ampcg_ctx* c) {
+  return c->n <= kBatchRows && c->mtype != M_CHEBYSHEV;
+}
+
+// One persistent launch per column-index width over the eligible systems
+// (idx[]), on stream s.  Fills results for them.
+static ampcg_status batched_persistent(const std::vector<int>& idx, ampcg_t const* systems,
+                                       const double* const* b, double* const* x, double tol, int maxit,
+                                       const ampcg_policy& pol, ampcg_result* results, cudaStream_t s,
+                                       std::vector<ampcg_status>& sts) {
+  const int m = (int)idx.size();
+  if (m == 0) return AMPCG_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<BatchSys> hs(m);
+  std::vector<char> bdev(m), xdev(m);
+  for (int q = 0; q < m; ++q) {
+    ampcg_ctx* c = systems[idx[q]];
+    ampcg_status hs_ = ensure_hist(c, maxit);
+    if (hs_ != AMPCG_OK) return hs_;
+    BatchSys& D = hs[q];
+    D.A = c->sell();
+    D.B = c->bufs();
+    D.n = c->n;
+    D.mt = c->mtype;
+    D.delta_hist = c->dhist;
+    D.prec_hist = c->phist;
+    D.bbuf = c->b;
+    bdev[q] = is_device_ptr(b[idx[q]]);
+    xdev[q] = is_device_ptr(x[idx[q]]);
+    size_t vb = (size_t)c->n * sizeof(double);
+    if (bdev[q]) {
+      D.b = b[idx[q]];
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(c->b, b[idx[q]], vb, cudaMemcpyHostToDevice, s));
+      D.b = c->b;
+    }
+    if (xdev[q]) {
+      D.x = x[idx[q]];
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(c->x, x[idx[q]], vb, cudaMemcpyHostToDevice, s));
+      D.x = c->x;
+    }
+  }
+  // longest first within each index width
+  std::vector<int> ord[2];
+  for (int q = 0; q < m; ++q) ord[systems[idx[q]]->idx16 ? 1 : 0].push_back(q);
+  for (auto& o : ord)
+    std::stable_sort(o.begin(), o.end(), [&](int a, int bq) { return hs[a].n > hs[bq].n; });
+  DevState tmpl;
+  init_state(&tmpl, &pol, tol, maxit, nullptr);
+  // device scratch: systems, orders, two queue counters, template, outcomes
+  size_t off_sys = 0, off_ord = off_sys + sizeof(BatchSys) * m;
+  size_t off_cnt = (off_ord + sizeof(int) * m + 15) & ~(size_t)15;
+  size_t off_tmp = (off_cnt + 2 * sizeof(int) + 15) & ~(size_t)15;
+  size_t off_out = (off_tmp + sizeof(DevState) + 15) & ~(size_t)15;
+  size_t total = off_out + sizeof(BatchOut) * m;
+  std::vector<unsigned char> host(total, 0);
+  memcpy(host.data() + off_sys, hs.data(), sizeof(BatchSys) * m);
+  int* ho = (int*)(host.data() + off_ord);
+  int pos = 0;
+  for (auto& o : ord)
+    for (int q : o) ho[pos++] = q;
+  memcpy(host.data() + off_tmp, &tmpl, sizeof(DevState));
+  unsigned char* dev = nullptr;
+  CUDA_TRY(cudaMallocAsync((void**)&dev, total, s));
+  ampcg_status st = AMPCG_OK;
+  std::vector<BatchOut> out(m);
+  do {
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), total, cudaMemcpyHostToDevice, s);
+    int dev_id = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    int first = 0;
+    for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
+      const int cnt = (int)ord[g].size();
+      if (cnt == 0) continue;
+      const void* kern = g ? (const void*)k_batched<1> : (const void*)k_batched<0>;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchBlock, 0) != cudaSuccess ||
+          per_sm < 1)
+        per_sm = 1;
+      int grid = sms * per_sm < cnt ? sms * per_sm : cnt;
+      const BatchSys* dsys = (const BatchSys*)(dev + off_sys);
+      const int* dord = (const int*)(dev + off_ord) + first;
+      int* dcnt = (int*)(dev + off_cnt) + g;
+      const DevState* dtmp = (const DevState*)(dev + off_tmp);
+      BatchOut* dout = (BatchOut*)(dev + off_out);
+      int vr = pol.verify_refresh;
+      if (g) k_batched<1><<<grid, kBatchBlock, 0, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
+      else k_batched<0><<<grid, kBatchBlock, 0, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
+      e = cudaGetLastError();
+      first += cnt;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out.data(), dev + off_out, sizeof(BatchOut) * m, cudaMemcpyDeviceToHost, s);
+    for (int q = 0; q < m && e == cudaSuccess; ++q) {
+      ampcg_ctx* c = systems[idx[q]];
+      if (!xdev[q])
+        e = cudaMemcpyAsync(x[idx[q]], c->x, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(AMPCG_ERR_CUDA, "batched solve: %s", cudaGetErrorString(e));
+  } while (0);
+  cudaFreeAsync(dev, s);
+  if (st != AMPCG_OK) return st;
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int q = 0; q < m; ++q) {
+    const BatchOut& o = out[q];
+    sts[idx[q]] = o.status == ST_INTERNAL ? AMPCG_ERR_CUDA : (ampcg_status)o.status;
+    ampcg_result* r = results ? &results[idx[q]] : nullptr;
+    if (!r) continue;
+    ampcg_ctx* c = systems[idx[q]];
+    int iters = o.iters;
+    if (r->relres_hist)
+      CUDA_TRY(cudaMemcpy(r->relres_hist, c->dhist, (iters + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    if (r->prec_hist && iters > 0)
+      CUDA_TRY(cudaMemcpy(r->prec_hist, c->phist, iters, cudaMemcpyDeviceToHost));
+    if (r->relres_hist)
+      for (int i = 0; i <= iters; ++i) r->relres_hist[i] /= o.nb;
+    r->iters = iters;
+    r->converged = o.status == ST_OK;
+    r->refreshes = o.refreshes;
+    r->status = o.status == ST_INTERNAL ? AMPCG_ERR_CUDA : o.status;
+    r->true_relres = o.true_relres;
+    r->updated_relres = o.updated_relres;
+    for (int j = 0; j < 3; ++j) r->switch_iter[j] = o.switch_iter[j];
+    r->seconds = secs;
+    // the persistent launches are reported once, with the first system
+    r->kernel_launches = q == 0 ? (ord[0].empty() ? 0 : 1) + (ord[1].empty() ? 0 : 1) : 0;
+  }
+  return AMPCG_OK;
+}
+
 extern "C" ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, const double* const* b,
                                             double* const* x, double tol, int maxit,
                                             const ampcg_policy* policy, ampcg_result* results) {
   if (nsys < 0 || (nsys > 0 && (!systems || !b || !x)))
     return fail(AMPCG_ERR_INVALID_ARG, "bad batched arguments");
   if (nsys == 0) return AMPCG_OK;
+  if (!(tol >= 0.0) || maxit < 0) return fail(AMPCG_ERR_INVALID_ARG, "need tol >= 0 and maxit >= 0");
   for (int i = 0; i < nsys; ++i) {
     if (!systems[i] || !b[i] || !x[i]) return fail(AMPCG_ERR_INVALID_ARG, "NULL entry %d", i);
     for (int j = 0; j < i; ++j)
       if (systems[j] == systems[i]) return fail(AMPCG_ERR_INVALID_ARG, "system %d appears twice", i);
   }
+  ampcg_policy pol;
+  if (policy) pol = *policy;
+  else ampcg_policy_default(&pol);
+  ampcg_status ps = check_policy(&pol);
+  if (ps != AMPCG_OK) return ps;
   int dev = 0;
   cudaGetDevice(&dev);
-  const int W = nsys < 16 ? nsys : 16;
-  std::vector<cudaStream_t> ws(W, nullptr);
+  std::vector<int> small, rest;
+  for (int i = 0; i < nsys; ++i) (batch_eligible(systems[i]) ? small : rest).push_back(i);
+  const int W = (int)(rest.size() < 16 ? rest.size() : 16);
+  const int NS = W + (small.empty() ? 0 : 1);   // stream W: the persistent path
+  std::vector<cudaStream_t> ws(NS, nullptr);
   cudaEvent_t ev = nullptr;
   ampcg_status st = AMPCG_OK;
   auto cleanup = [&]() {
@@ -1403,7 +1550,7 @@ extern "C" ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, co
       if (s) cudaStreamDestroy(s);
     if (ev) cudaEventDestroy(ev);
   };
-  for (int w = 0; w < W; ++w) {
+  for (int w = 0; w < NS; ++w) {
     if (cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking) != cudaSuccess) {
       cleanup();
       return fail(AMPCG_ERR_CUDA, "stream creation failed");
@@ -1416,35 +1563,50 @@ extern "C" ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, co
   // work queued on the systems' own streams (their inputs) comes first
   for (int i = 0; i < nsys; ++i) {
     cudaEventRecord(ev, systems[i]->stream);
-    for (int w = 0; w < W; ++w) cudaStreamWaitEvent(ws[w], ev, 0);
+    for (int w = 0; w < NS; ++w) cudaStreamWaitEvent(ws[w], ev, 0);
   }
-  std::atomic<int> next(0);
   std::vector<ampcg_status> sts(nsys, AMPCG_OK);
   std::vector<std::string> errs(nsys);
+  ampcg_status pst = AMPCG_OK;
+  std::string perr;
+  std::thread pth;
+  if (!small.empty()) {
+    pth = std::thread([&]() {
+      cudaSetDevice(dev);
+      pst = batched_persistent(small, systems, b, x, tol, maxit, pol, results, ws[W], sts);
+      if (pst != AMPCG_OK) perr = g_err;
+    });
+  }
+  std::atomic<int> next(0);
   auto worker = [&](int w) {
     cudaSetDevice(dev);
     for (;;) {
-      int i = next.fetch_add(1);
-      if (i >= nsys) break;
+      int q = next.fetch_add(1);
+      if (q >= (int)rest.size()) break;
+      int i = rest[q];
       ampcg_result* r = results ? &results[i] : nullptr;
-      sts[i] = solve_impl(systems[i], b[i], x[i], tol, maxit, policy, r, nullptr, ws[w]);
+      sts[i] = solve_impl(systems[i], b[i], x[i], tol, maxit, &pol, r, nullptr, ws[w]);
       if (sts[i] != AMPCG_OK && sts[i] != AMPCG_NOT_CONVERGED) errs[i] = g_err;
     }
   };
   std::vector<std::thread> th;
-  for (int w = 1; w < W; ++w) th.emplace_back(worker, w);
-  worker(0);
+  for (int w = 0; w < W; ++w) th.emplace_back(worker, w);
   for (auto& t : th) t.join();
+  if (pth.joinable()) pth.join();
   // later work on the systems' streams waits for the batch
-  for (int w = 0; w < W; ++w) {
+  for (int w = 0; w < NS; ++w) {
     cudaEventRecord(ev, ws[w]);
     for (int i = 0; i < nsys; ++i) cudaStreamWaitEvent(systems[i]->stream, ev, 0);
   }
   cleanup();
+  if (pst != AMPCG_OK) {
+    g_err = "batched kernel: " + perr;
+    return pst;
+  }
   for (int i = 0; i < nsys; ++i) {
     if (sts[i] == AMPCG_NOT_CONVERGED && st == AMPCG_OK) st = AMPCG_NOT_CONVERGED;
     if (sts[i] != AMPCG_OK && sts[i] != AMPCG_NOT_CONVERGED) {
-      g_err = "system " + std::to_string(i) + ": " + errs[i];
+      g_err = "system " + std::to_string(i) + ": " + (errs[i].empty() ? ampcg_status_string(sts[i]) : errs[i]);
       return sts[i];
     }
   }

@@ -1,0 +1,224 @@
+// batched.cuh -- many independent small systems in one persistent launch.
+//
+// Each block runs the whole of Alg. 3 for one system at a time (initial
+// residual, selector, scale + precondition, direction, SpMV, updates,
+// stopping test, FP64 verification and replacement), with block-level
+// reductions and the system's state in shared memory, so an iteration costs
+// block barriers instead of kernel launches and grid-wide reductions.  Blocks
+// take systems from a queue ordered by decreasing size (longest first) and
+// run until the queue is empty.  The row and element loops are the
+// single-system solver's (kernels.cuh) over the block's threads; only the
+// reduction order differs, so iterates agree with a single-system solve to
+// rounding.  There are no waits other than __syncthreads.
+#pragma once
+#include "kernels.cuh"
+
+namespace ampcg {
+
+// One system of a batch: its matrix, buffers and histories (from its
+// context), where b and x live, and where its outcome goes.
+struct BatchSys {
+  Sell A;
+  Bufs B;
+  int64_t n;
+  int mt;                  // M_NONE or M_JACOBI
+  const double* b;         // device; copied into bbuf (= B.b) by the block
+  double* x;               // device, in/out; copied to and from B.x
+  double* bbuf;            // the context's padded right-hand-side buffer
+  double* delta_hist;      // [maxit + 2]
+  unsigned char* prec_hist;
+};
+
+// Outcome of one system.
+struct BatchOut {
+  int iters, status, refreshes, switch_iter[3];
+  double true_relres, updated_relres, nb;
+};
+
+constexpr int kBatchBlock = 1024;
+
+template <int UZ, int UR, int MT, int IT>
+__device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int64_t n, DevState* S) {
+  // Alg. 3 lines 5-10
+  {
+    double rho = 0.0;
+    Dot2 d2;
+    precond_and_cast<UZ, UR, MT, 8, BlockPart>(B, n, S, rho, d2);
+    double v[1];
+    if constexpr ((UR != P64) && (UZ != P64)) {
+      v[0] = block_sum_dot2(d2, S->inv_sig);
+    } else {
+      v[0] = rho;
+      block_sum<1>(v);
+    }
+    if (threadIdx.x == 0) {
+      S->phase_runs[2 * UZ + UR] += 1;
+      rho_step(S, v[0]);
+    }
+    __syncthreads();
+    if (S->done) return;
+  }
+  // line 11
+  axpy_rows<UZ, 8, BlockPart>(B, n, S);
+  __syncthreads();
+  // lines 12-14
+  {
+    double gam = 0.0;
+    Dot2 d2;
+    spmv_rows<UZ, UR, IT, BlockPart>(A, B, S, gam, d2);
+    double v[1];
+    if constexpr ((UR != P64) && (UZ != P64)) {
+      v[0] = block_sum_dot2(d2, 1.0);
+    } else {
+      v[0] = gam;
+      block_sum<1>(v);
+    }
+    if (threadIdx.x == 0) gamma_step(S, v[0]);
+    __syncthreads();
+    if (S->done) return;
+  }
+  // lines 15-18
+  {
+    double rr = 0.0;
+    Dot2 d2;
+    unsigned long long mx = 0ull;
+    update_rows<UZ, UR, 8, BlockPart>(B, n, S, rr, d2, mx);
+    double v[1];
+    if constexpr (UR != P64) {
+      v[0] = block_sum_dot2(d2, S->inv_sig2);
+    } else {
+      v[0] = rr;
+      block_sum<1>(v);
+    }
+    mx = block_max(mx);
+    if (threadIdx.x == 0) {
+      double d = update_step(S, v[0], mx);
+      S->delta_hist[S->k] = d;
+    }
+    __syncthreads();
+  }
+}
+
+template <int MT, int IT>
+__device__ __forceinline__ void cta_dispatch(int ph, const Sell& A, const Bufs& B, int64_t n, DevState* S) {
+  switch (ph) {
+    case 0: cta_iteration<P64, P64, MT, IT>(A, B, n, S); break;
+    case 1: cta_iteration<P64, P32, MT, IT>(A, B, n, S); break;
+    case 2: cta_iteration<P32, P64, MT, IT>(A, B, n, S); break;
+    case 3: cta_iteration<P32, P32, MT, IT>(A, B, n, S); break;
+    case 4: cta_iteration<P16, P64, MT, IT>(A, B, n, S); break;
+    default: cta_iteration<P16, P32, MT, IT>(A, B, n, S); break;
+  }
+}
+
+template <int IT>
+__device__ __forceinline__ void cta_dispatch_mt(int mt, int ph, const Sell& A, const Bufs& B, int64_t n,
+                                                DevState* S) {
+  if (mt == M_JACOBI) cta_dispatch<M_JACOBI, IT>(ph, A, B, n, S);
+  else cta_dispatch<M_NONE, IT>(ph, A, B, n, S);
+}
+
+// The whole solve of one system by one block (every thread calls it).
+template <int IT>
+__device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
+  const Sell& A = D.A;
+  const Bufs& B = D.B;
+  const int64_t n = D.n;
+  // the row loops use whole 8-element vectors: work in the context's padded buffers
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    D.bbuf[i] = D.b[i];
+    B.x[i] = D.x[i];
+  }
+  __syncthreads();
+  // Alg. 3 line 1
+  {
+    double v[2] = {0.0, 0.0};
+    unsigned long long mx = 0ull;
+    init_rows<IT, BlockPart>(A, B, v, mx);
+    block_sum<2>(v);
+    mx = block_max(mx);
+    if (threadIdx.x == 0) S->delta_hist[0] = init_step(S, v[0], v[1], mx);
+    __syncthreads();
+  }
+  int bodies = 0;
+  const int limit = S->maxit + 1;
+  for (;;) {
+    while (!S->done) {
+      cta_dispatch_mt<IT>(D.mt, 2 * S->uz + S->ur, A, B, n, S);
+      if (++bodies > limit) {      // every iteration advances k or stops: cannot happen
+        if (threadIdx.x == 0) {
+          S->status = ST_INTERNAL;
+          S->done = 1;
+        }
+        __syncthreads();
+      }
+    }
+    // exit verification in FP64
+    {
+      double v[1] = {0.0};
+      true_res_rows<IT, BlockPart>(A, B, v);
+      block_sum<1>(v);
+      if (threadIdx.x == 0) S->true_relres = sqrt(v[0]) / S->nb;
+      __syncthreads();
+    }
+    // reading R9
+    const bool refresh = S->status == ST_OK && S->refreshes < verify_refresh && S->k < S->maxit &&
+                         S->true_relres * S->nb > S->tol_nb;
+    if (!refresh) break;
+    double rr = 0.0;
+    unsigned long long mx = 0ull;
+    refresh_rows<BlockPart>(B, n, S, rr, mx);
+    double v[1] = {rr};
+    block_sum<1>(v);
+    mx = block_max(mx);
+    if (threadIdx.x == 0) {
+      int k = S->k;
+      S->delta_hist[k] = refresh_step(S, v[0], mx);
+    }
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) D.x[i] = B.x[i];
+}
+
+// Persistent batched solver: blocks take systems order[next++] until the
+// queue is empty.  tmpl: the initial state (policy, tol, maxit) shared by all
+// systems.  Per system: x updated in place, the outcome in out[], histories
+// in the system's arrays.
+template <int IT>
+__global__ void __launch_bounds__(kBatchBlock) k_batched(const BatchSys* sys, const int* order, int nsys,
+                                                         int* next, const DevState* tmpl,
+                                                         int verify_refresh, BatchOut* out) {
+  __shared__ DevState S;
+  __shared__ int s_i;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_i = atomicAdd(next, 1);
+    __syncthreads();
+    const int q = s_i;
+    if (q >= nsys) return;
+    const int i = order[q];
+    const BatchSys D = sys[i];
+    state_load(&S, tmpl);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      S.delta_hist = D.delta_hist;
+      S.prec_hist = D.prec_hist;
+    }
+    __syncthreads();
+    cta_solve<IT>(D, &S, verify_refresh);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      BatchOut o;
+      o.iters = S.k;
+      o.status = S.status;
+      o.refreshes = S.refreshes;
+      for (int j = 0; j < 3; ++j) o.switch_iter[j] = S.switch_iter[j];
+      o.true_relres = S.true_relres;
+      o.updated_relres = S.delta / S.nb;
+      o.nb = S.nb;
+      out[i] = o;
+    }
+  }
+}
+
+}  // namespace ampcg

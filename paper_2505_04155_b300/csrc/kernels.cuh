@@ -432,19 +432,30 @@ __device__ __forceinline__ void rho_step(DevState* s, double r) {
 }
 
 // ---------------------------------------------------------------------------
+// Work partition of the row and element loops: the whole grid (one system
+// per launch) or one block (one system per block, batched solver).
+struct GridPart {
+  __device__ static __forceinline__ int64_t first() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ static __forceinline__ int64_t count() { return (int64_t)gridDim.x * blockDim.x; }
+};
+struct BlockPart {
+  __device__ static __forceinline__ int64_t first() { return threadIdx.x; }
+  __device__ static __forceinline__ int64_t count() { return blockDim.x; }
+};
+
+// ---------------------------------------------------------------------------
 // Initial residual r_0 = b - A x_0 (FP64), ||b||, ||r_0||, max|r_0|; the last
 // block stores delta_0 and decides iteration 0.  One thread per row.
-template <int IT>
-__global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
-  int lane = threadIdx.x & 31;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int nwarps = (gridDim.x * blockDim.x) >> 5;
-  double v[2] = {0.0, 0.0};
-  unsigned long long mx = 0ull;
-  for (int s = warp; s < A.nslices; s += nwarps) {
-    int row = s * 32 + lane;
+template <int IT, class Part = GridPart>
+__device__ __forceinline__ void init_rows(const Sell& A, const Bufs& B, double (&v)[2],
+                                          unsigned long long& mx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = Part::first() >> 5;
+  const int64_t nwarps = Part::count() >> 5;
+  for (int64_t s = warp; s < A.nslices; s += nwarps) {
+    int row = (int)s * 32 + lane;
     if (row < A.n) {
-      double t = sell_row64<IT>(A, s, lane, row, B.x);
+      double t = sell_row64<IT>(A, (int)s, lane, row, B.x);
       double bi = B.b[row];
       double ri = bi - t;
       B.r64[row] = ri;
@@ -454,6 +465,41 @@ __global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
       mx = kk > mx ? kk : mx;
     }
   }
+}
+
+// Alg. 3 line 1 on the state copy: ||b||, delta_0, the stopping test and the
+// decision for iteration 0; returns delta_0.
+__device__ __forceinline__ double init_step(DevState* s, double bb, double rr, unsigned long long m) {
+  double nb = sqrt(bb);
+  double d0 = sqrt(rr);
+  s->nb = nb;
+  s->tol_nb = s->tol * nb;
+  prep_selector(s);
+  s->delta = d0;
+  s->maxr = __longlong_as_double((long long)m);
+  s->dring[0] = d0;
+  s->k = 0;
+  s->done = 0;
+  s->status = ST_NOT_CONVERGED;
+  if (!isfinite(nb) || !isfinite(d0)) {
+    s->status = ST_NONFINITE;
+    s->done = 1;
+  } else if (d0 <= s->tol_nb) {
+    s->status = ST_OK;
+    s->done = 1;
+  } else if (s->maxit <= 0) {
+    s->done = 1;
+  } else {
+    decide(s, RingHist{s});
+  }
+  return d0;
+}
+
+template <int IT>
+__global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
+  double v[2] = {0.0, 0.0};
+  unsigned long long mx = 0ull;
+  init_rows<IT>(A, B, v, mx);
   block_sum<2>(v);
   mx = block_max(mx);
   if (threadIdx.x == 0) {
@@ -466,31 +512,10 @@ __global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
   state_load(&S, st);
   double vv[2];
   unsigned long long m = final_sum_max<2>(B.part, 4, B.pmax, gridDim.x, vv);
-  double d0 = 0.0, nb = 0.0;
+  double d0 = 0.0;
   if (threadIdx.x == 0) {
     S.ticket[0] = 0u;
-    nb = sqrt(vv[0]);
-    d0 = sqrt(vv[1]);
-    S.nb = nb;
-    S.tol_nb = S.tol * nb;
-    prep_selector(&S);
-    S.delta = d0;
-    S.maxr = __longlong_as_double((long long)m);
-    S.dring[0] = d0;
-    S.k = 0;
-    S.done = 0;
-    S.status = ST_NOT_CONVERGED;
-    if (!isfinite(nb) || !isfinite(d0)) {
-      S.status = ST_NONFINITE;
-      S.done = 1;
-    } else if (d0 <= S.tol_nb) {
-      S.status = ST_OK;
-      S.done = 1;
-    } else if (S.maxit <= 0) {
-      S.done = 1;
-    } else {
-      decide(&S, RingHist{&S});
-    }
+    d0 = init_step(&S, vv[0], vv[1], m);
   }
   state_store(st, &S);
   if (threadIdx.x == 0) {
@@ -505,7 +530,7 @@ __global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
 // first m = min(V, n - i0) elements of a vector are used and stored.
 
 // Alg. 3 lines 5-7 (+ the storage conversions of readings R10 and line 11).
-template <int UZ, int UR, int MT, int V>
+template <int UZ, int UR, int MT, int V, class Part = GridPart>
 __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const DevState* st,
                                              double& rho, Dot2& d2) {
   using TZ = typename Store<UZ>::T;
@@ -521,8 +546,8 @@ __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const Dev
   constexpr bool kSmall = (UR != P64) && (UZ != P64);
   const float sigf = st->sig_f;
   const int64_t nv = (n + V - 1) / V;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+  const int64_t stride = Part::count();
+  for (int64_t v = Part::first(); v < nv; v += stride) {
     const int64_t i0 = v * V;
     const int m = (n - i0 < V) ? (int)(n - i0) : V;
     // r_k in u_r (converted once when u_r changed, reading R10)
@@ -582,15 +607,15 @@ __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const Dev
 
 // p_{k-1} brought to the new u_z once, when u_z changed (line 11 computes p_k
 // in u_z); the converted copy goes to the other search-direction buffer.
-template <int UZ>
+template <int UZ, class Part = GridPart>
 __device__ __forceinline__ void cast_p(const Bufs& B, int64_t n, const DevState* st) {
   using TZ = typename Store<UZ>::T;
   const int uz_p = st->uz_p;
   const int pc = st->pcur;
   const void* pold = pc ? B.p[1] : B.p[0];
   TZ* pnew = (TZ*)(pc ? B.p[0] : B.p[1]);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  const int64_t stride = Part::count();
+  for (int64_t i = Part::first(); i < n; i += stride) {
     double pv;
     if (uz_p == P64) pv = ((const double*)pold)[i];
     else if (uz_p == P32) pv = f2d(((const float*)pold)[i]);
@@ -599,11 +624,11 @@ __device__ __forceinline__ void cast_p(const Bufs& B, int64_t n, const DevState*
   }
 }
 
-template <int UZ, int UR, int MT, int V>
+template <int UZ, int UR, int MT, int V, class Part = GridPart>
 __device__ __forceinline__ void precond_and_cast(const Bufs& B, int64_t n, const DevState* st,
                                                  double& rho, Dot2& d2) {
-  precond_rows<UZ, UR, MT, V>(B, n, st, rho, d2);
-  if (st->p_cast) cast_p<UZ>(B, n, st);
+  precond_rows<UZ, UR, MT, V, Part>(B, n, st, rho, d2);
+  if (st->p_cast) cast_p<UZ, Part>(B, n, st);
 }
 
 template <int UZ, int UR, int MT>
@@ -645,7 +670,7 @@ __device__ __forceinline__ typename Store<UZ>::T axpy_one(float bf, typename Sto
   else return __float2half_rn(__fmaf_rn(bf, h2f(pp), h2f(zz)));
 }
 
-template <int UZ, int V>
+template <int UZ, int V, class Part = GridPart>
 __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevState* st) {
   using TZ = typename Store<UZ>::T;
   const TZ* __restrict__ z = (const TZ*)B.z;
@@ -656,8 +681,8 @@ __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevSta
   const double beta = st->beta;
   const float bf = st->beta_f;
   const int64_t nv = (n + V - 1) / V;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+  const int64_t stride = Part::count();
+  for (int64_t v = Part::first(); v < nv; v += stride) {
     const int64_t i0 = v * V;
     const int m = (n - i0 < V) ? (int)(n - i0) : V;
     alignas(16) TZ zz[V];
@@ -798,7 +823,7 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
 // width) of up to 32 slices with one coalesced load and hands them out by
 // shuffle, so a slice costs two dependent memory round trips (entries, then
 // gathers) instead of three.
-template <int UZ, int UR, int IT>
+template <int UZ, int UR, int IT, class Part = GridPart>
 __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const DevState* st,
                                           double& gam, Dot2& d2) {
   using TZ = typename Store<UZ>::T;
@@ -808,8 +833,8 @@ __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const De
   constexpr bool kSmall = (UR != P64) && (UZ != P64);
   const TR* __restrict__ va = mat_vals<UR>(A);
   const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t gw = (Part::first()) >> 5;
+  const int64_t nw = (Part::count()) >> 5;
   const int64_t spw = (A.nslices + nw - 1) / nw;
   const int64_t s0 = gw * spw;
   const int64_t s1 = s0 + spw < A.nslices ? s0 + spw : A.nslices;
@@ -853,6 +878,23 @@ __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const De
   }
 }
 
+// Alg. 3 lines 13-14 on the state copy: gamma_k, its checks (reading R12),
+// alpha_k = rho_k / gamma_k.
+__device__ __forceinline__ void gamma_step(DevState* s, double g) {
+  s->gamma = g;
+  if (!isfinite(g)) {
+    s->status = ST_NONFINITE;
+    s->done = 1;
+  } else if (!(g > 0.0)) {
+    s->status = ST_BREAKDOWN;
+    s->done = 1;
+  } else {
+    double a = s->rho / g;
+    s->alpha = a;
+    s->alpha_f = __double2float_rn(a);
+  }
+}
+
 // Launched with staged_smem_bytes<UR, IT>() of dynamic shared memory when
 // every slice is at most kStageW wide (staged path), else with none.
 template <int UZ, int UR, int IT>
@@ -879,19 +921,7 @@ __global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
   final_sum<1>(B.part, gridDim.x, 1, tot);
   if (threadIdx.x == 0) {
     S.ticket[1] = 0u;
-    double g = tot[0];
-    S.gamma = g;
-    if (!isfinite(g)) {
-      S.status = ST_NONFINITE;
-      S.done = 1;
-    } else if (!(g > 0.0)) {
-      S.status = ST_BREAKDOWN;
-      S.done = 1;
-    } else {
-      double a = S.rho / g;
-      S.alpha = a;
-      S.alpha_f = __double2float_rn(a);
-    }
+    gamma_step(&S, tot[0]);
   }
   state_store(st, &S);
 }
@@ -900,7 +930,7 @@ __global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
 // Alg. 3 lines 15-18: x += alpha p (FP64), r -= alpha q (u_r),
 // delta_{k+1} = ||r|| (FP64), max|r| (exact); last block: stopping test and
 // the decision for iteration k+1.
-template <int UZ, int UR, int V>
+template <int UZ, int UR, int V, class Part = GridPart>
 __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevState* st,
                                             double& rr, Dot2& d2, unsigned long long& mx) {
   using TZ = typename Store<UZ>::T;
@@ -912,8 +942,8 @@ __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevS
   const float af = st->alpha_f;
   const float sigf = st->sig_f;
   const int64_t nv = (n + V - 1) / V;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+  const int64_t stride = Part::count();
+  for (int64_t v = Part::first(); v < nv; v += stride) {
     const int64_t i0 = v * V;
     const int m = (n - i0 < V) ? (int)(n - i0) : V;
     alignas(16) TZ pp[V];
@@ -951,6 +981,34 @@ __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevS
   if constexpr (UR != P64) mx = abs_key(__uint_as_float((unsigned)mx));
 }
 
+// Alg. 3 lines 17-18 on the state copy: delta_{k+1}, the stopping test,
+// k <- k + 1 and the decision for the new iteration; returns delta_{k+1}.
+__device__ __forceinline__ double update_step(DevState* s, double rr, unsigned long long m) {
+  double d = sqrt(rr);
+  int k1 = s->k + 1;
+  s->delta = d;
+  s->maxr = __longlong_as_double((long long)m);
+  s->dring[k1 & (kRing - 1)] = d;
+  s->rho_prev = s->rho;
+  s->first = 0;
+  s->pcur ^= 1;        // p_k is now the previous direction
+  s->uz_p = s->uz;
+  s->k = k1;
+  if (!isfinite(d)) {
+    s->status = ST_NONFINITE;
+    s->done = 1;
+  } else if (d <= s->tol_nb) {
+    s->status = ST_OK;
+    s->done = 1;
+  } else if (k1 >= s->maxit) {
+    s->status = ST_NOT_CONVERGED;
+    s->done = 1;
+  } else {
+    decide(s, RingHist{s});
+  }
+  return d;
+}
+
 // h_next / has_next: the SWITCH handle of the next iteration in the loop
 // graph, set here to the phase the selector chose (or AMPCG_PHASE_NONE).
 template <int UZ, int UR>
@@ -984,28 +1042,8 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st,
   unsigned next = AMPCG_PHASE_NONE;
   if (threadIdx.x == 0) {
     S.ticket[2] = 0u;
-    d = sqrt(tot[0]);
-    k1 = S.k + 1;
-    S.delta = d;
-    S.maxr = __longlong_as_double((long long)m);
-    S.dring[k1 & (kRing - 1)] = d;
-    S.rho_prev = S.rho;
-    S.first = 0;
-    S.pcur ^= 1;        // p_k is now the previous direction
-    S.uz_p = S.uz;
-    S.k = k1;
-    if (!isfinite(d)) {
-      S.status = ST_NONFINITE;
-      S.done = 1;
-    } else if (d <= S.tol_nb) {
-      S.status = ST_OK;
-      S.done = 1;
-    } else if (k1 >= S.maxit) {
-      S.status = ST_NOT_CONVERGED;
-      S.done = 1;
-    } else {
-      decide(&S, RingHist{&S});
-    }
+    d = update_step(&S, tot[0], m);
+    k1 = S.k;
     if (!S.done) next = 2 * S.uz + S.ur;
   }
   state_store(st, &S);
@@ -1035,20 +1073,25 @@ __global__ void k_loop_ctl(DevState* st, cudaGraphConditionalHandle h) {
 
 // ---------------------------------------------------------------------------
 // True residual t = b - A x in FP64 and ||t|| / ||b|| (exit verification).
-template <int IT>
-__global__ void __launch_bounds__(256) k_true_residual(Sell A, Bufs B, DevState* st) {
-  int lane = threadIdx.x & 31;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int nwarps = (gridDim.x * blockDim.x) >> 5;
-  double v[1] = {0.0};
-  for (int s = warp; s < A.nslices; s += nwarps) {
-    int row = s * 32 + lane;
+template <int IT, class Part = GridPart>
+__device__ __forceinline__ void true_res_rows(const Sell& A, const Bufs& B, double (&v)[1]) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = Part::first() >> 5;
+  const int64_t nwarps = Part::count() >> 5;
+  for (int64_t s = warp; s < A.nslices; s += nwarps) {
+    int row = (int)s * 32 + lane;
     if (row < A.n) {
-      double t = B.b[row] - sell_row64<IT>(A, s, lane, row, B.x);
+      double t = B.b[row] - sell_row64<IT>(A, (int)s, lane, row, B.x);
       B.t[row] = t;
       v[0] = fma(t, t, v[0]);
     }
   }
+}
+
+template <int IT>
+__global__ void __launch_bounds__(256) k_true_residual(Sell A, Bufs B, DevState* st) {
+  double v[1] = {0.0};
+  true_res_rows<IT>(A, B, v);
   block_sum<1>(v);
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[3])) return;
@@ -1065,12 +1108,12 @@ __global__ void __launch_bounds__(256) k_true_residual(Sell A, Bufs B, DevState*
 
 // Residual replacement (reading R9): r <- round_ur(t), delta, max|r|; the
 // solve continues from iteration st->k if the new residual misses tol.
-__global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st) {
+template <class Part = GridPart>
+__device__ __forceinline__ void refresh_rows(const Bufs& B, int64_t n, const DevState* st, double& rr,
+                                             unsigned long long& mx) {
   const int ur = st->ur;
-  double rr = 0.0;
-  unsigned long long mx = 0ull;
-  int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  const int64_t stride = Part::count();
+  for (int64_t i = Part::first(); i < n; i += stride) {
     double t = B.t[i];
     double rv;
     if (ur == P64) { rv = t; B.r64[i] = t; }
@@ -1079,6 +1122,32 @@ __global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st
     unsigned long long kk = abs_key(rv);
     mx = kk > mx ? kk : mx;
   }
+}
+
+// Reading R9 on the state copy: the replaced residual's norm, the stopping
+// test, and the decision for iteration k; returns the new delta_k.
+__device__ __forceinline__ double refresh_step(DevState* s, double rr, unsigned long long m) {
+  double d = sqrt(rr);
+  int k = s->k;
+  s->delta = d;
+  s->maxr = __longlong_as_double((long long)m);
+  s->dring[k & (kRing - 1)] = d;
+  s->refreshes += 1;
+  if (d <= s->tol_nb) {
+    s->status = ST_OK;
+    s->done = 1;
+  } else {
+    s->status = ST_NOT_CONVERGED;
+    s->done = 0;
+    decide(s, RingHist{s});
+  }
+  return d;
+}
+
+__global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st) {
+  double rr = 0.0;
+  unsigned long long mx = 0ull;
+  refresh_rows(B, n, st, rr, mx);
   double v[1] = {rr};
   block_sum<1>(v);
   mx = block_max(mx);
@@ -1095,20 +1164,8 @@ __global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st
   int k = 0;
   if (threadIdx.x == 0) {
     S.ticket[3] = 0u;
-    d = sqrt(tot[0]);
     k = S.k;
-    S.delta = d;
-    S.maxr = __longlong_as_double((long long)m);
-    S.dring[k & (kRing - 1)] = d;
-    S.refreshes += 1;
-    if (d <= S.tol_nb) {
-      S.status = ST_OK;
-      S.done = 1;
-    } else {
-      S.status = ST_NOT_CONVERGED;
-      S.done = 0;
-      decide(&S, RingHist{&S});
-    }
+    d = refresh_step(&S, tot[0], m);
   }
   state_store(st, &S);
   if (threadIdx.x == 0) {
