@@ -175,14 +175,22 @@ ampcg_status ampcg_solve(ampcg_t ctx, const double* b, double* x, double tol, in
                          const ampcg_policy* policy, ampcg_result* res);
 
 /* Solves nsys independent systems (distinct contexts, each with its own
- * b[i] and in/out x[i], host or device) with the same tol, maxit and policy.
- * The systems run concurrently on library-owned streams (up to 16 at a
- * time), after all work already queued on their contexts' streams and
- * before any work queued there later; each system keeps its own device-side
- * loop and stops on its own test (per-system convergence).  results[i] (may
- * be NULL) as in ampcg_solve.  Returns AMPCG_OK if every system converged,
- * AMPCG_NOT_CONVERGED if some reached maxit, else the first system's error
- * (ampcg_last_error names the system).  Synchronous.  Not from the paper. */
+ * b[i] and in/out x[i], host or device, n_i doubles) with the same tol, maxit
+ * and policy, after all work already queued on the contexts' streams and
+ * before any work queued there later.  Each system stops on its own test.
+ *   - Systems of at most 131072 rows with Jacobi or no preconditioner run in
+ *     one persistent launch: a block of 1024 threads solves one system at a
+ *     time (block-level reductions, state in shared memory), taking systems
+ *     largest first.  Iterates agree with ampcg_solve to rounding (the
+ *     reduction order differs); a system's result does not depend on the
+ *     rest of the batch.
+ *   - Other systems run ampcg_solve's device loop on library streams (up to
+ *     16 at a time): bitwise equal to ampcg_solve.
+ * results[i] (may be NULL) as in ampcg_solve; the persistent launches are
+ * counted in kernel_launches of the first system that used them.  Returns
+ * AMPCG_OK if every system converged, AMPCG_NOT_CONVERGED if some reached
+ * maxit, else the first failing system's status (ampcg_last_error names it).
+ * Synchronous.  Not from the paper. */
 ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, const double* const* b,
                                  double* const* x, double tol, int maxit,
                                  const ampcg_policy* policy, ampcg_result* results);

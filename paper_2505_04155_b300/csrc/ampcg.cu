@@ -1430,7 +1430,7 @@ static ampcg_status batched_persistent(const std::vector<int>& idx, ampcg_t cons
       D.x = c->x;
     }
   }
-  // longest first within each index width
+  // one queue per column-index width, longest first
   std::vector<int> ord[2];
   for (int q = 0; q < m; ++q) ord[systems[idx[q]]->idx16 ? 1 : 0].push_back(q);
   for (auto& o : ord)
@@ -1459,25 +1459,27 @@ static ampcg_status batched_persistent(const std::vector<int>& idx, ampcg_t cons
     int dev_id = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev_id);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    const BatchSys* dsys = (const BatchSys*)(dev + off_sys);
+    const DevState* dtmp = (const DevState*)(dev + off_tmp);
+    BatchOut* dout = (BatchOut*)(dev + off_out);
+    const int vr = pol.verify_refresh;
     int first = 0;
     for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
       const int cnt = (int)ord[g].size();
+      const int* dord = (const int*)(dev + off_ord) + first;
+      int* dcnt = (int*)(dev + off_cnt) + g;
+      first += cnt;
       if (cnt == 0) continue;
       const void* kern = g ? (const void*)k_batched<1> : (const void*)k_batched<0>;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchBlock, 0) != cudaSuccess ||
-          per_sm < 1)
+          per_sm < 1) {
+        cudaGetLastError();
         per_sm = 1;
-      int grid = sms * per_sm < cnt ? sms * per_sm : cnt;
-      const BatchSys* dsys = (const BatchSys*)(dev + off_sys);
-      const int* dord = (const int*)(dev + off_ord) + first;
-      int* dcnt = (int*)(dev + off_cnt) + g;
-      const DevState* dtmp = (const DevState*)(dev + off_tmp);
-      BatchOut* dout = (BatchOut*)(dev + off_out);
-      int vr = pol.verify_refresh;
+      }
+      const int grid = sms * per_sm < cnt ? sms * per_sm : cnt;
       if (g) k_batched<1><<<grid, kBatchBlock, 0, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
       else k_batched<0><<<grid, kBatchBlock, 0, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
       e = cudaGetLastError();
-      first += cnt;
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out.data(), dev + off_out, sizeof(BatchOut) * m, cudaMemcpyDeviceToHost, s);
@@ -1514,7 +1516,9 @@ static ampcg_status batched_persistent(const std::vector<int>& idx, ampcg_t cons
     for (int j = 0; j < 3; ++j) r->switch_iter[j] = o.switch_iter[j];
     r->seconds = secs;
     // the persistent launches are reported once, with the first system
-    r->kernel_launches = q == 0 ? (ord[0].empty() ? 0 : 1) + (ord[1].empty() ? 0 : 1) : 0;
+    int launches = 0;
+    for (auto& o : ord) launches += o.empty() ? 0 : 1;
+    r->kernel_launches = q == 0 ? launches : 0;
   }
   return AMPCG_OK;
 }

@@ -1,15 +1,19 @@
 // batched.cuh -- many independent small systems in one persistent launch.
 //
-// Each block runs the whole of Alg. 3 for one system at a time (initial
-// residual, selector, scale + precondition, direction, SpMV, updates,
-// stopping test, FP64 verification and replacement), with block-level
+// A block of 1024 threads runs the whole of Alg. 3 for one system at a time
+// (initial residual, selector, scale + precondition, direction, SpMV,
+// updates, stopping test, FP64 verification and replacement), with block
 // reductions and the system's state in shared memory, so an iteration costs
 // block barriers instead of kernel launches and grid-wide reductions.  Blocks
 // take systems from a queue ordered by decreasing size (longest first) and
 // run until the queue is empty.  The row and element loops are the
 // single-system solver's (kernels.cuh) over the block's threads; only the
 // reduction order differs, so iterates agree with a single-system solve to
-// rounding.  There are no waits other than __syncthreads.
+// rounding.  The only waits are __syncthreads.
+//
+// Measured on the 512-system workload: splitting the larger systems over a
+// cluster of 2, 4 or 8 blocks (distributed-shared-memory reductions, cluster
+// barriers) was 18-80% slower than one block per system with the queue.
 #pragma once
 #include "kernels.cuh"
 
@@ -36,14 +40,29 @@ struct BatchOut {
 };
 
 constexpr int kBatchBlock = 1024;
+// Work partition over the block's threads.  Vectors that other threads of
+// the block write during the launch are read with coherent loads
+// (ld.global.ca, never the read-only path); __syncthreads orders the writes
+// before the reads.
+struct TeamPart {
+  __device__ static __forceinline__ int64_t first() { return threadIdx.x; }
+  __device__ static __forceinline__ int64_t count() { return blockDim.x; }
+  template <class T>
+  __device__ static __forceinline__ T ldm(const T* p) { return __ldca(p); }
+  template <int V, class T>
+  __device__ static __forceinline__ void vldm(const T* p, T (&o)[V]) { vldca<V>(p, o); }
+  template <int V, class T>
+  __device__ static __forceinline__ void vldo(const T* p, T (&o)[V]) { vldca<V>(p, o); }
+};
 
 template <int UZ, int UR, int MT, int IT>
 __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int64_t n, DevState* S) {
+  using Part = TeamPart;
   // Alg. 3 lines 5-10
   {
     double rho = 0.0;
     Dot2 d2;
-    precond_and_cast<UZ, UR, MT, 8, BlockPart>(B, n, S, rho, d2);
+    precond_and_cast<UZ, UR, MT, 8, Part>(B, n, S, rho, d2);
     double v[1];
     if constexpr ((UR != P64) && (UZ != P64)) {
       v[0] = block_sum_dot2(d2, S->inv_sig);
@@ -58,14 +77,14 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
     __syncthreads();
     if (S->done) return;
   }
-  // line 11
-  axpy_rows<UZ, 8, BlockPart>(B, n, S);
+  // line 11 (p_k is read by other threads' gathers)
+  axpy_rows<UZ, 8, Part>(B, n, S);
   __syncthreads();
   // lines 12-14
   {
     double gam = 0.0;
     Dot2 d2;
-    spmv_rows<UZ, UR, IT, BlockPart>(A, B, S, gam, d2);
+    spmv_rows<UZ, UR, IT, Part>(A, B, S, gam, d2);
     double v[1];
     if constexpr ((UR != P64) && (UZ != P64)) {
       v[0] = block_sum_dot2(d2, 1.0);
@@ -82,7 +101,7 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
     double rr = 0.0;
     Dot2 d2;
     unsigned long long mx = 0ull;
-    update_rows<UZ, UR, 8, BlockPart>(B, n, S, rr, d2, mx);
+    update_rows<UZ, UR, 8, Part>(B, n, S, rr, d2, mx);
     double v[1];
     if constexpr (UR != P64) {
       v[0] = block_sum_dot2(d2, S->inv_sig2);
@@ -121,6 +140,7 @@ __device__ __forceinline__ void cta_dispatch_mt(int mt, int ph, const Sell& A, c
 // The whole solve of one system by one block (every thread calls it).
 template <int IT>
 __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
+  using Part = TeamPart;
   const Sell& A = D.A;
   const Bufs& B = D.B;
   const int64_t n = D.n;
@@ -134,7 +154,7 @@ __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
   {
     double v[2] = {0.0, 0.0};
     unsigned long long mx = 0ull;
-    init_rows<IT, BlockPart>(A, B, v, mx);
+    init_rows<IT, Part>(A, B, v, mx);
     block_sum<2>(v);
     mx = block_max(mx);
     if (threadIdx.x == 0) S->delta_hist[0] = init_step(S, v[0], v[1], mx);
@@ -156,7 +176,7 @@ __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
     // exit verification in FP64
     {
       double v[1] = {0.0};
-      true_res_rows<IT, BlockPart>(A, B, v);
+      true_res_rows<IT, Part>(A, B, v);
       block_sum<1>(v);
       if (threadIdx.x == 0) S->true_relres = sqrt(v[0]) / S->nb;
       __syncthreads();
@@ -167,7 +187,7 @@ __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
     if (!refresh) break;
     double rr = 0.0;
     unsigned long long mx = 0ull;
-    refresh_rows<BlockPart>(B, n, S, rr, mx);
+    refresh_rows<Part>(B, n, S, rr, mx);
     double v[1] = {rr};
     block_sum<1>(v);
     mx = block_max(mx);
@@ -177,6 +197,7 @@ __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
     }
     __syncthreads();
   }
+  __syncthreads();
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) D.x[i] = B.x[i];
 }
 

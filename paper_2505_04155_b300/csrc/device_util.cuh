@@ -142,6 +142,20 @@ __device__ __forceinline__ void vldg(const T* __restrict__ p, T (&o)[V]) {
   }
 }
 
+// Explicitly coherent variant (ld.global.ca, never the read-only path) for
+// arrays other threads of the running kernel write between barriers.
+template <int V, class T>
+__device__ __forceinline__ void vldca(const T* p, T (&o)[V]) {
+  if constexpr (V > 1 && (V * sizeof(T)) % 16 == 0) {
+    constexpr int NQ = (int)(V * sizeof(T) / 16);
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) reinterpret_cast<uint4*>(o)[j] = __ldca(reinterpret_cast<const uint4*>(p) + j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) o[j] = __ldca(p + j);
+  }
+}
+
 // Stores the first m of V elements (all V with one vector store when m == V).
 template <int V, class T>
 __device__ __forceinline__ void vst(T* __restrict__ p, const T (&o)[V], int m) {

@@ -285,7 +285,7 @@ __device__ void decide(DevState* st, H hist) {
   st->p_cast = (!st->first && uz != st->uz_p);
   st->uz = uz;
   st->ur = ur;
-  st->prec_hist[k] = (unsigned char)((uz << 4) | ur);
+  if (st->prec_hist) st->prec_hist[k] = (unsigned char)((uz << 4) | ur);
   // c = ceil(log2 max|r_k|) (none for max|r_k| = 0 or non-finite)
   const double mr = st->maxr;
   const bool have_c = mr > 0.0 && mr < __longlong_as_double(0x7ff0000000000000ll);
@@ -313,6 +313,25 @@ __device__ void decide(DevState* st, H hist) {
   st->inv_sig = pow2_f64(-se);
   st->inv_sig2 = pow2_f64(-2 * se);
 }
+
+// ---------------------------------------------------------------------------
+// Work partition of the row and element loops, and how they load vectors.
+// GridPart: the whole grid works on one system per launch; every vector a
+// loop reads was written by an earlier launch, so loads may take the
+// read-only path.  TeamPart<CL> (batched.cuh): one block or a cluster of CL
+// blocks runs the whole solve in one launch; vectors written by other
+// threads between barriers are loaded coherently at L2 (ld.global.cg).
+struct GridPart {
+  __device__ static __forceinline__ int64_t first() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ static __forceinline__ int64_t count() { return (int64_t)gridDim.x * blockDim.x; }
+  template <class T>
+  __device__ static __forceinline__ T ldm(const T* p) { return __ldg(p); }
+  template <int V, class T>
+  __device__ static __forceinline__ void vldm(const T* p, T (&o)[V]) { vldg<V>(p, o); }
+  // elements this thread itself reads and rewrites in the launch
+  template <int V, class T>
+  __device__ static __forceinline__ void vldo(const T* p, T (&o)[V]) { vld<V>(p, o); }
+};
 
 // ---------------------------------------------------------------------------
 // Sparse product of one row.  A in precision UR, p stored in precision UZ;
@@ -383,7 +402,7 @@ __device__ __forceinline__ typename Store<UR>::T sell_row(const Sell& A, int s, 
 }
 
 // FP64 fma-chain row product (initial/true residual, Alg. 3 line 1).
-template <int IT>
+template <int IT, class Part = GridPart>
 __device__ __forceinline__ double sell_row64(const Sell& A, int s, int lane, int row,
                                              const double* __restrict__ x) {
   long long base = __ldg(A.off + s) + lane;
@@ -391,7 +410,7 @@ __device__ __forceinline__ double sell_row64(const Sell& A, int s, int lane, int
   double t = 0.0;
   for (int j = 0; j < w; ++j) {
     long long e = base + 32 * j;
-    t = fma(__ldg(A.v64 + e), __ldg(x + col_at<IT>(A, e, row)), t);
+    t = fma(__ldg(A.v64 + e), Part::ldm(x + col_at<IT>(A, e, row)), t);
   }
   return t;
 }
@@ -432,18 +451,6 @@ __device__ __forceinline__ void rho_step(DevState* s, double r) {
 }
 
 // ---------------------------------------------------------------------------
-// Work partition of the row and element loops: the whole grid (one system
-// per launch) or one block (one system per block, batched solver).
-struct GridPart {
-  __device__ static __forceinline__ int64_t first() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
-  __device__ static __forceinline__ int64_t count() { return (int64_t)gridDim.x * blockDim.x; }
-};
-struct BlockPart {
-  __device__ static __forceinline__ int64_t first() { return threadIdx.x; }
-  __device__ static __forceinline__ int64_t count() { return blockDim.x; }
-};
-
-// ---------------------------------------------------------------------------
 // Initial residual r_0 = b - A x_0 (FP64), ||b||, ||r_0||, max|r_0|; the last
 // block stores delta_0 and decides iteration 0.  One thread per row.
 template <int IT, class Part = GridPart>
@@ -455,8 +462,8 @@ __device__ __forceinline__ void init_rows(const Sell& A, const Bufs& B, double (
   for (int64_t s = warp; s < A.nslices; s += nwarps) {
     int row = (int)s * 32 + lane;
     if (row < A.n) {
-      double t = sell_row64<IT>(A, (int)s, lane, row, B.x);
-      double bi = B.b[row];
+      double t = sell_row64<IT, Part>(A, (int)s, lane, row, B.x);
+      double bi = Part::ldm(B.b + row);
       double ri = bi - t;
       B.r64[row] = ri;
       v[0] = fma(bi, bi, v[0]);
@@ -555,22 +562,22 @@ __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const Dev
     if constexpr (UR == P64) {
       if (r_cast) {
         alignas(16) float t[V];
-        vld<V>(B.r32 + i0, t);
+        Part::template vldo<V>(B.r32 + i0, t);
 #pragma unroll
         for (int j = 0; j < V; ++j) r[j] = f2d(t[j]);
         vst<V>(B.r64 + i0, r, m);
       } else {
-        vld<V>(B.r64 + i0, r);
+        Part::template vldo<V>(B.r64 + i0, r);
       }
     } else {
       if (r_cast) {
         alignas(16) double t[V];
-        vld<V>(B.r64 + i0, t);
+        Part::template vldo<V>(B.r64 + i0, t);
 #pragma unroll
         for (int j = 0; j < V; ++j) r[j] = __double2float_rn(t[j]);
         vst<V>(B.r32 + i0, r, m);
       } else {
-        vld<V>(B.r32 + i0, r);
+        Part::template vldo<V>(B.r32 + i0, r);
       }
     }
     // y_k = omega_k r_k computed in u_r, stored in u_z (reading R6), then
@@ -687,12 +694,12 @@ __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevSta
     const int m = (n - i0 < V) ? (int)(n - i0) : V;
     alignas(16) TZ zz[V];
     alignas(16) TZ pp[V];
-    vldg<V>(z + i0, zz);
+    Part::template vldm<V>(z + i0, zz);
     if (first) {
       vst<V>(pn + i0, zz, m);
       continue;
     }
-    vldg<V>(po + i0, pp);
+    Part::template vldm<V>(po + i0, pp);
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       if constexpr (UZ == P64) pp[j] = fma(beta, pp[j], zz[j]);
@@ -865,15 +872,16 @@ __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const De
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          if (j < w) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(p[c[j]]), acc);
+          if (j < w) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(Part::ldm(p + c[j])), acc);
       } else {
         for (int j = 0; j < w; ++j)
           acc = fma_r<UR>(__ldg(va + base + 32 * j),
-                          PToR<UZ, UR>::cv(p[col_at<IT>(A, base + 32 * j, (int)row)]), acc);
+                          PToR<UZ, UR>::cv(Part::ldm(p + col_at<IT>(A, base + 32 * j, (int)row))), acc);
       }
       q[row] = acc;
-      if constexpr (kSmall) d2.add((float)acc, (float)p[row]);
-      else gam = fma(to_f64(acc), to_f64(p[row]), gam);
+      const TZ pr = Part::ldm(p + row);
+      if constexpr (kSmall) d2.add((float)acc, (float)pr);
+      else gam = fma(to_f64(acc), to_f64(pr), gam);
     }
   }
 }
@@ -950,10 +958,10 @@ __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevS
     alignas(16) TR qq[V];
     alignas(16) TR rr_[V];
     alignas(16) double xx[V];
-    vldg<V>(p + i0, pp);
-    vldg<V>(q + i0, qq);
-    vld<V>(rv + i0, rr_);
-    vld<V>(B.x + i0, xx);
+    Part::template vldm<V>(p + i0, pp);
+    Part::template vldm<V>(q + i0, qq);
+    Part::template vldo<V>(rv + i0, rr_);
+    Part::template vldo<V>(B.x + i0, xx);
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       xx[j] = fma(a, to_f64(pp[j]), xx[j]);
@@ -1081,7 +1089,7 @@ __device__ __forceinline__ void true_res_rows(const Sell& A, const Bufs& B, doub
   for (int64_t s = warp; s < A.nslices; s += nwarps) {
     int row = (int)s * 32 + lane;
     if (row < A.n) {
-      double t = B.b[row] - sell_row64<IT>(A, (int)s, lane, row, B.x);
+      double t = Part::ldm(B.b + row) - sell_row64<IT, Part>(A, (int)s, lane, row, B.x);
       B.t[row] = t;
       v[0] = fma(t, t, v[0]);
     }
@@ -1114,7 +1122,7 @@ __device__ __forceinline__ void refresh_rows(const Bufs& B, int64_t n, const Dev
   const int ur = st->ur;
   const int64_t stride = Part::count();
   for (int64_t i = Part::first(); i < n; i += stride) {
-    double t = B.t[i];
+    double t = Part::ldm(B.t + i);
     double rv;
     if (ur == P64) { rv = t; B.r64[i] = t; }
     else { float f = __double2float_rn(t); B.r32[i] = f; rv = f2d(f); }

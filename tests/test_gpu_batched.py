@@ -122,3 +122,24 @@ def test_mixed_batch():
     assert torch.equal(xb, xs[-1]) and ib.iters == infos[-1].iters
     for s in solvers:
         s.close()
+
+
+def test_larger_systems_match_oracle_and_are_independent():
+    # the batch's larger sizes (17K-33K rows) next to a small one
+    sides = [130, 150, 181, 40]
+    mats = [W.diffusion2d_cells(s, 2000 + i) for i, s in enumerate(sides)]
+    rhs = [W.rhs_uniform(m.n, 30 + i) for i, m in enumerate(mats)]
+    gp = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3)
+    op = oracle.Policy(u0=oracle.FP16, criterion=oracle.LINEAR, verify_refresh=3)
+    solvers = [P.Solver(m.rowptr, m.col, m.val) for m in mats]
+    xs, infos = _solve_batched(solvers, rhs, gp)
+    for m, b, x, info in zip(mats, rhs, xs, infos):
+        ref = oracle.ampcg(m.rowptr, m.col, m.val, b, tol=1e-10, maxit=5000, policy=op)
+        assert info.converged and ref.converged
+        assert abs(info.iters - ref.iters) <= max(3, 0.05 * ref.iters)
+        t = oracle.residual64(m.rowptr, m.col, m.val, b, x.cpu().numpy())
+        assert np.linalg.norm(t) / np.linalg.norm(b) <= 1e-10
+    x1, i1 = _solve_batched([solvers[1]], [rhs[1]], gp)
+    assert torch.equal(x1[0], xs[1]) and i1[0].iters == infos[1].iters
+    for s in solvers:
+        s.close()
