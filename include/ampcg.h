@@ -42,7 +42,7 @@ typedef enum {
   AMPCG_NOT_CONVERGED = 1,     /* maxit reached; x and histories are filled */
   AMPCG_ERR_INVALID_ARG = -1,  /* bad size, pointer, policy or CSR structure */
   AMPCG_ERR_NOT_SPD = -2,      /* create-time evidence: a diagonal entry <= 0 */
-  AMPCG_ERR_BREAKDOWN = -3,    /* rho_k <= 0 or gamma_k <= 0 (Alg. 3 lines 7, 13) */
+  AMPCG_ERR_BREAKDOWN = -3,    /* rho_k <= 0 or gamma_k <= 0 in Alg. 3 */
   AMPCG_ERR_NONFINITE = -4,    /* NaN/Inf in b, x0 or a recurrence scalar */
   AMPCG_ERR_CUDA = -5,         /* a CUDA runtime call failed */
   AMPCG_ERR_OOM = -6,          /* device allocation failed */
@@ -51,7 +51,7 @@ typedef enum {
   AMPCG_ERR_UNSUPPORTED = -9   /* valid request this build does not support */
 } ampcg_status;
 
-/* Preconditioner M (Alg. 3 line 6 applies M^-1). */
+/* Preconditioner M (Alg. 3 applies M^-1 to the scaled residual). */
 typedef enum { AMPCG_M_NONE = 0, AMPCG_M_JACOBI = 1, AMPCG_M_CHEBYSHEV = 2 } ampcg_m_type;
 
 /* Jacobi: M = diag(A).  Chebyshev: M^-1 = D^-1/2 P(Ahat) D^-1/2 with
@@ -74,7 +74,7 @@ typedef enum {
   AMPCG_CRIT_FIXED = 2    /* no selector: (u_z, u_r) = (fixed_uz, fixed_ur); FP64/FP64 = PCG */
 } ampcg_criterion;
 
-/* Dynamic scaling omega_k of y_k = omega_k r_k (Alg. 2 line 3, Alg. 3 line 5). */
+/* Dynamic scaling omega_k of y_k = omega_k r_k (Alg. 2, Alg. 3). */
 typedef enum {
   AMPCG_SCALE_NONE = 0,      /* omega = 1 (plain PCG) */
   AMPCG_SCALE_L2 = 1,        /* omega = 1/||r_k||, as printed in Alg. 3 */
@@ -165,7 +165,7 @@ ampcg_status ampcg_update_values(ampcg_t ctx, const double* vals);
 /* Solves A x = b with AMP-PCG (Alg. 3; Alg. 1 and Alg. 2 under the FIXED
  * criterion).  b[n] FP64 (device or host); x[n] FP64 (device or host), in:
  * x_0, out: the final iterate.  tol > 0: stop when ||r_{k+1}|| <= tol ||b||
- * (Alg. 3 line 18).  maxit >= 0.  policy NULL = ampcg_policy_default.
+ * (the stopping test of Alg. 3).  maxit >= 0.  policy NULL = ampcg_policy_default.
  * res (may be NULL) receives counts, final residuals, switch points and, when
  * its history pointers are set, the per-iteration residual and precision
  * histories.  Returns the solve's status (AMPCG_OK, AMPCG_NOT_CONVERGED,
@@ -198,8 +198,8 @@ ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, const double*
 /* Per-kernel device time of one solve, split by the precision pair of the
  * iteration, as the paper reports per-kernel time for each phase of
  * AMP-PCG (Sec. 5.5).  Index [kernel][phase]: kernel 0 = scale+precondition
- * +rho (Alg. 3 lines 5-10), 1 = search direction (line 11), 2 = SpMV+gamma
- * (lines 12-14), 3 = x/r update+norm+selector (lines 15-18); phase =
+ * +rho+beta, 1 = search direction, 2 = SpMV+gamma+alpha, 3 = x/r
+ * update+norm+stopping test+selector (the steps of Alg. 3); phase =
  * 2*u_z + u_r (u_z in {FP64, FP32, FP16}, u_r in {FP64, FP32}). */
 typedef struct {
   double ms[4][6];     /* summed CUDA-event durations */
@@ -250,20 +250,20 @@ ampcg_status ampcg_grad_log_coeff(ampcg_t ctx, const double* x, const double* la
 
 /* --- Single steps of the iteration, on device arrays of length n ---------- */
 
-/* q = A p in precision `prec` (Alg. 3 line 12): the FP64 or FP32 copy of A,
+/* q = A p in precision `prec` (the matrix product of Alg. 3): the FP64 or FP32 copy of A,
  * one fused multiply-add per stored entry in ascending column order,
  * accumulated in `prec`.  p and q are device arrays of doubles (FP64) or
  * floats (FP32).  Asynchronous on the context's stream. */
 ampcg_status ampcg_spmv(ampcg_t ctx, int prec, const void* p, void* q);
 
-/* z = M^-1 y with y = round_uz(omega * r computed in ur) (Alg. 3 lines 5-6).
+/* z = M^-1 y with y = round_uz(omega * r computed in ur) (the scaling and preconditioning of Alg. 3).
  * r: device array in precision ur (double or float); z: device array in
  * precision uz (double, float or IEEE half as uint16).  omega: the scale
  * factor.  Asynchronous on the context's stream. */
 ampcg_status ampcg_precond_apply(ampcg_t ctx, int uz, int ur, double omega, const void* r,
                                  void* z);
 
-/* r = b - A x in FP64 (Alg. 3 line 1): per row, an FP64 fused multiply-add
+/* r = b - A x in FP64 (the initial residual of Alg. 3): per row, an FP64 fused multiply-add
  * chain over the stored entries in ascending column order, subtracted from
  * b.  Device arrays of doubles.  Asynchronous on the context's stream. */
 ampcg_status ampcg_residual(ampcg_t ctx, const double* b, const double* x, double* r);

@@ -204,7 +204,7 @@ def dot(a, b):
 
 
 def scale_precond(rowptr, col, val, mtype, uz, ur, omega, r):
-    """Alg. 3 lines 5-6: z = M^-1 round_uz(fl_ur(omega r)), M none or Jacobi."""
+    """Alg. 3 scaling and preconditioning: z = M^-1 round_uz(fl_ur(omega r)), M none or Jacobi."""
     rowptr, col, val, r = _i32(rowptr), _i32(col), _f64(val), _f64(r)
     n = rowptr.size - 1
     z = np.empty(n)
@@ -214,7 +214,7 @@ def scale_precond(rowptr, col, val, mtype, uz, ur, omega, r):
 
 
 def scale_cheb(rowptr, col, val, degree, lmin, lmax, uz, ur, omega, r):
-    """Alg. 3 lines 5-6 with the Chebyshev preconditioner (reading R8)."""
+    """Alg. 3 scaling and preconditioning with the Chebyshev preconditioner (reading R8)."""
     rowptr, col, val, r = _i32(rowptr), _i32(col), _f64(val), _f64(r)
     n = rowptr.size - 1
     z = np.empty(n)

@@ -25,7 +25,7 @@
  *   R3  no u_r switch before k >= d (window) or k >= ell (linear); inside the
  *       window ||r_{-1}|| := ||r_0||.
  *   R4  latch: a precision never rises again within a solve (flag).
- *   R5  scale modes: NONE (omega=1), L2 (omega = 1/delta_k, Alg. 3 line 5),
+ *   R5  scale modes: NONE (omega=1), L2 (omega = 1/delta_k as in Alg. 3),
  *       LINF_POW2 (omega = 2^-ceil(log2 max|r_k|), an exact power of two;
  *       Sec. 3.3 allows any nonzero omega).
  *   R6  y_i = round_uz( fl_ur(omega * r_i) ): one multiply, computed in u_r,
@@ -141,7 +141,7 @@ void oracle_spmv(int64_t n, const int32_t* rowptr, const int32_t* col,
   }
 }
 
-/* r = b - A x in FP64 (Alg. 3 line 1): t_i = sum_j a_ij x_j as an FP64 fma
+/* r = b - A x in FP64 (Alg. 3 initial residual): t_i = sum_j a_ij x_j as an FP64 fma
  * chain in ascending column order, then r_i = b_i - t_i.                   */
 void oracle_residual64(int64_t n, const int32_t* rowptr, const int32_t* col,
                        const double* val, const double* b, const double* x,
@@ -375,7 +375,7 @@ int oracle_cheb_apply_public(int64_t n, int64_t nnz, const int32_t* rowptr,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Preconditioner apply z = M^-1 y in precision uz (Alg. 3 line 6).
+/* Preconditioner apply z = M^-1 y in precision uz (Alg. 3).
  * Jacobi: z_i = dinv_i * y_i with dinv_i = fl64(1/a_ii) rounded to uz; for
  * FP16 the product of two FP16 numbers is formed exactly in FP32 and
  * rounded once.                                                            */
@@ -389,7 +389,7 @@ static void apply_precond(int mtype, int64_t n, int uz, const double* dinv_u,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 3 line 5 (R6): y_i = round_uz( fl_ur(omega * r_i) ).                */
+/* Alg. 3 scaling (R6): y_i = round_uz( fl_ur(omega * r_i) ).               */
 static void scale_to_y(int64_t n, int uz, int ur, double omega, const double* r, double* y) {
   double omega_r = oracle_round(ur, omega);
   for (int64_t i = 0; i < n; ++i) {
@@ -399,7 +399,7 @@ static void scale_to_y(int64_t n, int uz, int ur, double omega, const double* r,
   }
 }
 
-/* Alg. 3 lines 5-6 on their own, with M = none or Jacobi built from A as in
+/* Alg. 3 scaling and preconditioning on their own, with M = none or Jacobi built from A as in
  * oracle_ampcg: z = M^-1 round_uz(omega r).  r must hold values of precision
  * ur.  Used by tests to check the device's preconditioner kernel.           */
 int oracle_scale_precond(int64_t n, const int32_t* rowptr, const int32_t* col,
@@ -538,7 +538,7 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
   for (int64_t i = 0; i < n; ++i) dinv[0][i] = 1.0 / dinv[0][i];
   for (int64_t i = 0; i < n; ++i) { dinv[1][i] = oracle_round32(dinv[0][i]); dinv[2][i] = oracle_round16(dinv[0][i]); }
 
-  /* Alg. 3 line 1: r_0 = b - A x_0 (FP64), delta_0 = ||r_0||. */
+  /* Alg. 3 initialisation: r_0 = b - A x_0 (FP64), delta_0 = ||r_0||. */
   oracle_residual64(n, rowptr, col, val, b, x, r);
   double nb = oracle_nrm2(n, b);
   double tol_nb = tol * nb;
@@ -557,7 +557,7 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
   int k = 0, refreshes = 0;
   int first = 1;             /* no search direction yet */
   for (k = 0; k < maxit && status == OR_NOT_CONVERGED; ++k) {
-    /* lines 3-4: indicator and selector */
+    /* indicator and precision selection */
     int uz, ur;
     if (pol->criterion == OR_CRIT_FIXED) {
       uz = pol->fixed_uz; ur = pol->fixed_ur;
@@ -580,19 +580,19 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
     if (ur != ur_prev)
       for (int64_t i = 0; i < n; ++i) r[i] = oracle_round(ur, r[i]);
 
-    /* line 5: y_k = omega_k r_k, computed in u_r, stored in u_z (R5, R6) */
+    /* scaling: y_k = omega_k r_k, computed in u_r, stored in u_z (R5, R6) */
     double omega = oracle_scale(pol->scale, delta[k], maxr);
     scale_to_y(n, uz, ur, omega, r, y);
-    /* line 6: z_k = M^-1 y_k in u_z */
+    /* preconditioning: z_k = M^-1 y_k in u_z */
     if (mtype == OR_M_CHEBYSHEV)
       oracle_cheb_apply(n, rowptr, col, &ch, uz, y, z, w0, w1, w2, w3);
     else
       apply_precond(mtype, n, uz, dinv[uz], y, z);
-    /* line 7: rho_k = r_k^T z_k (FP64) */
+    /* rho_k = r_k^T z_k (FP64) */
     double rho = oracle_dot(n, r, z);
     if (!isfinite(rho)) { status = OR_ERR_NONFINITE; break; }
     if (!(rho > 0.0)) { status = OR_ERR_BREAKDOWN; break; }
-    /* lines 8-11: beta_{k-1} = rho_k/rho_{k-1}; p_k = z_k + beta p_{k-1} in u_z;
+    /* beta_{k-1} = rho_k/rho_{k-1}; p_k = z_k + beta p_{k-1} in u_z;
        p_{k-1} is first brought to u_z when u_z changed.                   */
     double beta = first ? 0.0 : rho / rho_prev;
     for (int64_t i = 0; i < n; ++i) {
@@ -603,12 +603,12 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
     }
     p_prec = uz;
     first = 0;
-    /* lines 12-13: q_k = A p_k in u_r (R7); gamma_k = q_k^T p_k (FP64) */
+    /* q_k = A p_k in u_r (R7); gamma_k = q_k^T p_k (FP64) */
     oracle_spmv(n, rowptr, col, A[ur], ur, p, q);
     double gamma = oracle_dot(n, q, p);
     if (!isfinite(gamma)) { status = OR_ERR_NONFINITE; break; }
     if (!(gamma > 0.0)) { status = OR_ERR_BREAKDOWN; break; }
-    /* lines 14-16 */
+    /* alpha_k, x_{k+1}, r_{k+1} */
     double alpha = rho / gamma;
     for (int64_t i = 0; i < n; ++i) x[i] = fma(alpha, p[i], x[i]);
     double alpha_r = oracle_round(ur == OR_FP64 ? OR_FP64 : OR_FP32, alpha);
@@ -618,12 +618,12 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
     }
     ur_prev = ur; uz_prev = uz;
     rho_prev = rho;
-    /* line 17: delta_{k+1} = ||r_{k+1}|| (FP64); max|r| for the next scale */
+    /* delta_{k+1} = ||r_{k+1}|| (FP64); max|r| for the next scale */
     delta[k + 1] = oracle_nrm2(n, r);
     maxr = oracle_maxabs(n, r);
     if (relres_hist) relres_hist[k + 1] = delta[k + 1] / nb;
     if (!isfinite(delta[k + 1])) { status = OR_ERR_NONFINITE; k++; break; }
-    /* line 18: stop on the updated residual */
+    /* stop on the updated residual */
     if (delta[k + 1] <= tol_nb) {
       status = OR_OK;
       if (refreshes < pol->verify_refresh && k + 1 < maxit) {

@@ -58,7 +58,7 @@ struct TeamPart {
 template <int UZ, int UR, int MT, int IT>
 __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int64_t n, DevState* S) {
   using Part = TeamPart;
-  // Alg. 3 lines 5-10
+  // Alg. 3: scale, precondition, rho_k and beta
   {
     double rho = 0.0;
     Dot2 d2;
@@ -77,10 +77,10 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
     __syncthreads();
     if (S->done) return;
   }
-  // line 11 (p_k is read by other threads' gathers)
+  // Alg. 3: search direction (p_k is read by other threads' gathers)
   axpy_rows<UZ, 8, Part>(B, n, S);
   __syncthreads();
-  // lines 12-14
+  // Alg. 3: q_k = A p_k, gamma_k, alpha_k
   {
     double gam = 0.0;
     Dot2 d2;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
     __syncthreads();
     if (S->done) return;
   }
-  // lines 15-18
+  // Alg. 3: x and r updates, delta_{k+1}, stopping test, next precisions
   {
     double rr = 0.0;
     Dot2 d2;
@@ -150,7 +150,7 @@ __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
     B.x[i] = D.x[i];
   }
   __syncthreads();
-  // Alg. 3 line 1
+  // Alg. 3: initial residual
   {
     double v[2] = {0.0, 0.0};
     unsigned long long mx = 0ull;

@@ -3,14 +3,14 @@
 // is single-pass (last-block ticket) and the last block also performs the
 // scalar work of the algorithm, so no host synchronisation happens inside the
 // loop:
-//   k_precond : Alg. 3 lines 5-7    y = omega r (u_r), z = M^-1 y (u_z), rho;
-//                                   last block: beta (lines 8-10)
-//   k_axpy    : Alg. 3 line 11      p = z + beta p (u_z)
-//   k_spmv    : Alg. 3 lines 12-13  q = A p (u_r), gamma; last block: alpha
-//   k_update  : Alg. 3 lines 15-17  x += alpha p (FP64), r -= alpha q (u_r),
+//   k_precond : Alg. 3 scaling and preconditioning: y = omega r (u_r),
+//               z = M^-1 y (u_z), rho; last block: beta
+//   k_axpy    : Alg. 3 search direction: p = z + beta p (u_z)
+//   k_spmv    : Alg. 3 matrix product: q = A p (u_r), gamma; last block: alpha
+//   k_update  : Alg. 3 updates: x += alpha p (FP64), r -= alpha q (u_r),
 //                                   ||r||, max|r|; last block: stopping test
-//                                   (line 18), indicator and selector for the
-//                                   next iteration (lines 3-4), omega.
+//                                   (Alg. 3), indicator and selector for the
+//                                   next iteration (Alg. 3), omega.
 // Each kernel is specialised for one precision pair (u_z, u_r) (phase index
 // 2 u_z + u_r), so every variant gets its own register allocation.  The pair
 // of an iteration is decided on the device (last block of k_update / k_init)
@@ -250,7 +250,7 @@ __device__ __forceinline__ int ceil_log2(double m) {
   return eb - 1023 + (f ? 1 : 0);
 }
 
-// Decide the precisions of iteration st->k (Alg. 3 lines 3-4), the storage
+// Decide the precisions of iteration st->k (Alg. 3, precision selection), the storage
 // conversions they imply, and omega_k (reading R5).  Thread 0 of one block;
 // hist(t) gives delta_t.  Eq. (precision_selector): u_z from nu_k and u0, u_r
 // from eta_k (reading R2).  With the latch on, a u_r already at FP32 cannot
@@ -401,7 +401,7 @@ __device__ __forceinline__ typename Store<UR>::T sell_row(const Sell& A, int s, 
   return acc;
 }
 
-// FP64 fma-chain row product (initial/true residual, Alg. 3 line 1).
+// FP64 fma-chain row product (initial and true residual, Alg. 3).
 template <int IT, class Part = GridPart>
 __device__ __forceinline__ double sell_row64(const Sell& A, int s, int lane, int row,
                                              const double* __restrict__ x) {
@@ -433,7 +433,7 @@ struct Bufs {
   unsigned long long* pmax; // per-block partial maxima [G]
 };
 
-// Alg. 3 lines 7-10 on the state copy: rho_k, its checks (reading R12) and
+// Alg. 3 on the state copy: rho_k, its checks (reading R12) and
 // beta_{k-1} = rho_k / rho_{k-1}; completes the storage conversions.
 __device__ __forceinline__ void rho_step(DevState* s, double r) {
   s->rho = r;
@@ -474,7 +474,7 @@ __device__ __forceinline__ void init_rows(const Sell& A, const Bufs& B, double (
   }
 }
 
-// Alg. 3 line 1 on the state copy: ||b||, delta_0, the stopping test and the
+// Alg. 3 initialisation on the state copy: ||b||, delta_0, the stopping test and the
 // decision for iteration 0; returns delta_0.
 __device__ __forceinline__ double init_step(DevState* s, double bb, double rr, unsigned long long m) {
   double nb = sqrt(bb);
@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
 // elements so whole vectors stay in bounds; V = 1 on caller arrays).  Only the
 // first m = min(V, n - i0) elements of a vector are used and stored.
 
-// Alg. 3 lines 5-7 (+ the storage conversions of readings R10 and line 11).
+// Alg. 3 scaling, preconditioning and rho_k (+ the storage conversions of
+// reading R10 and of the search direction).
 template <int UZ, int UR, int MT, int V, class Part = GridPart>
 __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const DevState* st,
                                              double& rho, Dot2& d2) {
@@ -612,7 +613,7 @@ __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const Dev
   }
 }
 
-// p_{k-1} brought to the new u_z once, when u_z changed (line 11 computes p_k
+// p_{k-1} brought to the new u_z once, when u_z changed (the search direction p_k is computed
 // in u_z); the converted copy goes to the other search-direction buffer.
 template <int UZ, class Part = GridPart>
 __device__ __forceinline__ void cast_p(const Bufs& B, int64_t n, const DevState* st) {
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st
 }
 
 // ---------------------------------------------------------------------------
-// Alg. 3 line 11: p_k = z_k + beta_{k-1} p_{k-1} in u_z (p_0 = z_0).
+// Alg. 3 search direction: p_k = z_k + beta_{k-1} p_{k-1} in u_z (p_0 = z_0).
 // One element of p_k = z_k + beta p_{k-1} for binary32/binary16 storage:
 // binary32 fma, rounded once into u_z (reading R7).
 template <int UZ>
@@ -717,7 +718,7 @@ __global__ void __launch_bounds__(256) k_axpy(Bufs B, int64_t n, DevState* st) {
 }
 
 // ---------------------------------------------------------------------------
-// Alg. 3 lines 12-14: q_k = A p_k in u_r, gamma_k = q_k^T p_k (FP64),
+// Alg. 3 matrix product: q_k = A p_k in u_r, gamma_k = q_k^T p_k (FP64),
 // alpha_k = rho_k / gamma_k.  One thread per row of a warp's slice.
 // ---------------------------------------------------------------------------
 // Staged SpMV.  The matrix stream (values and column indices) is the bulk of
@@ -886,7 +887,7 @@ __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const De
   }
 }
 
-// Alg. 3 lines 13-14 on the state copy: gamma_k, its checks (reading R12),
+// Alg. 3 on the state copy: gamma_k, its checks (reading R12),
 // alpha_k = rho_k / gamma_k.
 __device__ __forceinline__ void gamma_step(DevState* s, double g) {
   s->gamma = g;
@@ -935,7 +936,7 @@ __global__ void __launch_bounds__(256) k_spmv(Sell A, Bufs B, DevState* st) {
 }
 
 // ---------------------------------------------------------------------------
-// Alg. 3 lines 15-18: x += alpha p (FP64), r -= alpha q (u_r),
+// Alg. 3 updates: x += alpha p (FP64), r -= alpha q (u_r),
 // delta_{k+1} = ||r|| (FP64), max|r| (exact); last block: stopping test and
 // the decision for iteration k+1.
 template <int UZ, int UR, int V, class Part = GridPart>
@@ -989,7 +990,7 @@ __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevS
   if constexpr (UR != P64) mx = abs_key(__uint_as_float((unsigned)mx));
 }
 
-// Alg. 3 lines 17-18 on the state copy: delta_{k+1}, the stopping test,
+// Alg. 3 on the state copy: delta_{k+1}, the stopping test,
 // k <- k + 1 and the decision for the new iteration; returns delta_{k+1}.
 __device__ __forceinline__ double update_step(DevState* s, double rr, unsigned long long m) {
   double d = sqrt(rr);

@@ -1,5 +1,5 @@
-"""Kernel-level parity through the C ABI: the device's SpMV (Alg. 3 line 12),
-FP64 residual (line 1), scale-and-precondition step (lines 5-6) and precision
+"""Kernel-level parity through the C ABI: the device's SpMV of Alg. 3, its
+FP64 initial residual, the scale-and-precondition step and the precision
 selector (Eq. precision_selector with Eq. eta_k / linear criterion) against
 the CPU oracle on the same seeded inputs.  All of these are elementwise or
 scalar computations with a fixed operation order, so the bar is bit-for-bit
