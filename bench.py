@@ -64,6 +64,12 @@ def config_dict(a, extra=None):
     return d
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
+# it is now (profiles/iteration_kernels_diffusion128.md); a kernel missing
+# here reports null.
+NCU_TRAFFIC = {"amp:spmv_gamma:uz16_ur64": 161.7e6, "amp:spmv_gamma:uz16_ur32": 96.5e6}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -263,7 +269,7 @@ def run_ours(args, rank, world):
     dk, dv = dom
     achieved = dv["gbs"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 3), "traffic": None, "kernel": dk,
+                "frac": round(achieved / peak, 3), "traffic": NCU_TRAFFIC.get(dk), "kernel": dk,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
     # end to end through the C ABI with pinned host buffers
