@@ -255,6 +255,7 @@ def run_ours(args, rank, world):
     idx_bytes = 2  # int16 column offsets (7-point offsets fit)
     kernels = {}
     for tag, ti in (("amp", tinfo), ("fp64", tinfo64)):
+        ksum = sum(ti.kernel_ms.values())   # shares of kernel time, as in an ncu launch list
         for (kn, ph), ms in ti.kernel_ms.items():
             L = ti.kernel_launches_by[(kn, ph)]
             us = ms / L * 1e3
@@ -262,7 +263,7 @@ def run_ours(args, rank, world):
             kernels[f"{tag}:{kn}:{ph}"] = {"launches": L, "avg_us": round(us, 2), "alg_bytes": int(by),
                                            "gbs": round(by / (us * 1e-6) / 1e9, 1),
                                            "frac": round(by / (us * 1e-6) / 1e9 / peak, 3),
-                                           "share": round(ms / ti.kernel_total_ms, 3)}
+                                           "share": round(ms / ksum, 3)}
     # dominant kernel of the AMP solve
     dom = max(((k, v) for k, v in kernels.items() if k.startswith("amp:")),
               key=lambda kv: kv[1]["avg_us"] * kv[1]["launches"])
