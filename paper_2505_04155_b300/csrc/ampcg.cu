@@ -1471,14 +1471,17 @@ static ampcg_status batched_persistent(const std::vector<int>& idx, ampcg_t cons
       first += cnt;
       if (cnt == 0) continue;
       const void* kern = g ? (const void*)k_batched<1> : (const void*)k_batched<0>;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchBlock, 0) != cudaSuccess ||
+      const int smem = g ? batch_smem_bytes<1>() : batch_smem_bytes<0>();
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) break;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchBlock, smem) != cudaSuccess ||
           per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
       }
       const int grid = sms * per_sm < cnt ? sms * per_sm : cnt;
-      if (g) k_batched<1><<<grid, kBatchBlock, 0, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
-      else k_batched<0><<<grid, kBatchBlock, 0, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
+      if (g) k_batched<1><<<grid, kBatchBlock, smem, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
+      else k_batched<0><<<grid, kBatchBlock, smem, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess)

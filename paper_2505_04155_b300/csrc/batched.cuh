@@ -40,6 +40,16 @@ struct BatchOut {
 };
 
 constexpr int kBatchBlock = 1024;
+
+// The staged SpMV in a 32-warp block: 3 stages per warp for binary32 values,
+// 2 for binary64, so the stages of every variant fit in shared memory.
+template <int UR> struct BatchStages { static constexpr int K = UR == P64 ? 2 : 3; };
+template <int IT>
+constexpr int batch_smem_bytes() {
+  return staged_smem_bytes<P32, IT, 3>(kBatchBlock / 32) > staged_smem_bytes<P64, IT, 2>(kBatchBlock / 32)
+             ? staged_smem_bytes<P32, IT, 3>(kBatchBlock / 32)
+             : staged_smem_bytes<P64, IT, 2>(kBatchBlock / 32);
+}
 // Work partition over the block's threads.  Vectors that other threads of
 // the block write during the launch are read with coherent loads
 // (ld.global.ca, never the read-only path); __syncthreads orders the writes
@@ -56,7 +66,8 @@ struct TeamPart {
 };
 
 template <int UZ, int UR, int MT, int IT>
-__device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int64_t n, DevState* S) {
+__device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int64_t n, DevState* S,
+                                              unsigned char* dsm) {
   using Part = TeamPart;
   // Alg. 3: scale, precondition, rho_k and beta
   {
@@ -84,7 +95,8 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
   {
     double gam = 0.0;
     Dot2 d2;
-    spmv_rows<UZ, UR, IT, Part>(A, B, S, gam, d2);
+    if (A.maxw <= kStageW) spmv_rows_staged<UZ, UR, IT, Part, BatchStages<UR>::K>(A, B, S, gam, d2, dsm);
+    else spmv_rows<UZ, UR, IT, Part>(A, B, S, gam, d2);
     double v[1];
     if constexpr ((UR != P64) && (UZ != P64)) {
       v[0] = block_sum_dot2(d2, 1.0);
@@ -119,27 +131,28 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
 }
 
 template <int MT, int IT>
-__device__ __forceinline__ void cta_dispatch(int ph, const Sell& A, const Bufs& B, int64_t n, DevState* S) {
+__device__ __forceinline__ void cta_dispatch(int ph, const Sell& A, const Bufs& B, int64_t n, DevState* S,
+                                             unsigned char* dsm) {
   switch (ph) {
-    case 0: cta_iteration<P64, P64, MT, IT>(A, B, n, S); break;
-    case 1: cta_iteration<P64, P32, MT, IT>(A, B, n, S); break;
-    case 2: cta_iteration<P32, P64, MT, IT>(A, B, n, S); break;
-    case 3: cta_iteration<P32, P32, MT, IT>(A, B, n, S); break;
-    case 4: cta_iteration<P16, P64, MT, IT>(A, B, n, S); break;
-    default: cta_iteration<P16, P32, MT, IT>(A, B, n, S); break;
+    case 0: cta_iteration<P64, P64, MT, IT>(A, B, n, S, dsm); break;
+    case 1: cta_iteration<P64, P32, MT, IT>(A, B, n, S, dsm); break;
+    case 2: cta_iteration<P32, P64, MT, IT>(A, B, n, S, dsm); break;
+    case 3: cta_iteration<P32, P32, MT, IT>(A, B, n, S, dsm); break;
+    case 4: cta_iteration<P16, P64, MT, IT>(A, B, n, S, dsm); break;
+    default: cta_iteration<P16, P32, MT, IT>(A, B, n, S, dsm); break;
   }
 }
 
 template <int IT>
 __device__ __forceinline__ void cta_dispatch_mt(int mt, int ph, const Sell& A, const Bufs& B, int64_t n,
-                                                DevState* S) {
-  if (mt == M_JACOBI) cta_dispatch<M_JACOBI, IT>(ph, A, B, n, S);
-  else cta_dispatch<M_NONE, IT>(ph, A, B, n, S);
+                                                DevState* S, unsigned char* dsm) {
+  if (mt == M_JACOBI) cta_dispatch<M_JACOBI, IT>(ph, A, B, n, S, dsm);
+  else cta_dispatch<M_NONE, IT>(ph, A, B, n, S, dsm);
 }
 
 // The whole solve of one system by one block (every thread calls it).
 template <int IT>
-__device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
+__device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh, unsigned char* dsm) {
   using Part = TeamPart;
   const Sell& A = D.A;
   const Bufs& B = D.B;
@@ -164,7 +177,7 @@ __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh) {
   const int limit = S->maxit + 1;
   for (;;) {
     while (!S->done) {
-      cta_dispatch_mt<IT>(D.mt, 2 * S->uz + S->ur, A, B, n, S);
+      cta_dispatch_mt<IT>(D.mt, 2 * S->uz + S->ur, A, B, n, S, dsm);
       if (++bodies > limit) {      // every iteration advances k or stops: cannot happen
         if (threadIdx.x == 0) {
           S->status = ST_INTERNAL;
@@ -209,6 +222,7 @@ template <int IT>
 __global__ void __launch_bounds__(kBatchBlock) k_batched(const BatchSys* sys, const int* order, int nsys,
                                                          int* next, const DevState* tmpl,
                                                          int verify_refresh, BatchOut* out) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ DevState S;
   __shared__ int s_i;
   for (;;) {
@@ -226,7 +240,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_batched(const BatchSys* sys, co
       S.prec_hist = D.prec_hist;
     }
     __syncthreads();
-    cta_solve<IT>(D, &S, verify_refresh);
+    cta_solve<IT>(D, &S, verify_refresh, dsm);
     __syncthreads();
     if (threadIdx.x == 0) {
       BatchOut o;

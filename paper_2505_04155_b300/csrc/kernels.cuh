@@ -318,15 +318,15 @@ __device__ void decide(DevState* st, H hist) {
 // ---------------------------------------------------------------------------
 // Work partition of the row and element loops, and how they load vectors.
 // GridPart: the whole grid works on one system per launch; every vector a
-// loop reads was written by an earlier launch, so loads may take the
-// read-only path.  TeamPart<CL> (batched.cuh): one block or a cluster of CL
-// blocks runs the whole solve in one launch; vectors written by other
-// threads between barriers are loaded coherently at L2 (ld.global.cg).
+// loop reads was written by an earlier launch, so any load path is valid
+// (plain cached loads for gathers, the read-only path for streams).
+// TeamPart (batched.cuh): one block runs a whole solve in one launch, and
+// vectors written by other threads between barriers are loaded coherently.
 struct GridPart {
   __device__ static __forceinline__ int64_t first() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
   __device__ static __forceinline__ int64_t count() { return (int64_t)gridDim.x * blockDim.x; }
   template <class T>
-  __device__ static __forceinline__ T ldm(const T* p) { return __ldg(p); }
+  __device__ static __forceinline__ T ldm(const T* p) { return *p; }
   template <int V, class T>
   __device__ static __forceinline__ void vldm(const T* p, T (&o)[V]) { vldg<V>(p, o); }
   // elements this thread itself reads and rewrites in the launch
@@ -750,20 +750,19 @@ template <int IT> struct IdxT;
 template <> struct IdxT<0> { using T = int; };
 template <> struct IdxT<1> { using T = short; };
 
-// Shared-memory bytes per block of 256 threads for the staged SpMV.
-template <int UR, int IT>
-constexpr int staged_smem_bytes() {
-  return 8 * StageCfg<UR>::K * 32 * kStageW *
-         (int)(sizeof(typename Store<UR>::T) + sizeof(typename IdxT<IT>::T));
+// Shared-memory bytes of the staged SpMV for a block of `warps` warps with K
+// stages per warp.
+template <int UR, int IT, int K = StageCfg<UR>::K>
+constexpr int staged_smem_bytes(int warps = 8) {
+  return warps * K * 32 * kStageW * (int)(sizeof(typename Store<UR>::T) + sizeof(typename IdxT<IT>::T));
 }
 
-template <int UZ, int UR, int IT>
+template <int UZ, int UR, int IT, class Part = GridPart, int K = StageCfg<UR>::K>
 __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, const DevState* st,
                                                  double& gam, Dot2& d2, unsigned char* smem) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
   using TI = typename IdxT<IT>::T;
-  constexpr int K = StageCfg<UR>::K;
   constexpr int SE = 32 * kStageW;  // entries per stage
   constexpr bool kSmall = (UR != P64) && (UZ != P64);
   const TZ* __restrict__ p = (const TZ*)(st->pcur ? B.p[0] : B.p[1]);
@@ -773,85 +772,90 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   TR* sv = (TR*)(smem + (size_t)wib * K * SE * (sizeof(TR) + sizeof(TI)));
   TI* si = (TI*)(sv + K * SE);
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t gw = Part::first() >> 5;
+  const int64_t nw = Part::count() >> 5;
   const int64_t spw = (A.nslices + nw - 1) / nw;
-  const int64_t s0 = gw * spw;
-  const int cnt = (int)(s0 >= A.nslices ? 0 : (s0 + spw < A.nslices ? spw : A.nslices - s0));
-  if (cnt <= 0) return;
-  long long hoff = 0;
-  int hw = 0;
-  if (lane < cnt) {
-    hoff = __ldg(A.off + s0 + lane);
-    hw = __ldg(A.width + s0 + lane);
-  }
-  auto issue = [&](int t) {
-    if (t < cnt) {
-      const long long o = __shfl_sync(0xffffffffu, hoff, t);
-      const int w = __shfl_sync(0xffffffffu, hw, t);
-      const int stg = t % K;
-      const char* gv = (const char*)(va + o);
-      char* dv = (char*)(sv + stg * SE);
-      const int nv = 2 * w * (int)sizeof(TR);  // 16-byte chunks: 32 w sizeof(TR) / 16
-#pragma unroll
-      for (int u = 0; u < kStageW * (int)sizeof(TR) / 16; ++u) {
-        const int c = lane + 32 * u;
-        if (c < nv) cp_async16(dv + 16 * c, gv + 16 * c);
-      }
-      const char* gi = (const char*)(ia + o);
-      char* di = (char*)(si + stg * SE);
-      const int ni = 2 * w * (int)sizeof(TI);
-#pragma unroll
-      for (int u = 0; u < (kStageW * (int)sizeof(TI) + 15) / 16; ++u) {
-        const int c = lane + 32 * u;
-        if (c < ni) cp_async16(di + 16 * c, gi + 16 * c);
-      }
+  const int64_t s1 = gw * spw + spw < A.nslices ? gw * spw + spw : A.nslices;
+  // chunks of at most 32 slices (one header per lane); one chunk in the
+  // single-system launch, whose grid gives every warp at most 32 slices
+  for (int64_t s0 = gw * spw; s0 < s1; s0 += 32) {
+    const int cnt = (int)(s1 - s0 < 32 ? s1 - s0 : 32);
+    long long hoff = 0;
+    int hw = 0;
+    if (lane < cnt) {
+      hoff = __ldg(A.off + s0 + lane);
+      hw = __ldg(A.width + s0 + lane);
     }
-    cp_async_commit();
-  };
-#pragma unroll
-  for (int t = 0; t < K - 1; ++t) issue(t);
-  for (int t = 0; t < cnt; ++t) {
-    issue(t + K - 1);
-    cp_async_wait<K - 1>();
-    __syncwarp();
-    const int w = __shfl_sync(0xffffffffu, hw, t);
-    const int64_t row = (s0 + t) * 32 + lane;
-    if (row < A.n) {
-      const int stg = t % K;
-      const TR* sa = sv + stg * SE + lane;
-      const TI* sc = si + stg * SE + lane;
-      // the row's w entries with w known at compile time (no per-entry predicates)
-      auto body = [&](auto wc) {
-        constexpr int W = decltype(wc)::value;
-        TR a[W];
-        int cc[W];
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-          a[j] = sa[32 * j];
-          cc[j] = IT ? (int)row + (int)sc[32 * j] : (int)sc[32 * j];
+    auto issue = [&](int t) {
+      if (t < cnt) {
+        const long long o = __shfl_sync(0xffffffffu, hoff, t);
+        const int w = __shfl_sync(0xffffffffu, hw, t);
+        const int stg = t % K;
+        const char* gv = (const char*)(va + o);
+        char* dv = (char*)(sv + stg * SE);
+        const int nv = 2 * w * (int)sizeof(TR);  // 16-byte chunks: 32 w sizeof(TR) / 16
+  #pragma unroll
+        for (int u = 0; u < kStageW * (int)sizeof(TR) / 16; ++u) {
+          const int c = lane + 32 * u;
+          if (c < nv) cp_async16(dv + 16 * c, gv + 16 * c);
         }
-        TR acc = (TR)0;
-#pragma unroll
-        for (int j = 0; j < W; ++j) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(p[cc[j]]), acc);
-        q[row] = acc;
-        if constexpr (kSmall) d2.add((float)acc, (float)p[row]);
-        else gam = fma(to_f64(acc), to_f64(p[row]), gam);
-      };
-      switch (w) {
-        case 1: body(std::integral_constant<int, 1>{}); break;
-        case 2: body(std::integral_constant<int, 2>{}); break;
-        case 3: body(std::integral_constant<int, 3>{}); break;
-        case 4: body(std::integral_constant<int, 4>{}); break;
-        case 5: body(std::integral_constant<int, 5>{}); break;
-        case 6: body(std::integral_constant<int, 6>{}); break;
-        case 7: body(std::integral_constant<int, 7>{}); break;
-        default: body(std::integral_constant<int, kStageW>{}); break;
+        const char* gi = (const char*)(ia + o);
+        char* di = (char*)(si + stg * SE);
+        const int ni = 2 * w * (int)sizeof(TI);
+  #pragma unroll
+        for (int u = 0; u < (kStageW * (int)sizeof(TI) + 15) / 16; ++u) {
+          const int c = lane + 32 * u;
+          if (c < ni) cp_async16(di + 16 * c, gi + 16 * c);
+        }
       }
+      cp_async_commit();
+    };
+  #pragma unroll
+    for (int t = 0; t < K - 1; ++t) issue(t);
+    for (int t = 0; t < cnt; ++t) {
+      issue(t + K - 1);
+      cp_async_wait<K - 1>();
+      __syncwarp();
+      const int w = __shfl_sync(0xffffffffu, hw, t);
+      const int64_t row = (s0 + t) * 32 + lane;
+      if (row < A.n) {
+        const int stg = t % K;
+        const TR* sa = sv + stg * SE + lane;
+        const TI* sc = si + stg * SE + lane;
+        // the row's w entries with w known at compile time (no per-entry predicates)
+        auto body = [&](auto wc) {
+          constexpr int W = decltype(wc)::value;
+          TR a[W];
+          int cc[W];
+  #pragma unroll
+          for (int j = 0; j < W; ++j) {
+            a[j] = sa[32 * j];
+            cc[j] = IT ? (int)row + (int)sc[32 * j] : (int)sc[32 * j];
+          }
+          TR acc = (TR)0;
+  #pragma unroll
+          for (int j = 0; j < W; ++j) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(Part::ldm(p + cc[j])), acc);
+          q[row] = acc;
+          const TZ pr = Part::ldm(p + row);
+          if constexpr (kSmall) d2.add((float)acc, (float)pr);
+          else gam = fma(to_f64(acc), to_f64(pr), gam);
+        };
+        switch (w) {
+          case 1: body(std::integral_constant<int, 1>{}); break;
+          case 2: body(std::integral_constant<int, 2>{}); break;
+          case 3: body(std::integral_constant<int, 3>{}); break;
+          case 4: body(std::integral_constant<int, 4>{}); break;
+          case 5: body(std::integral_constant<int, 5>{}); break;
+          case 6: body(std::integral_constant<int, 6>{}); break;
+          case 7: body(std::integral_constant<int, 7>{}); break;
+          default: body(std::integral_constant<int, kStageW>{}); break;
+        }
+      }
+      __syncwarp();  // the stage is refilled by the next trip's issue
     }
-    __syncwarp();  // the stage is refilled by the next trip's issue
+    cp_async_wait<0>();
+    __syncwarp();    // the next chunk refills the stages
   }
-  cp_async_wait<0>();
 }
 
 // Each warp owns a contiguous run of slices; it loads the headers (offset,
