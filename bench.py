@@ -475,6 +475,22 @@ def run_profile(args):
         for s in ss:
             s.close()
         return
+    if args.profile.startswith("cheb"):
+        # Chebyshev(8) on block-CSR Q1 elasticity, 48^3 nodes (330K dof), Phase 2 or
+        # FP64 precisions, profile_iters iterations, kernels launched one by one
+        import workloads as W
+        e = W.elasticity_q1(48, seed=0)
+        s = P.Solver.from_bsr(e.browptr, e.bcol, e.bval, 3, precond=P.M_CHEBYSHEV, degree=8)
+        bd = torch.as_tensor(W.rhs_uniform(e.nb * 3, seed=1), device="cuda")
+        pol = (P.Policy.pcg64() if args.profile == "cheb_fp64"
+               else P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32))
+        _, info = s.solve(bd, tol=1e-8, maxit=args.profile_iters or 20, policy=pol, history=False, timed=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "iters": info.iters,
+                          "kernel_us": {f"{k[0]}:{k[1]}": round(v / info.kernel_launches_by[k] * 1e3, 2)
+                                        for k, v in info.kernel_ms.items()}}), flush=True)
+        s.close()
+        return
     a, b = workload()
     s = P.Solver(a.rowptr, a.col, a.val)
     pol = {"amp": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3),
@@ -499,7 +515,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--profile", choices=["amp", "p1", "p2", "fp64", "batch_p1", "batch_p2"], default=None,
+    ap.add_argument("--profile", choices=["amp", "p1", "p2", "fp64", "batch_p1", "batch_p2", "cheb_p2", "cheb_fp64"],
+                    default=None,
                     help="run one solve for a profiler and exit")
     ap.add_argument("--profile-iters", type=int, default=0, help="maxit of the profiled solve (0: converge)")
     ap.add_argument("--workload", choices=["diffusion128", "elasticity96", "batch512", "adjoint64"],

@@ -523,8 +523,10 @@ static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
     add((const void*)k_precond<UZ, UR, MT>, KA_ELEM, 0, nvec, 0);
   }
   add((const void*)k_axpy<UZ>, KA_ELEM, 1, nvec, 0);
-  const int sm = c->maxw <= kStageW ? staged_smem_bytes<UR, IT>() : 0;
-  add((const void*)k_spmv<UZ, UR, IT>, KA_SPMV, 2, c->nslices * 32, sm);
+  const bool wide = c->maxw > kStageW;
+  const int sm = wide ? 0 : staged_smem_bytes<UR, IT>();
+  add(wide ? (const void*)k_spmv<UZ, UR, IT, true> : (const void*)k_spmv<UZ, UR, IT, false>, KA_SPMV, 2,
+      c->nslices * 32, sm);
   if (sm > 0) {
     // staged SpMV: a warp takes at most 32 slices, so at least nslices/32 warps
     int need = (int)((c->nslices + 32 * 8 - 1) / (32 * 8));

@@ -369,6 +369,55 @@ template <> __device__ __forceinline__ int col_at<1>(const Sell& A, long long e,
   return row + (int)__ldg(A.coff + e);
 }
 
+// acc = fma(val_j, x_j, acc) over the w stored entries of one row (entry j at
+// base + 32 j), in ascending order.  Values and columns are loaded 8 entries
+// (4 for binary64) at a time and the next chunk's loads are issued before the
+// current chunk's gathers, so a wide row (elasticity: ~80 entries) keeps
+// 8-16 loads in flight instead of one.
+template <int IT, class TA, class Acc, class Gather, class Fma>
+__device__ __forceinline__ Acc row_sum_chunked(const Sell& A, const TA* __restrict__ va, long long base, int w,
+                                               int row, Acc acc, Gather gather, Fma fmaop) {
+  constexpr int CH = (sizeof(TA) == 8 || sizeof(Acc) == 8) ? 4 : 8;
+  TA a[CH];
+  int c[CH];
+#pragma unroll
+  for (int u = 0; u < CH; ++u) {
+    a[u] = TA(0);
+    c[u] = row;
+    if (u < w) {
+      a[u] = __ldg(va + base + 32 * u);
+      c[u] = col_at<IT>(A, base + 32 * u, row);
+    }
+  }
+  for (int j0 = 0; j0 < w; j0 += CH) {
+    TA an[CH];
+    int cn[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = j0 + CH + u;
+      an[u] = TA(0);
+      cn[u] = row;
+      if (j < w) {
+        an[u] = __ldg(va + base + 32 * j);
+        cn[u] = col_at<IT>(A, base + 32 * j, row);
+      }
+    }
+    decltype(gather(0)) g[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (j0 + u < w) g[u] = gather(c[u]);
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (j0 + u < w) acc = fmaop(a[u], g[u], acc);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      a[u] = an[u];
+      c[u] = cn[u];
+    }
+  }
+  return acc;
+}
+
 // acc = sum_j a_ij p_j over row `row` of slice s (lane = row % 32).
 template <int UZ, int UR, int IT>
 __device__ __forceinline__ typename Store<UR>::T sell_row(const Sell& A, int s, int lane, int row,
@@ -393,11 +442,9 @@ __device__ __forceinline__ typename Store<UR>::T sell_row(const Sell& A, int s, 
       if (j < w) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(p[c[j]]), acc);
     }
   } else {
-    for (int j = 0; j < w; ++j) {
-      TR a = __ldg(va + base + 32 * j);
-      int c = col_at<IT>(A, base + 32 * j, row);
-      acc = fma_r<UR>(a, PToR<UZ, UR>::cv(p[c]), acc);
-    }
+    acc = row_sum_chunked<IT>(A, va, base, w, row, acc,
+                              [=](int j) { return PToR<UZ, UR>::cv(p[j]); },
+                              [](TR av, TR xv, TR s) { return fma_r<UR>(av, xv, s); });
   }
   return acc;
 }
@@ -408,12 +455,8 @@ __device__ __forceinline__ double sell_row64(const Sell& A, int s, int lane, int
                                              const double* __restrict__ x) {
   long long base = __ldg(A.off + s) + lane;
   int w = __ldg(A.width + s);
-  double t = 0.0;
-  for (int j = 0; j < w; ++j) {
-    long long e = base + 32 * j;
-    t = fma(__ldg(A.v64 + e), Part::ldm(x + col_at<IT>(A, e, row)), t);
-  }
-  return t;
+  return row_sum_chunked<IT>(A, A.v64, base, w, row, 0.0, [=](int j) { return Part::ldm(x + j); },
+                             [](double av, double xv, double t) { return fma(av, xv, t); });
 }
 
 // ---------------------------------------------------------------------------
@@ -906,9 +949,9 @@ __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const De
         for (int j = 0; j < 8; ++j)
           if (j < w) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(Part::ldm(p + c[j])), acc);
       } else {
-        for (int j = 0; j < w; ++j)
-          acc = fma_r<UR>(__ldg(va + base + 32 * j),
-                          PToR<UZ, UR>::cv(Part::ldm(p + col_at<IT>(A, base + 32 * j, (int)row))), acc);
+        acc = row_sum_chunked<IT>(A, va, base, w, (int)row, acc,
+                                  [=](int j) { return PToR<UZ, UR>::cv(Part::ldm(p + j)); },
+                                  [](TR av, TR xv, TR s) { return fma_r<UR>(av, xv, s); });
       }
       q[row] = acc;
       const TZ pr = Part::ldm(p + row);
@@ -935,17 +978,20 @@ __device__ __forceinline__ void gamma_step(DevState* s, double g) {
   }
 }
 
-// Launched with staged_smem_bytes<UR, IT>() of dynamic shared memory when
-// every slice is at most kStageW wide (staged path), else with none.
-template <int UZ, int UR, int IT>
-__global__ void __launch_bounds__(256, 4) k_spmv(Sell A, Bufs B, DevState* st) {
+// WIDE = false (every slice at most kStageW wide): the staged path, launched
+// with staged_smem_bytes<UR, IT>() of dynamic shared memory.  WIDE = true:
+// the direct path with chunked row sums, no dynamic shared memory (a kernel
+// of its own, so the wide-row code does not take registers from the staged
+// one).
+template <int UZ, int UR, int IT, bool WIDE>
+__global__ void __launch_bounds__(256, WIDE ? 3 : 4) k_spmv(Sell A, Bufs B, DevState* st) {
   extern __shared__ __align__(16) unsigned char dsm[];
   if (st->done) return;
   if (phase_mismatch(st, UZ, UR)) return;
   double gam = 0.0;
   Dot2 d2;
-  if (A.maxw <= kStageW) spmv_rows_staged<UZ, UR, IT>(A, B, st, gam, d2, dsm);
-  else spmv_rows<UZ, UR, IT>(A, B, st, gam, d2);
+  if constexpr (WIDE) spmv_rows<UZ, UR, IT>(A, B, st, gam, d2);
+  else spmv_rows_staged<UZ, UR, IT>(A, B, st, gam, d2, dsm);
   double v[1];
   if constexpr ((UR != P64) && (UZ != P64)) {
     v[0] = block_sum_dot2(d2, 1.0);
@@ -1590,8 +1636,8 @@ __global__ void __launch_bounds__(256) k_cheb_step(Sell A, Cheb C, DevState* st,
   using TZ = typename Store<UZ>::T;
   if (st->done) return;
   if (phase_mismatch(st, UZ, -1)) return;
-  const TZ* __restrict__ dp = (const TZ*)C.d[(j - 1) & 1];
-  TZ* dn = (TZ*)C.d[j & 1];
+  const TZ* __restrict__ dp = (const TZ*)(((j - 1) & 1) ? C.d[1] : C.d[0]);
+  TZ* dn = (TZ*)((j & 1) ? C.d[1] : C.d[0]);
   TZ* res = (TZ*)C.res;
   TZ* u = (TZ*)C.u;
   const float c1f = __double2float_rn(c1), c2f = __double2float_rn(c2);
@@ -1605,25 +1651,16 @@ __global__ void __launch_bounds__(256) k_cheb_step(Sell A, Cheb C, DevState* st,
     int w = __ldg(A.width + s);
     TZ t;
     if constexpr (UZ == P64) {
-      double acc = 0.0;
-      for (int k = 0; k < w; ++k) {
-        long long e = base + 32ll * k;
-        acc = fma(__ldg(C.ah64 + e), dp[col_at<IT>(A, e, row)], acc);
-      }
-      t = acc;
+      t = row_sum_chunked<IT>(A, C.ah64, base, w, row, 0.0, [=](int j) { return dp[j]; },
+                              [](double av, double xv, double s) { return fma(av, xv, s); });
     } else if constexpr (UZ == P32) {
-      float acc = 0.f;
-      for (int k = 0; k < w; ++k) {
-        long long e = base + 32ll * k;
-        acc = __fmaf_rn(__ldg(C.ah32 + e), dp[col_at<IT>(A, e, row)], acc);
-      }
-      t = acc;
+      t = row_sum_chunked<IT>(A, C.ah32, base, w, row, 0.f, [=](int j) { return dp[j]; },
+                              [](float av, float xv, float s) { return __fmaf_rn(av, xv, s); });
     } else {
-      float acc = 0.f;
-      for (int k = 0; k < w; ++k) {
-        long long e = base + 32ll * k;
-        acc = __fmaf_rn(__half2float(C.ah16[e]), __half2float(dp[col_at<IT>(A, e, row)]), acc);
-      }
+      float acc = row_sum_chunked<IT>(A, C.ah16, base, w, row, 0.f, [=](int j) { return dp[j]; },
+                                      [](__half av, __half xv, float s) {
+                                        return __fmaf_rn(__half2float(av), __half2float(xv), s);
+                                      });
       t = __float2half_rn(acc);
     }
     TZ rs = sub_u<UZ>(res[row], t);
