@@ -224,6 +224,40 @@ __device__ __forceinline__ bool linear_switch(const DevState* s, H delta, int k)
   return eta_linear_dev(delta, k, ell, s->C) <= s->tol_nb;
 }
 
+// eta_k <= tol ||b|| for Eq. (eta_k).  eta_k = eps32 (c3 S1 + c2 S2) with
+// S1 = sum of delta_{t-1}, S2 = sum of delta_t over the window: all terms are
+// positive, so sums taken in any order are within (d + 4) u of the exact
+// value, as is the binary64 evaluation of the formula in its own order; the
+// bracket uses four independent partial sums (the exact-order evaluation costs
+// a chain of ~4 (d + 1) dependent binary64 operations).
+template <class H>
+__device__ __forceinline__ bool window_switch(const DevState* s, H delta, int k) {
+  const int d = s->d;
+  if (k < d) return false;   // eta_k = +inf (reading R3)
+  double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
+  int t = k - d;
+  for (; t + 3 <= k; t += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int tt = t + u;
+      a[u] = __dadd_rn(a[u], (tt >= 1) ? delta(tt - 1) : delta(0));
+      b[u] = __dadd_rn(b[u], delta(tt));
+    }
+  }
+  for (; t <= k; ++t) {
+    a[0] = __dadd_rn(a[0], (t >= 1) ? delta(t - 1) : delta(0));
+    b[0] = __dadd_rn(b[0], delta(t));
+  }
+  const double s1 = __dadd_rn(__dadd_rn(a[0], a[1]), __dadd_rn(a[2], a[3]));
+  const double s2 = __dadd_rn(__dadd_rn(b[0], b[1]), __dadd_rn(b[2], b[3]));
+  const double c3 = __dadd_rn(3.0, s->C), c2 = __dadd_rn(2.0, s->C);
+  const double eta = __dmul_rn(AMPCG_EPS32, __dadd_rn(__dmul_rn(c3, s1), __dmul_rn(c2, s2)));
+  const double T = s->tol_nb;
+  if (eta < __dmul_rn(T, 1.0 - kEtaMargin)) return true;
+  if (eta > __dmul_rn(T, 1.0 + kEtaMargin)) return false;
+  return eta_window_dev(delta, k, d, s->C) <= T;
+}
+
 // 2^e as binary64 / binary32 (round-to-nearest-even of the exact power),
 // built from the bit pattern.
 __device__ __forceinline__ double pow2_f64(int e) {
@@ -271,7 +305,7 @@ __device__ void decide(DevState* st, H hist) {
     else uz = (u0 > P16) ? u0 : P16;
     bool sw;
     if (st->latch && st->ur == P32) sw = true;
-    else if (st->criterion == CRIT_WINDOW) sw = eta_window_dev(hist, k, st->d, st->C) <= st->tol_nb;
+    else if (st->criterion == CRIT_WINDOW) sw = window_switch(st, hist, k);
     else sw = linear_switch(st, hist, k);
     ur = sw ? P32 : P64;
     if (st->latch) {
