@@ -887,48 +887,81 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
       }
       cp_async_commit();
     };
-  #pragma unroll
+#pragma unroll
     for (int t = 0; t < K - 1; ++t) issue(t);
-    for (int t = 0; t < cnt; ++t) {
-      issue(t + K - 1);
-      cp_async_wait<K - 1>();
-      __syncwarp();
-      const int w = __shfl_sync(0xffffffffu, hw, t);
-      const int64_t row = (s0 + t) * 32 + lane;
-      if (row < A.n) {
-        const int stg = t % K;
-        const TR* sa = sv + stg * SE + lane;
-        const TI* sc = si + stg * SE + lane;
-        // the row's w entries with w known at compile time (no per-entry predicates)
-        auto body = [&](auto wc) {
-          constexpr int W = decltype(wc)::value;
-          TR a[W];
-          int cc[W];
-  #pragma unroll
-          for (int j = 0; j < W; ++j) {
-            a[j] = sa[32 * j];
-            cc[j] = IT ? (int)row + (int)sc[32 * j] : (int)sc[32 * j];
-          }
-          TR acc = (TR)0;
-  #pragma unroll
-          for (int j = 0; j < W; ++j) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(Part::ldm(p + cc[j])), acc);
-          q[row] = acc;
-          const TZ pr = Part::ldm(p + row);
-          if constexpr (kSmall) d2.add((float)acc, (float)pr);
-          else gam = fma(to_f64(acc), to_f64(pr), gam);
-        };
-        switch (w) {
-          case 1: body(std::integral_constant<int, 1>{}); break;
-          case 2: body(std::integral_constant<int, 2>{}); break;
-          case 3: body(std::integral_constant<int, 3>{}); break;
-          case 4: body(std::integral_constant<int, 4>{}); break;
-          case 5: body(std::integral_constant<int, 5>{}); break;
-          case 6: body(std::integral_constant<int, 6>{}); break;
-          case 7: body(std::integral_constant<int, 7>{}); break;
-          default: body(std::integral_constant<int, kStageW>{}); break;
-        }
+    // one row's product over a slice held in stage stg (w entries, w known at
+    // compile time: no per-entry predicates)
+    auto rowprod = [&](auto wc, int stg, int64_t row, TR& acc) {
+      constexpr int W = decltype(wc)::value;
+      const TR* sa = sv + stg * SE + lane;
+      const TI* sc = si + stg * SE + lane;
+      TR a[W];
+      int cc[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        a[j] = sa[32 * j];
+        cc[j] = IT ? (int)row + (int)sc[32 * j] : (int)sc[32 * j];
       }
-      __syncwarp();  // the stage is refilled by the next trip's issue
+      TZ g[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) g[j] = Part::ldm(p + cc[j]);
+      acc = (TR)0;
+#pragma unroll
+      for (int j = 0; j < W; ++j) acc = fma_r<UR>(a[j], PToR<UZ, UR>::cv(g[j]), acc);
+    };
+    auto finish = [&](int64_t row, TR acc) {
+      q[row] = acc;
+      const TZ pr = Part::ldm(p + row);
+      if constexpr (kSmall) d2.add((float)acc, (float)pr);
+      else gam = fma(to_f64(acc), to_f64(pr), gam);
+    };
+    // one slice, or two of equal width whose gathers then overlap
+    auto dispatch = [&](int w, auto fn) {
+      switch (w) {
+        case 1: fn(std::integral_constant<int, 1>{}); break;
+        case 2: fn(std::integral_constant<int, 2>{}); break;
+        case 3: fn(std::integral_constant<int, 3>{}); break;
+        case 4: fn(std::integral_constant<int, 4>{}); break;
+        case 5: fn(std::integral_constant<int, 5>{}); break;
+        case 6: fn(std::integral_constant<int, 6>{}); break;
+        case 7: fn(std::integral_constant<int, 7>{}); break;
+        default: fn(std::integral_constant<int, kStageW>{}); break;
+      }
+    };
+    // Invariant at the top of a trip at slice t: groups 0 .. t + K - 2 issued
+    // (each issue commits one group, group i holding slice i in stage i % K).
+    for (int t = 0; t < cnt;) {
+      const int w0 = __shfl_sync(0xffffffffu, hw, t);
+      const int w1 = __shfl_sync(0xffffffffu, hw, t + 1 < cnt ? t + 1 : t);
+      const int64_t row = (s0 + t) * 32 + lane;
+      if (K >= 3 && t + 1 < cnt && w0 == w1 && (s0 + t + 2) * 32 <= A.n) {
+        issue(t + K - 1);          // into the stage of slice t - 1 (consumed)
+        cp_async_wait<K - 2>();    // slices t and t + 1 have landed
+        __syncwarp();
+        dispatch(w0, [&](auto wc) {
+          TR acc0, acc1;
+          rowprod(wc, t % K, row, acc0);
+          rowprod(wc, (t + 1) % K, row + 32, acc1);
+          finish(row, acc0);
+          finish(row + 32, acc1);
+        });
+        __syncwarp();              // the stages are refilled by the next issues
+        issue(t + K);              // into the stage of slice t (consumed)
+        t += 2;
+      } else {
+        issue(t + K - 1);
+        cp_async_wait<K - 1>();
+        __syncwarp();
+        if (row < A.n) {
+          dispatch(w0, [&](auto wc) {
+            TR acc;
+            rowprod(wc, t % K, row, acc);
+            finish(row, acc);
+          });
+        }
+        __syncwarp();              // the stage is refilled by the next trip's issue
+        t += 1;
+      }
     }
     cp_async_wait<0>();
     __syncwarp();    // the next chunk refills the stages
