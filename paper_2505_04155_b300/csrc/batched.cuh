@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_batched(const BatchSys* sys, co
                                                          int verify_refresh, BatchOut* out) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ DevState S;
+  __shared__ BatchSys D;   // the system's descriptor, shared by the block (not per-thread local memory)
   __shared__ int s_i;
   for (;;) {
     __syncthreads();
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_batched(const BatchSys* sys, co
     const int q = s_i;
     if (q >= nsys) return;
     const int i = order[q];
-    const BatchSys D = sys[i];
+    if (threadIdx.x == 0) D = sys[i];
     state_load(&S, tmpl);
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -143,3 +143,22 @@ def test_larger_systems_match_oracle_and_are_independent():
     assert torch.equal(x1[0], xs[1]) and i1[0].iters == infos[1].iters
     for s in solvers:
         s.close()
+
+
+def test_batched_statuses():
+    # per-system statuses in the persistent kernel: converged, zero right-hand
+    # side (done at iteration 0), maxit reached, non-finite input
+    mats, rhs = W.batch_2d(4, seed=8, smin=12, smax=24)
+    rhs[1] = np.zeros_like(rhs[1])
+    solvers = [P.Solver(m.rowptr, m.col, m.val) for m in mats]
+    xs, infos = _solve_batched(solvers, rhs, P.Policy(verify_refresh=3))
+    assert infos[0].status == P.OK and infos[1].status == P.OK and infos[1].iters == 0
+    assert not torch.any(xs[1])
+    xs, infos = _solve_batched(solvers[:1], rhs[:1], P.Policy(), maxit=3)
+    assert infos[0].status == P.NOT_CONVERGED and infos[0].iters == 3
+    bad = rhs[2].copy()
+    bad[4] = np.nan
+    xs, infos = _solve_batched([solvers[2], solvers[3]], [bad, rhs[3]], P.Policy())
+    assert infos[0].status == P.ERR_NONFINITE and infos[1].status == P.OK
+    for s in solvers:
+        s.close()
