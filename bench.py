@@ -67,7 +67,7 @@ def config_dict(a, extra=None):
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it is now (profiles/iteration_kernels_diffusion128.md); a kernel missing
 # here reports null.
-NCU_TRAFFIC = {"amp:spmv_gamma:uz16_ur64": 161.7e6, "amp:spmv_gamma:uz16_ur32": 96.5e6}
+NCU_TRAFFIC = {"amp:spmv_gamma:uz16_ur64": 161.9e6, "amp:spmv_gamma:uz16_ur32": 96.3e6}
 
 
 def peaks():
