@@ -124,13 +124,14 @@ struct ampcg_ctx {
   double* ah64 = nullptr;
   float* ah32 = nullptr;
   __half* ah16 = nullptr;
+  unsigned* ahp = nullptr;      // packed FP16 value + int16 offset (int16-offset matrices)
   double* ds64 = nullptr;
   float* ds32 = nullptr;
   __half* ds16 = nullptr;
   void *cres = nullptr, *cd0 = nullptr, *cd1 = nullptr, *cu = nullptr;
   Cheb cheb() const {
     Cheb C;
-    C.ah64 = ah64; C.ah32 = ah32; C.ah16 = ah16;
+    C.ah64 = ah64; C.ah32 = ah32; C.ah16 = ah16; C.ahp = ahp;
     C.ds64 = ds64; C.ds32 = ds32; C.ds16 = ds16;
     C.res = cres; C.d[0] = cd0; C.d[1] = cd1; C.u = cu;
     C.inv_theta = cheb_inv_theta;
@@ -178,7 +179,7 @@ static void release(ampcg_ctx* c) {
   if (!c) return;
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
-  void* ptrs[] = {c->ah64, c->ah32, c->ah16, c->ds64, c->ds32, c->ds16, c->cres, c->cd0, c->cd1, c->cu,
+  void* ptrs[] = {c->ah64, c->ah32, c->ah16, c->ahp, c->ds64, c->ds32, c->ds16, c->cres, c->cd0, c->cd1, c->cu,
                   c->rowptr, c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
                   c->dinv16, c->x, c->b, c->r64, c->t, c->r32, c->z, c->p0, c->p1, c->q,
                   c->part, c->pmax, c->st, c->dhist, c->phist};
@@ -391,6 +392,7 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
     TRY(dalloc(&c->ah64, stored));
     TRY(dalloc(&c->ah32, stored));
     TRY(dalloc(&c->ah16, stored));
+    if (c->idx16) TRY(dalloc(&c->ahp, stored));
     TRY(dalloc(&c->ds64, npad));
     TRY(dalloc(&c->ds32, npad));
     TRY(dalloc(&c->ds16, npad));
@@ -569,10 +571,10 @@ static ampcg_status cheb_prepare(ampcg_ctx* c) {
   if (e == cudaSuccess) {
     if (c->idx16) {
       k_cheb_setup<1><<<gs, kBlock, 0, s>>>(A, c->ah64, c->ah32, c->ah16, c->ds64, c->ds32, c->ds16, gk);
-      k_cheb_setup2<1><<<gs, kBlock, 0, s>>>(A, c->ds64, c->ah64, c->ah32, c->ah16, gk);
+      k_cheb_setup2<1><<<gs, kBlock, 0, s>>>(A, c->ds64, c->ah64, c->ah32, c->ah16, c->ahp, gk);
     } else {
       k_cheb_setup<0><<<gs, kBlock, 0, s>>>(A, c->ah64, c->ah32, c->ah16, c->ds64, c->ds32, c->ds16, gk);
-      k_cheb_setup2<0><<<gs, kBlock, 0, s>>>(A, c->ds64, c->ah64, c->ah32, c->ah16, gk);
+      k_cheb_setup2<0><<<gs, kBlock, 0, s>>>(A, c->ds64, c->ah64, c->ah32, c->ah16, nullptr, gk);
     }
     e = cudaGetLastError();
   }

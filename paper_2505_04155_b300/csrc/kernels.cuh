@@ -1613,6 +1613,10 @@ struct Cheb {
   const double* ah64;
   const float* ah32;
   const __half* ah16;
+  // binary16 Ahat value and int16 column offset of each stored entry in one
+  // 32-bit word (value in the low half), when the offsets fit: one load per
+  // entry instead of two for the FP16 steps
+  const unsigned* ahp;
   const double* ds64;
   const float* ds32;
   const __half* ds16;
@@ -1697,6 +1701,37 @@ __global__ void __launch_bounds__(256) k_cheb_init(Bufs B, Cheb C, int64_t n, De
 
 // One Chebyshev step j >= 1: t = Ahat d_{j-1} (accumulated in u_z's compute
 // precision), res -= t, d_j = c1 d_{j-1} + c2 res, u += d_j.  Thread per row.
+// Row product of the packed FP16 Chebyshev matrix (Cheb::ahp): FP32
+// accumulation in ascending entry order, 8 entries per chunk with the next
+// chunk's words loaded before the current chunk's gathers.
+__device__ __forceinline__ float row_sum_packed16(const unsigned* __restrict__ ahp, long long base, int w,
+                                                  int row, const __half* __restrict__ x) {
+  constexpr int CH = 8;
+  unsigned a[CH];
+#pragma unroll
+  for (int u = 0; u < CH; ++u) a[u] = (u < w) ? __ldg(ahp + base + 32 * u) : 0u;
+  float acc = 0.f;
+  for (int j0 = 0; j0 < w; j0 += CH) {
+    unsigned an[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = j0 + CH + u;
+      an[u] = (j < w) ? __ldg(ahp + base + 32 * j) : 0u;
+    }
+    __half g[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (j0 + u < w) g[u] = x[row + (int)(short)(a[u] >> 16)];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (j0 + u < w)
+        acc = __fmaf_rn(__half2float(__ushort_as_half((unsigned short)(a[u] & 0xffffu))), __half2float(g[u]), acc);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) a[u] = an[u];
+  }
+  return acc;
+}
+
 template <int UZ, int IT>
 __global__ void __launch_bounds__(256) k_cheb_step(Sell A, Cheb C, DevState* st, int j, double c1,
                                                    double c2) {
@@ -1724,10 +1759,15 @@ __global__ void __launch_bounds__(256) k_cheb_step(Sell A, Cheb C, DevState* st,
       t = row_sum_chunked<IT>(A, C.ah32, base, w, row, 0.f, [=](int j) { return dp[j]; },
                               [](float av, float xv, float s) { return __fmaf_rn(av, xv, s); });
     } else {
-      float acc = row_sum_chunked<IT>(A, C.ah16, base, w, row, 0.f, [=](int j) { return dp[j]; },
-                                      [](__half av, __half xv, float s) {
-                                        return __fmaf_rn(__half2float(av), __half2float(xv), s);
-                                      });
+      float acc;
+      if (IT == 1 && C.ahp) {
+        acc = row_sum_packed16(C.ahp, base, w, row, dp);
+      } else {
+        acc = row_sum_chunked<IT>(A, C.ah16, base, w, row, 0.f, [=](int j) { return dp[j]; },
+                                  [](__half av, __half xv, float s) {
+                                    return __fmaf_rn(__half2float(av), __half2float(xv), s);
+                                  });
+      }
       t = __float2half_rn(acc);
     }
     TZ rs = sub_u<UZ>(res[row], t);
@@ -1813,7 +1853,7 @@ __global__ void k_cheb_setup(Sell A, double* ah64, float* ah32, __half* ah16, do
 
 template <int IT>
 __global__ void k_cheb_setup2(Sell A, const double* ds64, double* ah64, float* ah32, __half* ah16,
-                              unsigned long long* gersh) {
+                              unsigned* ahp, unsigned long long* gersh) {
   int lane = threadIdx.x & 31;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1829,7 +1869,10 @@ __global__ void k_cheb_setup2(Sell A, const double* ds64, double* ah64, float* a
       double ah = __dmul_rn(__dmul_rn(di, A.v64[e]), ds64[c]);
       ah64[e] = ah;
       ah32[e] = __double2float_rn(ah);
-      ah16[e] = d2h(ah);
+      const __half h = d2h(ah);
+      ah16[e] = h;
+      if (IT == 1 && ahp)
+        ahp[e] = ((unsigned)(unsigned short)A.coff[e] << 16) | (unsigned)__half_as_ushort(h);
       sum += fabs(ah);
     }
     atomicMax(gersh, abs_key(sum));
