@@ -3,10 +3,10 @@
 // A context owns the matrix in the sliced layout with its FP64/FP32 value
 // copies, the Jacobi inverse diagonal in three precisions, every vector buffer
 // of the iteration and one device state block.  A solve is: copy b and x_0 in,
-// one initial-residual launch, then a CUDA graph whose conditional WHILE node
-// repeats a body of `graph_chunk` iterations (4 launches each) until the
-// device sets `done`; then an FP64 true-residual launch and one read of the
-// state block.  The host synchronises once per solve (plus once per optional
+// one initial-residual launch, then a CUDA graph of conditional nodes that
+// repeats chunks of `graph_chunk` iterations (4 launches each with Jacobi)
+// of the current precision pair until the device sets `done`; then an FP64
+// true-residual launch and one read of the state block.  The host synchronises once per solve (plus once per optional
 // residual replacement).
 #include <cuda_runtime.h>
 
@@ -518,13 +518,13 @@ static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
   if constexpr (MT == M_CHEBYSHEV) {
     add((const void*)k_cheb_init<UZ, UR>, KA_CINIT, 0, n, 0);
     for (int j = 1; j < c->cheb_m; ++j)
-      add((const void*)k_cheb_step<UZ, IT>, KA_CSTEP, 0, c->nslices * 32, 0, j, c->cheb_c1[j - 1],
+      add((const void*)k_cheb_step<UZ, UR, IT>, KA_CSTEP, 0, c->nslices * 32, 0, j, c->cheb_c1[j - 1],
           c->cheb_c2[j - 1]);
     add((const void*)k_cheb_final<UZ, UR>, KA_CFINAL, 0, n, 0);
   } else {
     add((const void*)k_precond<UZ, UR, MT>, KA_ELEM, 0, nvec, 0);
   }
-  add((const void*)k_axpy<UZ>, KA_ELEM, 1, nvec, 0);
+  add((const void*)k_axpy<UZ, UR>, KA_ELEM, 1, nvec, 0);
   const bool wide = c->maxw > kStageW;
   const int sm = wide ? 0 : staged_smem_bytes<UR, IT>();
   add(wide ? (const void*)k_spmv<UZ, UR, IT, true> : (const void*)k_spmv<UZ, UR, IT, false>, KA_SPMV, 2,
@@ -613,18 +613,16 @@ struct ArgPack {
   Cheb C;
   int64_t n;
   DevState* st;
-  cudaGraphConditionalHandle h;
-  int has_next, j;
+  int j;
   double c1, c2;
   void* a[8];
-  ArgPack(const ampcg_ctx* c, cudaGraphConditionalHandle hn, int has)
-      : B(c->bufs()), A(c->sell()), C(c->cheb()), n(c->n), st(c->st), h(hn), has_next(has), j(0),
-        c1(0), c2(0) {}
+  explicit ArgPack(const ampcg_ctx* c)
+      : B(c->bufs()), A(c->sell()), C(c->cheb()), n(c->n), st(c->st), j(0), c1(0), c2(0) {}
   void** args(const Launch& L) {
     switch (L.kind) {
-      case KA_ELEM: a[0] = &B; a[1] = &n; a[2] = &st; break;
+      case KA_ELEM:
+      case KA_UPD: a[0] = &B; a[1] = &n; a[2] = &st; break;
       case KA_SPMV: a[0] = &A; a[1] = &B; a[2] = &st; break;
-      case KA_UPD: a[0] = &B; a[1] = &n; a[2] = &st; a[3] = &h; a[4] = &has_next; break;
       case KA_CINIT:
       case KA_CFINAL: a[0] = &B; a[1] = &C; a[2] = &n; a[3] = &st; break;
       case KA_CSTEP:
@@ -640,7 +638,7 @@ struct ArgPack {
 // ev[slot] is recorded before the first kernel of each slot and ev[4] after
 // the last kernel.
 static cudaError_t launch_phase(ampcg_ctx* c, int ph, cudaStream_t s, cudaEvent_t* ev) {
-  ArgPack pa(c, 0, 0);
+  ArgPack pa(c);
   int slot = -1;
   for (const Launch& L : c->seq[ph]) {
     while (ev && slot < L.slot) {   // slots without a kernel in this phase get an empty interval
@@ -670,11 +668,16 @@ static cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const c
   return cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &p);
 }
 
-// Loop graph: WHILE(!done) { k_phase; SWITCH_0 .. SWITCH_{chunk-1}; k_loop_ctl }.
-// SWITCH_i has six bodies, one per phase, each holding that phase's launch
-// sequence; the update kernel of iteration i sets the value of SWITCH_{i+1}
-// (k_phase sets SWITCH_0).  After the stop every value is AMPCG_PHASE_NONE,
-// which matches no body, so the rest of the chunk launches nothing.
+// Loop graph:
+//   WHILE(!done) {
+//     k_phase;                                  // SWITCH value = current pair
+//     SWITCH { body ph (one per pair 2 u_z + u_r):
+//       WHILE(pair == ph && !done) { `chunk` x (ph's launch sequence); k_chunk_ctl } }
+//     k_loop_ctl }
+// A SWITCH is evaluated once per precision change (about 5 us each on B300,
+// against about 1.3 us per kernel node); after a change or the stop inside a
+// chunk, the chunk's remaining launches return at entry (phase_mismatch,
+// done).
 static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
   if (c->gexec && c->graph_chunk == chunk) return AMPCG_OK;
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
@@ -690,38 +693,47 @@ static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
   cudaGraphNode_t wnode;
   CUDA_TRY(cudaGraphAddNode(&wnode, c->graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  std::vector<cudaGraphConditionalHandle> hs(chunk);
-  for (int i = 0; i < chunk; ++i)
-    CUDA_TRY(cudaGraphConditionalHandleCreate(&hs[i], body, AMPCG_PHASE_NONE, cudaGraphCondAssignDefault));
+  cudaGraphConditionalHandle hs;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&hs, body, AMPCG_PHASE_NONE, cudaGraphCondAssignDefault));
   DevState* st = c->st;
-  cudaGraphConditionalHandle h0 = hs[0];
-  void* aphase[2] = {&st, &h0};
-  cudaGraphNode_t prev;
-  CUDA_TRY(add_kernel_node(&prev, body, nullptr, (const void*)k_phase, 1, 1, aphase));
-  for (int i = 0; i < chunk; ++i) {
-    cudaGraphNodeParams sp = {cudaGraphNodeTypeConditional};
-    sp.type = cudaGraphNodeTypeConditional;
-    sp.conditional.handle = hs[i];
-    sp.conditional.type = cudaGraphCondTypeSwitch;
-    sp.conditional.size = 6;
-    cudaGraphNode_t snode;
-    CUDA_TRY(cudaGraphAddNode(&snode, body, &prev, nullptr, 1, &sp));
-    bool has_next = i + 1 < chunk;
-    ArgPack pa(c, has_next ? hs[i + 1] : 0, has_next ? 1 : 0);
-    for (int ph = 0; ph < 6; ++ph) {
-      cudaGraph_t pg = sp.conditional.phGraph_out[ph];
-      cudaGraphNode_t kn = nullptr;
+  void* aphase[2] = {&st, &hs};
+  cudaGraphNode_t kphase;
+  CUDA_TRY(add_kernel_node(&kphase, body, nullptr, (const void*)k_phase, 1, 1, aphase));
+  cudaGraphNodeParams sp = {cudaGraphNodeTypeConditional};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = hs;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = 6;
+  cudaGraphNode_t snode;
+  CUDA_TRY(cudaGraphAddNode(&snode, body, &kphase, nullptr, 1, &sp));
+  ArgPack pa(c);
+  for (int ph = 0; ph < 6; ++ph) {
+    cudaGraph_t pg = sp.conditional.phGraph_out[ph];
+    cudaGraphConditionalHandle hi;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, pg, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hi;
+    ip.conditional.type = cudaGraphCondTypeWhile;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    CUDA_TRY(cudaGraphAddNode(&inode, pg, nullptr, nullptr, 0, &ip));
+    cudaGraph_t ib = ip.conditional.phGraph_out[0];
+    cudaGraphNode_t kn = nullptr;
+    for (int i = 0; i < chunk; ++i)
       for (const Launch& L : c->seq[ph]) {
         cudaGraphNode_t nn;
-        CUDA_TRY(add_kernel_node(&nn, pg, kn ? &kn : nullptr, L.fn, L.grid, kBlock, pa.args(L), L.smem));
+        CUDA_TRY(add_kernel_node(&nn, ib, kn ? &kn : nullptr, L.fn, L.grid, kBlock, pa.args(L), L.smem));
         kn = nn;
       }
-    }
-    prev = snode;
+    int phv = ph;
+    void* actl[3] = {&st, &hi, &phv};
+    cudaGraphNode_t cn;
+    CUDA_TRY(add_kernel_node(&cn, ib, kn ? &kn : nullptr, (const void*)k_chunk_ctl, 1, 1, actl));
   }
   void* actl[2] = {&st, &hw};
   cudaGraphNode_t cnode;
-  CUDA_TRY(add_kernel_node(&cnode, body, &prev, (const void*)k_loop_ctl, 1, 1, actl));
+  CUDA_TRY(add_kernel_node(&cnode, body, &snode, (const void*)k_loop_ctl, 1, 1, actl));
   CUDA_TRY(cudaGraphInstantiate(&c->gexec, c->graph, 0));
   c->graph_chunk = chunk;
   return AMPCG_OK;
@@ -862,8 +874,8 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   else k_init<0><<<gi, kBlock, 0, s>>>(A, B, c->st);
   CUDA_TRY(cudaGetLastError());
   long long launches = 1;  // k_init
-  int k_before = 0;
   int runs_before[6] = {0, 0, 0, 0, 0, 0};
+  int loops_before = 0;
   if (kt) {
     CUDA_TRY(cudaEventRecord(e_first, s));
     CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -884,18 +896,16 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
     CUDA_TRY(cudaStreamSynchronize(s));
     const DevState& h = *c->hst;
     if (!kt) {
-      // device loop: every body launches k_phase and k_loop_ctl; switch nodes
-      // launch their four kernels only for iterations that run (an iteration
-      // that stops on breakdown still launches its four)
-      long long it = h.k - k_before + (h.status == ST_OK || h.status == ST_NOT_CONVERGED ? 0 : 1);
-      long long bodies = it <= 0 ? 1 : (it + chunk - 1) / chunk;
-      launches += 2 * bodies;
+      // device loop: every outer body launches k_phase and k_loop_ctl, every
+      // inner chunk its pair's sequence `chunk` times and k_chunk_ctl (the
+      // launches that return at entry after a change or the stop included)
+      launches += 2LL * (h.loop_runs - loops_before);
+      loops_before = h.loop_runs;
       for (int ph = 0; ph < 6; ++ph) {
-        launches += (long long)c->seq[ph].size() * (h.phase_runs[ph] - runs_before[ph]);
-        runs_before[ph] = h.phase_runs[ph];
+        launches += ((long long)chunk * (long long)c->seq[ph].size() + 1) * (h.chunk_runs[ph] - runs_before[ph]);
+        runs_before[ph] = h.chunk_runs[ph];
       }
     }
-    k_before = h.k;
     // reading R9: verify, and replace r when the true residual misses tol
     bool refresh = h.status == ST_OK && h.refreshes < pol.verify_refresh && h.k < maxit &&
                    h.true_relres * h.nb > h.tol_nb;
@@ -1012,7 +1022,7 @@ extern "C" ampcg_status ampcg_precond_apply(ampcg_t c, int uz, int ur, double om
   B.z = z;
   if (c->mtype == M_CHEBYSHEV) {
     // the precondition part of the phase's launch sequence on the caller's r, z
-    ArgPack pa(c, 0, 0);
+    ArgPack pa(c);
     pa.B = B;
     for (const Launch& L : c->seq[2 * uz + ur]) {
       if (L.slot != 0) break;

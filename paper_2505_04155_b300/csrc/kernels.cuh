@@ -52,7 +52,10 @@ struct __align__(16) DevState {
   int first;           // no search direction yet
   int refreshes;
   int switch_iter[3];
-  int k_body;          // iteration counter seen by the previous loop-body end
+  int k_body;          // iteration counter seen by the previous outer-loop body end
+  int k_chunk;         // iteration counter seen by the previous inner-loop chunk end
+  int loop_runs;       // outer-loop bodies run (launch accounting)
+  int chunk_runs[6];   // inner-loop chunks run per pair 2 u_z + u_r
   // policy
   int criterion, u0, d, ell, scale, latch, fixed_uz, fixed_ur;
   double C, tau_zs, tau_zh, tol;
@@ -102,17 +105,14 @@ struct ArrayHist {
   __device__ __forceinline__ double operator()(int t) const { return d[t]; }
 };
 
-// Precision pair check at kernel entry: a variant launched for another pair
-// (which the dispatch never does) stops the solve with an internal error
-// instead of computing with the wrong types.  All blocks read the same state,
-// so all return together and no reduction ticket is taken.
-__device__ __forceinline__ bool phase_mismatch(DevState* st, int uz, int ur) {
-  if (st->uz == uz && (ur < 0 || st->ur == ur)) return false;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->status = ST_INTERNAL;
-    st->done = 1;
-  }
-  return true;
+// Precision pair check at kernel entry.  The loop graph repeats one pair's
+// launch sequence `chunk` times; after the selector changes the pair inside a
+// chunk, the rest of that chunk's launches find another pair here and do
+// nothing (every kernel of an iteration checks the same pair, which only the
+// update kernel's last block changes).  All blocks read the same state, so
+// all return together and no reduction ticket is taken.
+__device__ __forceinline__ bool phase_mismatch(const DevState* st, int uz, int ur) {
+  return st->uz != uz || st->ur != ur;
 }
 
 // Matrix in sliced-ELL form: rows are grouped 32 per slice (one warp); the
@@ -791,10 +791,10 @@ __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevSta
   }
 }
 
-template <int UZ>
+template <int UZ, int UR>
 __global__ void __launch_bounds__(256) k_axpy(Bufs B, int64_t n, DevState* st) {
   if (st->done) return;
-  if (phase_mismatch(st, UZ, -1)) return;
+  if (phase_mismatch(st, UZ, UR)) return;
   axpy_rows<UZ, 8>(B, n, st);
 }
 
@@ -1162,11 +1162,8 @@ __device__ __forceinline__ double update_step(DevState* s, double rr, unsigned l
   return d;
 }
 
-// h_next / has_next: the SWITCH handle of the next iteration in the loop
-// graph, set here to the phase the selector chose (or AMPCG_PHASE_NONE).
 template <int UZ, int UR>
-__global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st,
-                                                cudaGraphConditionalHandle h_next, int has_next) {
+__global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st) {
   if (st->done) return;
   if (phase_mismatch(st, UZ, UR)) return;
   double rr = 0.0;
@@ -1192,30 +1189,43 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st,
   unsigned long long m = final_sum_max<1>(B.part, 1, B.pmax, gridDim.x, tot);
   double d = 0.0;
   int k1 = 0;
-  unsigned next = AMPCG_PHASE_NONE;
   if (threadIdx.x == 0) {
     S.ticket[2] = 0u;
     d = update_step(&S, tot[0], m);
     k1 = S.k;
-    if (!S.done) next = 2 * S.uz + S.ur;
   }
   state_store(st, &S);
-  if (threadIdx.x == 0) {
-    S.delta_hist[k1] = d;
-    if (has_next) cudaGraphSetConditional(h_next, next);
-  }
+  if (threadIdx.x == 0) S.delta_hist[k1] = d;
 }
 
-// Sets the SWITCH value of the first iteration of a loop-graph body.
+// Loop graph control (one thread each).  The outer loop picks the precision
+// pair's body with a SWITCH; the body repeats chunks of that pair's
+// iterations in an inner loop while the pair stays current, so a SWITCH is
+// evaluated once per precision change rather than once per iteration.
+
+// Sets the SWITCH value of an outer-loop body: the current pair 2 u_z + u_r.
 __global__ void k_phase(DevState* st, cudaGraphConditionalHandle h) {
   cudaGraphSetConditional(h, st->done ? AMPCG_PHASE_NONE : 2 * st->uz + st->ur);
 }
 
-// Sets the while-loop condition of the device-side iteration loop.  A body
-// that ends without the iteration counter having advanced (which the
-// dispatch never produces) stops the solve with an internal error, so the
-// loop always ends within maxit bodies.
+// End of an inner-loop chunk of pair ph: continue while the solve runs and
+// the pair is still ph.  A chunk that ends without the iteration counter
+// having advanced (which the dispatch never produces: the SWITCH chose ph
+// from the same state) stops the solve with an internal error, so the inner
+// loop ends within maxit chunks.
+__global__ void k_chunk_ctl(DevState* st, cudaGraphConditionalHandle h, int ph) {
+  st->chunk_runs[ph] += 1;
+  if (!st->done && st->k == st->k_chunk) {
+    st->status = ST_INTERNAL;
+    st->done = 1;
+  }
+  st->k_chunk = st->k;
+  cudaGraphSetConditional(h, (!st->done && 2 * st->uz + st->ur == ph) ? 1u : 0u);
+}
+
+// Sets the condition of the outer loop; the same progress check per body.
 __global__ void k_loop_ctl(DevState* st, cudaGraphConditionalHandle h) {
+  st->loop_runs += 1;
   if (!st->done && st->k == st->k_body) {
     st->status = ST_INTERNAL;
     st->done = 1;
@@ -1732,12 +1742,12 @@ __device__ __forceinline__ float row_sum_packed16(const unsigned* __restrict__ a
   return acc;
 }
 
-template <int UZ, int IT>
+template <int UZ, int UR, int IT>
 __global__ void __launch_bounds__(256) k_cheb_step(Sell A, Cheb C, DevState* st, int j, double c1,
                                                    double c2) {
   using TZ = typename Store<UZ>::T;
   if (st->done) return;
-  if (phase_mismatch(st, UZ, -1)) return;
+  if (phase_mismatch(st, UZ, UR)) return;
   const TZ* __restrict__ dp = (const TZ*)(((j - 1) & 1) ? C.d[1] : C.d[0]);
   TZ* dn = (TZ*)((j & 1) ? C.d[1] : C.d[0]);
   TZ* res = (TZ*)C.res;

@@ -135,6 +135,44 @@ def test_repeated_solves_are_deterministic():
         assert torch.equal(x, outs[0][0])
 
 
+@pytest.mark.parametrize("kind", ["amp16", "amp64_window", "cheb"])
+def test_loop_graph_equals_kernel_by_kernel(kind):
+    # the loop graph (SWITCH per precision change, inner loop of chunks) runs
+    # the same kernels in the same order as the host-driven launches, for any
+    # chunk length, including chunks that straddle a precision change or the stop
+    a = W.diffusion3d(20, 2.0, 6)
+    b = torch.as_tensor(W.rhs_uniform(a.n, 8), device="cuda")
+    kw = dict(precond=P.M_CHEBYSHEV, degree=4) if kind == "cheb" else {}
+    s = P.Solver(a.rowptr, a.col, a.val, **kw)
+    pol = (P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3) if kind == "amp64_window"
+           else P.Policy(verify_refresh=3))
+    x0, i0 = s.solve(b, tol=TOL, maxit=5000, policy=pol, timed=True)
+    assert i0.converged and (kind == "cheb" or any(k >= 0 for k in i0.switch_iter))
+    for chunk in (1, 3, 16, 64):
+        pol.graph_chunk = chunk
+        x1, i1 = s.solve(b, tol=TOL, maxit=5000, policy=pol)
+        assert i1.iters == i0.iters and i1.refreshes == i0.refreshes
+        assert list(i1.switch_iter) == list(i0.switch_iter)
+        assert np.array_equal(i1.prec_hist, i0.prec_hist)
+        assert torch.equal(x1, x0)
+    s.close()
+
+
+def test_loop_graph_launch_count():
+    # one precision pair, no replacement: k_init, one outer body (k_phase,
+    # k_loop_ctl), ceil(iters / chunk) chunks of chunk x 4 launches plus
+    # k_chunk_ctl, and the true residual
+    a = W.diffusion3d(16, 1.0, 3)
+    b = torch.as_tensor(W.rhs_uniform(a.n, 2), device="cuda")
+    s = P.Solver(a.rowptr, a.col, a.val)
+    for chunk in (1, 7, 16):
+        pol = P.Policy.pcg64(graph_chunk=chunk)
+        _, info = s.solve(b, tol=TOL, maxit=5000, policy=pol)
+        chunks = -(-info.iters // chunk)
+        assert info.kernel_launches == 1 + 2 + chunks * (4 * chunk + 1) + 1
+    s.close()
+
+
 def test_warm_start_and_zero_rhs():
     a = W.poisson2d(32)
     b = W.rhs_uniform(a.n, 5)
