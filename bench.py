@@ -138,8 +138,9 @@ def alg_bytes(kernel: str, phase: str, n: int, nnz: int, nslices: int, idx_bytes
     once, in the storage precision the iteration uses)."""
     sz = {"64": 8, "32": 4, "16": 2}
     zb, rb = sz[phase[2:4]], sz[phase[7:9]]
-    if kernel == "precond_rho":
-        return n * (rb + 2 * zb)
+    if kernel == "precond":
+        # Jacobi: r, D^-1, p_{k-1} read, p_k written (z_k stays in registers)
+        return n * (rb + 3 * zb)
     if kernel == "search_dir":
         return n * 3 * zb
     if kernel == "spmv_gamma":

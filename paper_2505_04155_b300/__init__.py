@@ -60,7 +60,10 @@ class KernelTimesC(C.Structure):
     _fields_ = [("ms", (C.c_double * 6) * 4), ("launches", (C.c_int * 6) * 4), ("total_ms", C.c_double)]
 
 
-KERNEL_NAMES = ("precond_rho", "search_dir", "spmv_gamma", "update_norm")
+# event-timed slots of an iteration: the precondition step (with Jacobi or no
+# preconditioner also rho, beta and the search direction, one cooperative
+# kernel), the search direction (Chebyshev only), SpMV + gamma, update + norm
+KERNEL_NAMES = ("precond", "search_dir", "spmv_gamma", "update_norm")
 
 
 def phase_name(phase: int) -> str:

@@ -74,11 +74,13 @@ ampcg_status dalloc(T** p, size_t count) {
 // One kernel launch of an iteration: function, launch shape, argument list
 // kind, timing slot (0 precondition, 1 search direction, 2 SpMV, 3 update)
 // and, for a Chebyshev step, its index and constants.
-enum { KA_ELEM = 0, KA_SPMV, KA_UPD, KA_CINIT, KA_CSTEP, KA_CFINAL };
+enum { KA_ELEM = 0, KA_SPMV, KA_UPD, KA_CINIT, KA_CSTEP, KA_CFINAL, KA_LOOP };
 struct Launch {
   const void* fn;
   int grid, smem, kind, slot, j;
   double c1, c2;
+  bool coop;   // cooperative launch (the kernel has a grid barrier)
+  int block = kBlock;
 };
 
 struct ampcg_ctx {
@@ -107,6 +109,7 @@ struct ampcg_ctx {
   void *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
   double* part = nullptr;
   unsigned long long* pmax = nullptr;
+  GridSumBarrier* bar = nullptr;  // barriers of the cooperative launches (k_precond_dir, k_loop; one per pair), zeroed per solve
   DevState* st = nullptr;       // device
   DevState* hst = nullptr;      // pinned host mirror
   double* dhist = nullptr;      // delta history
@@ -116,6 +119,11 @@ struct ampcg_ctx {
   int g_elem = 1, g_rows = 1, g_max = 1;
   // iteration kernels per phase (2 u_z + u_r), in launch order
   std::vector<Launch> seq[6];
+  // k_loop per precision pair (Jacobi or none, slices at most kStageW wide):
+  // the device loop and the timed path launch it instead of seq
+  Launch loop[6];
+  bool loop_ok = true;    // every pair's k_loop configured (set while building)
+  bool use_loop = false;
   // Chebyshev preconditioner data (reading R8)
   int cheb_m = 0;
   int cheb_auto = 0;            // interval from the Gershgorin bound
@@ -171,6 +179,7 @@ struct ampcg_ctx {
     B.dinv16 = dinv16;
     B.part = part;
     B.pmax = pmax;
+    B.bar = bar;
     return B;
   }
 };
@@ -182,7 +191,7 @@ static void release(ampcg_ctx* c) {
   void* ptrs[] = {c->ah64, c->ah32, c->ah16, c->ahp, c->ds64, c->ds32, c->ds16, c->cres, c->cd0, c->cd1, c->cu,
                   c->rowptr, c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
                   c->dinv16, c->x, c->b, c->r64, c->t, c->r32, c->z, c->p0, c->p1, c->q,
-                  c->part, c->pmax, c->st, c->dhist, c->phist};
+                  c->part, c->pmax, c->bar, c->st, c->dhist, c->phist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hst) cudaFreeHost(c->hst);
@@ -191,15 +200,15 @@ static void release(ampcg_ctx* c) {
   delete c;
 }
 
-static int occ_grid(const void* kern, int sms, int64_t work_threads, int smem = 0) {
+static int occ_grid(const void* kern, int sms, int64_t work_threads, int smem = 0, int block = kBlock) {
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem) != cudaSuccess) {
     cudaGetLastError();
     per_sm = 4;
   }
   if (per_sm < 1) per_sm = 1;
   int64_t g = (int64_t)sms * per_sm;
-  int64_t need = (work_threads + kBlock - 1) / kBlock;
+  int64_t need = (work_threads + block - 1) / block;
   if (need < 1) need = 1;
   return (int)(g < need ? g : need);
 }
@@ -407,13 +416,16 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   c->g_rows = occ_grid(c->idx16 ? (const void*)k_true_residual<1> : (const void*)k_true_residual<0>, sms,
                        rows_pad);
   c->g_max = c->g_elem > c->g_rows ? c->g_elem : c->g_rows;
-  for (int ph = 0; ph < 6; ++ph)
+  for (int ph = 0; ph < 6; ++ph) {
     for (const Launch& L : c->seq[ph])
       if (L.grid > c->g_max) c->g_max = L.grid;
+    if (c->use_loop && c->loop[ph].grid > c->g_max) c->g_max = c->loop[ph].grid;
+  }
   int gi = occ_grid((const void*)k_init<0>, sms, rows_pad);
   if (gi > c->g_max) c->g_max = gi;
   TRY(dalloc(&c->part, (size_t)c->g_max * 4));
-  TRY(dalloc(&c->pmax, (size_t)c->g_max));
+  TRY(dalloc(&c->pmax, (size_t)c->g_max * 2));   // two halves for the grid barriers
+  TRY(dalloc(&c->bar, 12));
   TRY(dalloc(&c->st, 1));
   CTRY(cudaMallocHost((void**)&c->hst, sizeof(DevState)));
   memset(c->hst, 0, sizeof(DevState));
@@ -509,7 +521,7 @@ static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
   auto add = [&](const void* fn, int kind, int slot, int64_t work, int smem, int j = 0, double c1 = 0,
                  double c2 = 0) {
     Launch L;
-    L.fn = fn; L.kind = kind; L.slot = slot; L.j = j; L.c1 = c1; L.c2 = c2; L.smem = smem;
+    L.fn = fn; L.kind = kind; L.slot = slot; L.j = j; L.c1 = c1; L.c2 = c2; L.smem = smem; L.coop = false;
     if (smem > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     L.grid = occ_grid(fn, sms, work, smem);
     v.push_back(L);
@@ -521,10 +533,13 @@ static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
       add((const void*)k_cheb_step<UZ, UR, IT>, KA_CSTEP, 0, c->nslices * 32, 0, j, c->cheb_c1[j - 1],
           c->cheb_c2[j - 1]);
     add((const void*)k_cheb_final<UZ, UR>, KA_CFINAL, 0, n, 0);
+    add((const void*)k_axpy<UZ, UR>, KA_ELEM, 1, nvec, 0);
   } else {
-    add((const void*)k_precond<UZ, UR, MT>, KA_ELEM, 0, nvec, 0);
+    // precondition, rho, beta and the search direction in one cooperative
+    // launch (its grid is at most the resident blocks: occ_grid)
+    add((const void*)k_precond_dir<UZ, UR, MT>, KA_ELEM, 0, nvec, 0);
+    v.back().coop = true;
   }
-  add((const void*)k_axpy<UZ, UR>, KA_ELEM, 1, nvec, 0);
   const bool wide = c->maxw > kStageW;
   const int sm = wide ? 0 : staged_smem_bytes<UR, IT>();
   add(wide ? (const void*)k_spmv<UZ, UR, IT, true> : (const void*)k_spmv<UZ, UR, IT, false>, KA_SPMV, 2,
@@ -535,16 +550,42 @@ static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
     if (v.back().grid < need) v.back().grid = need;
   }
   add((const void*)k_update<UZ, UR>, KA_UPD, 3, nvec, 0);
+  if constexpr (MT != M_CHEBYSHEV) {
+    if (!wide) {
+      // the whole iteration loop in one cooperative launch, one block of
+      // kLoopBlock threads per SM (a context whose pairs cannot all be
+      // configured keeps the kernel sequences)
+      const void* fn = (const void*)k_loop<UZ, UR, MT, IT>;
+      const int lsm = LoopStageCfg<UR, IT>::kBytes;
+      int per_sm = 0;
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLoopBlock, lsm) != cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        c->loop_ok = false;
+      } else {
+        Launch L;
+        L.fn = fn; L.kind = KA_LOOP; L.slot = 0; L.j = 0; L.c1 = 0; L.c2 = 0; L.smem = lsm; L.coop = true;
+        L.block = kLoopBlock;
+        L.grid = occ_grid(fn, sms, c->nslices * 32, lsm, kLoopBlock);
+        c->loop[2 * UZ + UR] = L;
+      }
+    } else {
+      c->loop_ok = false;
+    }
+  }
 }
 
 template <int MT, int IT>
 static void build_sequences_t(ampcg_ctx* c, int sms) {
+  c->loop_ok = MT != M_CHEBYSHEV;
   phase_seq<MT, IT, P64, P64>(c, sms, c->seq[0]);
   phase_seq<MT, IT, P64, P32>(c, sms, c->seq[1]);
   phase_seq<MT, IT, P32, P64>(c, sms, c->seq[2]);
   phase_seq<MT, IT, P32, P32>(c, sms, c->seq[3]);
   phase_seq<MT, IT, P16, P64>(c, sms, c->seq[4]);
   phase_seq<MT, IT, P16, P32>(c, sms, c->seq[5]);
+  c->use_loop = c->loop_ok;
 }
 
 static ampcg_status build_sequences(ampcg_ctx* c, int sms) {
@@ -613,16 +654,17 @@ struct ArgPack {
   Cheb C;
   int64_t n;
   DevState* st;
-  int j;
+  int j, iters;
   double c1, c2;
   void* a[8];
-  explicit ArgPack(const ampcg_ctx* c)
-      : B(c->bufs()), A(c->sell()), C(c->cheb()), n(c->n), st(c->st), j(0), c1(0), c2(0) {}
+  explicit ArgPack(const ampcg_ctx* c, int it = 1)
+      : B(c->bufs()), A(c->sell()), C(c->cheb()), n(c->n), st(c->st), j(0), iters(it), c1(0), c2(0) {}
   void** args(const Launch& L) {
     switch (L.kind) {
       case KA_ELEM:
       case KA_UPD: a[0] = &B; a[1] = &n; a[2] = &st; break;
       case KA_SPMV: a[0] = &A; a[1] = &B; a[2] = &st; break;
+      case KA_LOOP: a[0] = &A; a[1] = &B; a[2] = &n; a[3] = &st; a[4] = &iters; break;
       case KA_CINIT:
       case KA_CFINAL: a[0] = &B; a[1] = &C; a[2] = &n; a[3] = &st; break;
       case KA_CSTEP:
@@ -637,15 +679,24 @@ struct ArgPack {
 // One iteration of phase ph launched kernel by kernel on stream s; with ev,
 // ev[slot] is recorded before the first kernel of each slot and ev[4] after
 // the last kernel.
+// The launches of one iteration of phase ph: k_loop (one iteration) where it
+// applies, else the phase's kernel sequence.
+static std::vector<Launch> iteration_launches(const ampcg_ctx* c, int ph) {
+  if (c->use_loop) return {c->loop[ph]};
+  return c->seq[ph];
+}
+
 static cudaError_t launch_phase(ampcg_ctx* c, int ph, cudaStream_t s, cudaEvent_t* ev) {
-  ArgPack pa(c);
+  ArgPack pa(c, 1);
   int slot = -1;
-  for (const Launch& L : c->seq[ph]) {
+  for (const Launch& L : iteration_launches(c, ph)) {
     while (ev && slot < L.slot) {   // slots without a kernel in this phase get an empty interval
       cudaError_t e = cudaEventRecord(ev[++slot], s);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaLaunchKernel(L.fn, dim3(L.grid), dim3(kBlock), pa.args(L), (size_t)L.smem, s);
+    cudaError_t e = L.coop ? cudaLaunchCooperativeKernel(L.fn, dim3(L.grid), dim3(L.block), pa.args(L),
+                                                         (size_t)L.smem, s)
+                           : cudaLaunchKernel(L.fn, dim3(L.grid), dim3(L.block), pa.args(L), (size_t)L.smem, s);
     if (e != cudaSuccess) return e;
   }
   while (ev && slot < 4) {
@@ -720,10 +771,19 @@ static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
     CUDA_TRY(cudaGraphAddNode(&inode, pg, nullptr, nullptr, 0, &ip));
     cudaGraph_t ib = ip.conditional.phGraph_out[0];
     cudaGraphNode_t kn = nullptr;
-    for (int i = 0; i < chunk; ++i)
-      for (const Launch& L : c->seq[ph]) {
+    // k_loop runs the whole chunk in one launch
+    const std::vector<Launch> seq = iteration_launches(c, ph);
+    pa.iters = chunk;
+    for (int i = 0; i < (c->use_loop ? 1 : chunk); ++i)
+      for (const Launch& L : seq) {
         cudaGraphNode_t nn;
-        CUDA_TRY(add_kernel_node(&nn, ib, kn ? &kn : nullptr, L.fn, L.grid, kBlock, pa.args(L), L.smem));
+        CUDA_TRY(add_kernel_node(&nn, ib, kn ? &kn : nullptr, L.fn, L.grid, L.block, pa.args(L), L.smem));
+        if (L.coop) {
+          cudaLaunchAttributeValue av;
+          memset(&av, 0, sizeof(av));
+          av.cooperative = 1;
+          CUDA_TRY(cudaGraphKernelNodeSetAttribute(nn, cudaLaunchAttributeCooperative, &av));
+        }
         kn = nn;
       }
     int phv = ph;
@@ -788,13 +848,14 @@ static ampcg_status timed_loop(ampcg_ctx* c, ampcg_kernel_times* kt, cudaEvent_t
     int ph = 2 * c->hst->uz + c->hst->ur;
     if (ph < 0 || ph > 5) return fail(AMPCG_ERR_CUDA, "invalid phase %d in device state", ph);
     CUDA_TRY(launch_phase(c, ph, s, ev));
-    launches += (long long)c->seq[ph].size();
+    const std::vector<Launch> seq = iteration_launches(c, ph);
+    launches += (long long)seq.size();
     CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (c->hst->k > k0) {
       for (int j = 0; j < 4; ++j) {
         bool has = false;
-        for (const Launch& L : c->seq[ph]) has = has || L.slot == j;
+        for (const Launch& L : seq) has = has || L.slot == j;
         if (!has) continue;
         float ms = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&ms, ev[j], ev[j + 1]));
@@ -846,6 +907,7 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   CUDA_TRY(cudaMemcpyAsync(c->x, x, vb, x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   init_state(c->hst, &pol, tol, maxit, c);
   CUDA_TRY(cudaMemcpyAsync(c->st, c->hst, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(c->bar, 0, 12 * sizeof(GridSumBarrier), s));
   if (!kt) {
     hs = ensure_graph(c, chunk);
     if (hs != AMPCG_OK) return hs;
@@ -902,7 +964,8 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
       launches += 2LL * (h.loop_runs - loops_before);
       loops_before = h.loop_runs;
       for (int ph = 0; ph < 6; ++ph) {
-        launches += ((long long)chunk * (long long)c->seq[ph].size() + 1) * (h.chunk_runs[ph] - runs_before[ph]);
+        const long long per_chunk = c->use_loop ? 1 : (long long)chunk * (long long)c->seq[ph].size();
+        launches += (per_chunk + 1) * (h.chunk_runs[ph] - runs_before[ph]);
         runs_before[ph] = h.chunk_runs[ph];
       }
     }

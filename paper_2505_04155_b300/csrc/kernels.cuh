@@ -1,21 +1,24 @@
 // kernels.cuh -- AMP-PCG (Algorithm 3 of Guo, de Sturler, Warburton) on one
-// B300.  One iteration is four bandwidth-bound launches; each grid reduction
-// is single-pass (last-block ticket) and the last block also performs the
-// scalar work of the algorithm, so no host synchronisation happens inside the
-// loop:
-//   k_precond : Alg. 3 scaling and preconditioning: y = omega r (u_r),
-//               z = M^-1 y (u_z), rho; last block: beta
-//   k_axpy    : Alg. 3 search direction: p = z + beta p (u_z)
-//   k_spmv    : Alg. 3 matrix product: q = A p (u_r), gamma; last block: alpha
-//   k_update  : Alg. 3 updates: x += alpha p (FP64), r -= alpha q (u_r),
-//                                   ||r||, max|r|; last block: stopping test
-//                                   (Alg. 3), indicator and selector for the
-//                                   next iteration (Alg. 3), omega.
-// Each kernel is specialised for one precision pair (u_z, u_r) (phase index
-// 2 u_z + u_r), so every variant gets its own register allocation.  The pair
-// of an iteration is decided on the device (last block of k_update / k_init)
-// and selects the variant through a conditional SWITCH node of the loop graph
-// (or through the host, in the launch-by-launch timing mode).
+// B300.  The row loops of each step of Alg. 3 are device functions shared by
+// three drivers:
+//   k_loop (Jacobi or no preconditioner, slices at most kStageW wide): the
+//     iteration loop of one precision pair in one cooperative launch; grid
+//     barriers (with the grid sums) separate the steps.
+//   the kernel sequence (Chebyshev preconditioner, wide slices, and the
+//     launch-by-launch mode): the precondition step (k_precond_dir, or the
+//     Chebyshev kernels then k_axpy), k_spmv and k_update; each grid reduction
+//     is single-pass (last-block ticket) and its last block runs the scalar
+//     step of the algorithm.
+//   k_batched (batched.cuh): one block per system.
+// The steps: scaling and preconditioning y = omega r (u_r), z = M^-1 y (u_z),
+// rho and beta; search direction p = z + beta p (u_z); q = A p (u_r), gamma
+// and alpha; x += alpha p (FP64), r -= alpha q (u_r), ||r||, max|r|, the
+// stopping test, indicator and selector for the next iteration, omega.  No
+// host synchronisation happens inside the loop.  Each kernel is specialised
+// for one precision pair (u_z, u_r) (phase index 2 u_z + u_r), so every
+// variant gets its own register allocation; the pair of an iteration is
+// decided on the device and selects the variant through a conditional SWITCH
+// node of the loop graph (or through the host, in the launch-by-launch mode).
 #pragma once
 #include <type_traits>
 #include "device_util.cuh"
@@ -113,6 +116,17 @@ struct ArrayHist {
 // all return together and no reduction ticket is taken.
 __device__ __forceinline__ bool phase_mismatch(const DevState* st, int uz, int ur) {
   return st->uz != uz || st->ur != ur;
+}
+
+// Entry of an iteration kernel: the block copies the state to shared memory
+// in one round of loads (instead of a chain of dependent reads: the done
+// flag, then the precision pair, then the scalars and buffer choices), and
+// every thread reads its fields there.  False: the solve is done or the
+// precision pair is not (uz, ur).
+__device__ __forceinline__ bool state_enter(DevState* S, const DevState* st, int uz, int ur) {
+  state_load(S, st);
+  __syncthreads();
+  return !S->done && !phase_mismatch(S, uz, ur);
 }
 
 // Matrix in sliced-ELL form: rows are grouped 32 per slice (one warp); the
@@ -509,6 +523,7 @@ struct Bufs {
   const __half* dinv16;
   double* part;            // per-block partial sums [G * 4]
   unsigned long long* pmax; // per-block partial maxima [G]
+  GridSumBarrier* bar;      // barriers of the cooperative launches, one per precision pair [6]
 };
 
 // Alg. 3 on the state copy: rho_k, its checks (reading R12) and
@@ -617,79 +632,93 @@ __global__ void __launch_bounds__(256) k_init(Sell A, Bufs B, DevState* st) {
 // more loop trips per thread let warps drift apart, so loads of one overlap
 // the FP64 work of another).
 
-// Alg. 3 scaling, preconditioning and rho_k (+ the storage conversions of
-// reading R10 and of the search direction).
+// Alg. 3 scaling and preconditioning of V consecutive elements starting at
+// i0 (m of them in range), and their rho_k terms: r_k is read in u_r
+// (converted once when u_r changed, reading R10), y_k = omega_k r_k is
+// computed in u_r and stored in u_z (reading R6), z_k = M^-1 y_k in u_z
+// (Jacobi: one rounding of dinv_i * y_i).  rho_k = r_k^T z_k: binary32
+// compensated products when neither operand is binary64 (r scaled by the
+// exact power of two sig_f; the block total is unscaled), else one FP64 fma
+// per term.
+struct PrecondScalars {
+  int r_cast, pow2, oe;
+  bool om_one;
+  double om;
+  float omf, sigf;
+  __device__ __forceinline__ explicit PrecondScalars(const DevState* st)
+      : r_cast(st->r_cast), pow2(st->omega_pow2), oe(st->omega_e),
+        om_one(st->omega_pow2 && st->omega_e == 0), om(st->omega), omf(st->omega_f), sigf(st->sig_f) {}
+};
+
+template <int UZ, int UR, int MT, int V, class Part>
+__device__ __forceinline__ void precond_vec(const Bufs& B, const PrecondScalars& c, int64_t i0, int m,
+                                            typename Store<UZ>::T (&zz)[V], double& rho, Dot2& d2) {
+  using TZ = typename Store<UZ>::T;
+  using TR = typename Store<UR>::T;
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+  alignas(16) TR r[V];
+  if constexpr (UR == P64) {
+    if (c.r_cast) {
+      alignas(16) float t[V];
+      Part::template vldo<V>(B.r32 + i0, t);
+#pragma unroll
+      for (int j = 0; j < V; ++j) r[j] = f2d(t[j]);
+      vst<V>(B.r64 + i0, r, m);
+    } else {
+      Part::template vldo<V>(B.r64 + i0, r);
+    }
+  } else {
+    if (c.r_cast) {
+      alignas(16) double t[V];
+      Part::template vldo<V>(B.r64 + i0, t);
+#pragma unroll
+      for (int j = 0; j < V; ++j) r[j] = __double2float_rn(t[j]);
+      vst<V>(B.r32 + i0, r, m);
+    } else {
+      Part::template vldo<V>(B.r32 + i0, r);
+    }
+  }
+  alignas(16) TZ dv[V];
+  if constexpr (MT != M_NONE) {
+    if constexpr (UZ == P64) vldg<V>(B.dinv64 + i0, dv);
+    else if constexpr (UZ == P32) vldg<V>(B.dinv32 + i0, dv);
+    else vldg<V>(B.dinv16 + i0, dv);
+  }
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    TZ y;
+    if constexpr (UR == P64) {
+      if constexpr (UZ == P16) y = c.pow2 ? d2h_scaled(r[j], c.oe) : d2h(__dmul_rn(c.om, r[j]));
+      else y = round_from_f64<UZ>(c.om_one ? r[j] : __dmul_rn(c.om, r[j]));
+    } else {
+      y = round_from_f32<UZ>(__fmul_rn(c.omf, r[j]));
+    }
+    if constexpr (MT == M_NONE) zz[j] = y;
+    else if constexpr (UZ == P64) zz[j] = __dmul_rn(dv[j], y);
+    else if constexpr (UZ == P32) zz[j] = __fmul_rn(dv[j], y);
+    else zz[j] = __float2half_rn(__fmul_rn(h2f(dv[j]), h2f(y)));
+    if (j < m) {
+      if constexpr (kSmall) d2.add(__fmul_rn((float)r[j], c.sigf), (float)zz[j]);
+      else rho = fma(to_f64(r[j]), to_f64(zz[j]), rho);
+    }
+  }
+}
+
+// Alg. 3 scaling, preconditioning and rho_k over the thread's vectors; z_k
+// goes to its buffer.
 template <int UZ, int UR, int MT, int V, class Part = GridPart>
 __device__ __forceinline__ void precond_rows(const Bufs& B, int64_t n, const DevState* st,
                                              double& rho, Dot2& d2) {
   using TZ = typename Store<UZ>::T;
-  using TR = typename Store<UR>::T;
   TZ* __restrict__ z = (TZ*)B.z;
-  const int r_cast = st->r_cast;
-  const double om = st->omega;
-  const float omf = st->omega_f;
-  const int pow2 = st->omega_pow2, oe = st->omega_e;
-  const bool om_one = pow2 && oe == 0;
-  // rho: binary32 compensated products when neither operand is binary64
-  // (r scaled by the exact power of two sig_f; the block total is unscaled)
-  constexpr bool kSmall = (UR != P64) && (UZ != P64);
-  const float sigf = st->sig_f;
+  const PrecondScalars c(st);
   const int64_t nv = (n + V - 1) / V;
   const int64_t stride = Part::count();
   for (int64_t v = Part::first(); v < nv; v += stride) {
     const int64_t i0 = v * V;
     const int m = (n - i0 < V) ? (int)(n - i0) : V;
-    // r_k in u_r (converted once when u_r changed, reading R10)
-    alignas(16) TR r[V];
-    if constexpr (UR == P64) {
-      if (r_cast) {
-        alignas(16) float t[V];
-        Part::template vldo<V>(B.r32 + i0, t);
-#pragma unroll
-        for (int j = 0; j < V; ++j) r[j] = f2d(t[j]);
-        vst<V>(B.r64 + i0, r, m);
-      } else {
-        Part::template vldo<V>(B.r64 + i0, r);
-      }
-    } else {
-      if (r_cast) {
-        alignas(16) double t[V];
-        Part::template vldo<V>(B.r64 + i0, t);
-#pragma unroll
-        for (int j = 0; j < V; ++j) r[j] = __double2float_rn(t[j]);
-        vst<V>(B.r32 + i0, r, m);
-      } else {
-        Part::template vldo<V>(B.r32 + i0, r);
-      }
-    }
-    // y_k = omega_k r_k computed in u_r, stored in u_z (reading R6), then
-    // z_k = M^-1 y_k in u_z (Jacobi: one rounding of dinv_i * y_i)
     alignas(16) TZ zz[V];
-    alignas(16) TZ dv[V];
-    if constexpr (MT != M_NONE) {
-      if constexpr (UZ == P64) vldg<V>(B.dinv64 + i0, dv);
-      else if constexpr (UZ == P32) vldg<V>(B.dinv32 + i0, dv);
-      else vldg<V>(B.dinv16 + i0, dv);
-    }
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      TZ y;
-      if constexpr (UR == P64) {
-        if constexpr (UZ == P16) y = pow2 ? d2h_scaled(r[j], oe) : d2h(__dmul_rn(om, r[j]));
-        else y = round_from_f64<UZ>(om_one ? r[j] : __dmul_rn(om, r[j]));
-      } else {
-        y = round_from_f32<UZ>(__fmul_rn(omf, r[j]));
-      }
-      if constexpr (MT == M_NONE) zz[j] = y;
-      else if constexpr (UZ == P64) zz[j] = __dmul_rn(dv[j], y);
-      else if constexpr (UZ == P32) zz[j] = __fmul_rn(dv[j], y);
-      else zz[j] = __float2half_rn(__fmul_rn(h2f(dv[j]), h2f(y)));
-      // rho_k = r_k^T z_k accumulated to FP64 accuracy
-      if (j < m) {
-        if constexpr (kSmall) d2.add(__fmul_rn((float)r[j], sigf), (float)zz[j]);
-        else rho = fma(to_f64(r[j]), to_f64(zz[j]), rho);
-      }
-    }
+    precond_vec<UZ, UR, MT, V, Part>(B, c, i0, m, zz, rho, d2);
     vst<V>(z + i0, zz, m);
   }
 }
@@ -720,33 +749,6 @@ __device__ __forceinline__ void precond_and_cast(const Bufs& B, int64_t n, const
   if (st->p_cast) cast_p<UZ, Part>(B, n, st);
 }
 
-template <int UZ, int UR, int MT>
-__global__ void __launch_bounds__(256) k_precond(Bufs B, int64_t n, DevState* st) {
-  if (st->done) return;
-  if (phase_mismatch(st, UZ, UR)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->phase_runs[2 * UZ + UR] += 1;
-  double rho = 0.0;
-  Dot2 d2;
-  precond_and_cast<UZ, UR, MT, 4>(B, n, st, rho, d2);
-  double v[1];
-  if constexpr ((UR != P64) && (UZ != P64)) {
-    v[0] = block_sum_dot2(d2, st->inv_sig);
-  } else {
-    v[0] = rho;
-    block_sum<1>(v);
-  }
-  if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
-  if (!last_block(&st->ticket[0])) return;
-  __shared__ DevState S;
-  state_load(&S, st);
-  double tot[1];
-  final_sum<1>(B.part, gridDim.x, 1, tot);
-  if (threadIdx.x == 0) {
-    S.ticket[0] = 0u;
-    rho_step(&S, tot[0]);
-  }
-  state_store(st, &S);
-}
 
 // ---------------------------------------------------------------------------
 // Alg. 3 search direction: p_k = z_k + beta_{k-1} p_{k-1} in u_z (p_0 = z_0).
@@ -793,9 +795,112 @@ __device__ __forceinline__ void axpy_rows(const Bufs& B, int64_t n, const DevSta
 
 template <int UZ, int UR>
 __global__ void __launch_bounds__(256) k_axpy(Bufs B, int64_t n, DevState* st) {
-  if (st->done) return;
-  if (phase_mismatch(st, UZ, UR)) return;
-  axpy_rows<UZ, 8>(B, n, st);
+  __shared__ DevState S;
+  if (!state_enter(&S, st, UZ, UR)) return;
+  axpy_rows<UZ, 8>(B, n, &S);
+}
+
+// Scaling, preconditioning, rho_k, beta_{k-1} and the search direction in one
+// cooperative launch (Jacobi or no preconditioner).  The blocks meet once, at
+// a grid barrier between rho_k's partial sums and the direction update; then
+// every block sums the partials in the same fixed order and runs the same
+// scalar step on its copy of the state, so all hold the same beta_{k-1}, and
+// block 0 writes the state back.  z_k of the first kZreg vectors of a thread
+// stays in registers between the two halves (it is read nowhere else); the
+// buffer carries any further ones.
+constexpr int kZreg = 2;
+template <int UZ, int UR, int MT>
+__global__ void __launch_bounds__(256) k_precond_dir(Bufs B, int64_t n, DevState* st) {
+  using TZ = typename Store<UZ>::T;
+  constexpr int V = 4;
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+  __shared__ DevState S;
+  if (!state_enter(&S, st, UZ, UR)) return;
+  const PrecondScalars c(&S);
+  TZ* __restrict__ z = (TZ*)B.z;
+  const int64_t nv = (n + V - 1) / V;
+  const int64_t stride = GridPart::count();
+  const int64_t v0 = GridPart::first();
+  double rho = 0.0;
+  Dot2 d2;
+  alignas(16) TZ zr[kZreg][V];
+#pragma unroll
+  for (int t = 0; t < kZreg; ++t) {
+    const int64_t v = v0 + t * stride;
+    if (v < nv) {
+      const int64_t i0 = v * V;
+      const int m = (n - i0 < V) ? (int)(n - i0) : V;
+      precond_vec<UZ, UR, MT, V, GridPart>(B, c, i0, m, zr[t], rho, d2);
+    }
+  }
+  for (int64_t v = v0 + kZreg * stride; v < nv; v += stride) {
+    const int64_t i0 = v * V;
+    const int m = (n - i0 < V) ? (int)(n - i0) : V;
+    alignas(16) TZ zz[V];
+    precond_vec<UZ, UR, MT, V, GridPart>(B, c, i0, m, zz, rho, d2);
+    vst<V>(z + i0, zz, m);
+  }
+  if (S.p_cast) cast_p<UZ>(B, n, &S);
+  double v[1];
+  if constexpr (kSmall) {
+    v[0] = block_sum_dot2(d2, S.inv_sig);
+  } else {
+    v[0] = rho;
+    block_sum<1>(v);
+  }
+  double tot;
+  unsigned long long unused;
+  int nb = 0;
+  const bool ok = grid_reduce_barrier<1>(B.bar + 2 * UZ + UR, B.part, nullptr, nb, v[0], 0ull, tot, unused);
+  if (threadIdx.x == 0) {
+    if (ok) {
+      rho_step(&S, tot);
+    } else {
+      S.status = ST_INTERNAL;
+      S.done = 1;
+    }
+    S.phase_runs[2 * UZ + UR] += 1;
+  }
+  __syncthreads();
+  if (!S.done) {
+    // p_k = z_k + beta_{k-1} p_{k-1}; p_{k-1} may have been converted by
+    // other blocks of this launch (cast_p), so it is read through L2
+    const int pc = S.pcur;
+    const TZ* __restrict__ po = (const TZ*)(pc ? B.p[1] : B.p[0]);
+    TZ* __restrict__ pn = (TZ*)(pc ? B.p[0] : B.p[1]);
+    const int first = S.first;
+    const double beta = S.beta;
+    const float bf = S.beta_f;
+    auto dir = [&](int64_t i0, int m, const TZ (&zz)[V]) {
+      if (first) {
+        vst<V>(pn + i0, zz, m);
+        return;
+      }
+      alignas(16) TZ pp[V];
+      vldcg<V>(po + i0, pp);
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        if constexpr (UZ == P64) pp[j] = fma(beta, pp[j], zz[j]);
+        else pp[j] = axpy_one<UZ>(bf, pp[j], zz[j]);
+      }
+      vst<V>(pn + i0, pp, m);
+    };
+#pragma unroll
+    for (int t = 0; t < kZreg; ++t) {
+      const int64_t v = v0 + t * stride;
+      if (v < nv) {
+        const int64_t i0 = v * V;
+        dir(i0, (n - i0 < V) ? (int)(n - i0) : V, zr[t]);
+      }
+    }
+    for (int64_t v = v0 + kZreg * stride; v < nv; v += stride) {
+      const int64_t i0 = v * V;
+      alignas(16) TZ zz[V];
+      vld<V>(z + i0, zz);
+      dir(i0, (n - i0 < V) ? (int)(n - i0) : V, zz);
+    }
+  }
+  if (blockIdx.x == 0) state_store(st, &S);
 }
 
 // ---------------------------------------------------------------------------
@@ -1053,12 +1158,12 @@ __device__ __forceinline__ void gamma_step(DevState* s, double g) {
 template <int UZ, int UR, int IT, bool WIDE>
 __global__ void __launch_bounds__(256, WIDE ? 3 : 4) k_spmv(Sell A, Bufs B, DevState* st) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  if (st->done) return;
-  if (phase_mismatch(st, UZ, UR)) return;
+  __shared__ DevState S;
+  if (!state_enter(&S, st, UZ, UR)) return;
   double gam = 0.0;
   Dot2 d2;
-  if constexpr (WIDE) spmv_rows<UZ, UR, IT>(A, B, st, gam, d2);
-  else spmv_rows_staged<UZ, UR, IT>(A, B, st, gam, d2, dsm);
+  if constexpr (WIDE) spmv_rows<UZ, UR, IT>(A, B, &S, gam, d2);
+  else spmv_rows_staged<UZ, UR, IT>(A, B, &S, gam, d2, dsm);
   double v[1];
   if constexpr ((UR != P64) && (UZ != P64)) {
     v[0] = block_sum_dot2(d2, 1.0);
@@ -1068,7 +1173,6 @@ __global__ void __launch_bounds__(256, WIDE ? 3 : 4) k_spmv(Sell A, Bufs B, DevS
   }
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[1])) return;
-  __shared__ DevState S;
   state_load(&S, st);
   double tot[1];
   final_sum<1>(B.part, gridDim.x, 1, tot);
@@ -1164,15 +1268,15 @@ __device__ __forceinline__ double update_step(DevState* s, double rr, unsigned l
 
 template <int UZ, int UR>
 __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st) {
-  if (st->done) return;
-  if (phase_mismatch(st, UZ, UR)) return;
+  __shared__ DevState S;
+  if (!state_enter(&S, st, UZ, UR)) return;
   double rr = 0.0;
   Dot2 d2;
   unsigned long long mx = 0ull;
-  update_rows<UZ, UR, 4>(B, n, st, rr, d2, mx);
+  update_rows<UZ, UR, 4>(B, n, &S, rr, d2, mx);
   double v[1];
   if constexpr (UR != P64) {
-    v[0] = block_sum_dot2(d2, st->inv_sig2);
+    v[0] = block_sum_dot2(d2, S.inv_sig2);
   } else {
     v[0] = rr;
     block_sum<1>(v);
@@ -1183,7 +1287,6 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st)
     B.pmax[blockIdx.x] = mx;
   }
   if (!last_block(&st->ticket[2])) return;
-  __shared__ DevState S;
   state_load(&S, st);
   double tot[1];
   unsigned long long m = final_sum_max<1>(B.part, 1, B.pmax, gridDim.x, tot);
@@ -1196,6 +1299,207 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st)
   }
   state_store(st, &S);
   if (threadIdx.x == 0) S.delta_hist[k1] = d;
+}
+
+// ---------------------------------------------------------------------------
+// The iteration loop of one precision pair as one cooperative launch (Jacobi
+// or no preconditioner, slices at most kStageW wide): up to `iters`
+// iterations of Alg. 3 on the same row loops as the kernels above, every block
+// holding its own copy of the state.  The four grid-wide dependences of an
+// iteration -- rho_k, p_k before the SpMV's gathers, gamma_k, and delta_{k+1}
+// with max|r| -- are grid barriers whose last arriving block sums the
+// partials (grid_reduce_barrier); every block then runs the same scalar step
+// on its copy, so all agree on beta, alpha, the stop and the next
+// precisions.  The launch ends after `iters` iterations, at the stop, or when
+// the selector picks another pair; block 0 writes the state back (only it
+// writes the histories).  Data that other blocks write during the launch is
+// read through L2 (LoopPart), never through the read-only path.
+struct LoopPart {
+  __device__ static __forceinline__ int64_t first() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ static __forceinline__ int64_t count() { return (int64_t)gridDim.x * blockDim.x; }
+  template <class T>
+  __device__ static __forceinline__ T ldm(const T* p) { return __ldcg(p); }
+  template <int V, class T>
+  __device__ static __forceinline__ void vldm(const T* p, T (&o)[V]) { vldcg<V>(p, o); }
+  template <int V, class T>
+  __device__ static __forceinline__ void vldo(const T* p, T (&o)[V]) { vldcg<V>(p, o); }
+};
+
+// One block of kLoopBlock threads per SM: fewer blocks meet at each grid
+// barrier (its arrivals and polls contend on one word), the same registers
+// and shared memory per SM as four blocks of 256.  The staged SpMV's stages
+// per warp are capped so that the block's stages fit in 200 KB.
+constexpr int kLoopBlock = 1024;
+template <int UR, int IT> struct LoopStageCfg {
+  static constexpr int kPer = (kLoopBlock / 32) * 32 * kStageW *
+                              (int)(sizeof(typename Store<UR>::T) + sizeof(typename IdxT<IT>::T));
+  static constexpr int K = StageCfg<UR>::K < (200 * 1024) / kPer ? StageCfg<UR>::K : (200 * 1024) / kPer;
+  static constexpr int kBytes = K * kPer;
+};
+template <int UZ, int UR, int MT, int IT>
+__global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t n, DevState* st, int iters) {
+  using TZ = typename Store<UZ>::T;
+  using Part = LoopPart;
+  constexpr int V = 4;                         // update
+  constexpr int VZ = (UZ == P64) ? 4 : 8;      // precondition and direction
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ DevState S;
+  if (!state_enter(&S, st, UZ, UR)) return;
+  if (blockIdx.x != 0 && threadIdx.x == 0) S.prec_hist = nullptr;   // block 0 records the choices
+  GridSumBarrier* bar = B.bar + 6 + 2 * UZ + UR;
+  TZ* __restrict__ z = (TZ*)B.z;
+  const int64_t nvz = (n + VZ - 1) / VZ;
+  const int64_t stride = Part::count();
+  const int64_t v0 = Part::first();
+  double tot;
+  unsigned long long mtot;
+  bool ok = true;
+  int nb = 0;   // barriers passed in this launch
+  for (int it = 0; it < iters; ++it) {
+    // Alg. 3: scaling, preconditioning, rho_k and beta_{k-1}; with binary16
+    // storage p_{k-1} of the register-held vectors is loaded before the
+    // barrier (it does not depend on beta_{k-1}; not when it is converted)
+    alignas(16) TZ zr[kZreg][VZ];
+    alignas(16) TZ pr[kZreg][VZ];
+    const bool pre = (UZ == P16) && !S.p_cast && !S.first;
+    {
+      const PrecondScalars c(&S);
+      double rho = 0.0;
+      Dot2 d2;
+#pragma unroll
+      for (int t = 0; t < kZreg; ++t) {
+        const int64_t v = v0 + t * stride;
+        if (v < nvz) {
+          const int64_t i0 = v * VZ;
+          precond_vec<UZ, UR, MT, VZ, Part>(B, c, i0, (n - i0 < VZ) ? (int)(n - i0) : VZ, zr[t], rho, d2);
+        }
+      }
+      if constexpr (UZ == P16) {
+        if (pre) {
+          const TZ* po = (const TZ*)(S.pcur ? B.p[1] : B.p[0]);
+#pragma unroll
+          for (int t = 0; t < kZreg; ++t) {
+            const int64_t v = v0 + t * stride;
+            if (v < nvz) vldcg<VZ>(po + v * VZ, pr[t]);
+          }
+        }
+      }
+      for (int64_t v = v0 + kZreg * stride; v < nvz; v += stride) {
+        const int64_t i0 = v * VZ;
+        const int m = (n - i0 < VZ) ? (int)(n - i0) : VZ;
+        alignas(16) TZ zz[VZ];
+        precond_vec<UZ, UR, MT, VZ, Part>(B, c, i0, m, zz, rho, d2);
+        vst<VZ>(z + i0, zz, m);
+      }
+      if (S.p_cast) cast_p<UZ, Part>(B, n, &S);
+      double v[1];
+      if constexpr (kSmall) {
+        v[0] = block_sum_dot2(d2, S.inv_sig);
+      } else {
+        v[0] = rho;
+        block_sum<1>(v);
+      }
+      ok = grid_reduce_barrier<1>(bar, B.part, nullptr, nb, v[0], 0ull, tot, mtot);
+      if (!ok) break;
+      if (threadIdx.x == 0) {
+        S.phase_runs[2 * UZ + UR] += 1;
+        rho_step(&S, tot);
+      }
+      __syncthreads();
+      if (S.done) break;
+    }
+    // Alg. 3: search direction p_k = z_k + beta_{k-1} p_{k-1}
+    {
+      const int pc = S.pcur;
+      const TZ* __restrict__ po = (const TZ*)(pc ? B.p[1] : B.p[0]);
+      TZ* __restrict__ pn = (TZ*)(pc ? B.p[0] : B.p[1]);
+      const int first = S.first;
+      const double beta = S.beta;
+      const float bf = S.beta_f;
+      auto dir = [&](int64_t i0, int m, const TZ (&zz)[VZ], const TZ (&pp0)[VZ], bool have) {
+        if (first) {
+          vst<VZ>(pn + i0, zz, m);
+          return;
+        }
+        alignas(16) TZ pp[VZ];
+        if (have) {
+#pragma unroll
+          for (int j = 0; j < VZ; ++j) pp[j] = pp0[j];
+        } else {
+          vldcg<VZ>(po + i0, pp);
+        }
+#pragma unroll
+        for (int j = 0; j < VZ; ++j) {
+          if constexpr (UZ == P64) pp[j] = fma(beta, pp[j], zz[j]);
+          else pp[j] = axpy_one<UZ>(bf, pp[j], zz[j]);
+        }
+        vst<VZ>(pn + i0, pp, m);
+      };
+#pragma unroll
+      for (int t = 0; t < kZreg; ++t) {
+        const int64_t v = v0 + t * stride;
+        if (v < nvz) {
+          const int64_t i0 = v * VZ;
+          dir(i0, (n - i0 < VZ) ? (int)(n - i0) : VZ, zr[t], pr[t], pre);
+        }
+      }
+      for (int64_t v = v0 + kZreg * stride; v < nvz; v += stride) {
+        const int64_t i0 = v * VZ;
+        alignas(16) TZ zz[VZ];
+        vldcg<VZ>(z + i0, zz);
+        dir(i0, (n - i0 < VZ) ? (int)(n - i0) : VZ, zz, zz, false);
+      }
+      ok = grid_reduce_barrier<0>(bar, nullptr, nullptr, nb, 0.0, 0ull, tot, mtot);   // p_k before the gathers
+      if (!ok) break;
+    }
+    // Alg. 3: q_k = A p_k, gamma_k, alpha_k
+    {
+      double gam = 0.0;
+      Dot2 d2;
+      spmv_rows_staged<UZ, UR, IT, Part, LoopStageCfg<UR, IT>::K>(A, B, &S, gam, d2, dsm);
+      double v[1];
+      if constexpr (kSmall) {
+        v[0] = block_sum_dot2(d2, 1.0);
+      } else {
+        v[0] = gam;
+        block_sum<1>(v);
+      }
+      ok = grid_reduce_barrier<1>(bar, B.part, nullptr, nb, v[0], 0ull, tot, mtot);
+      if (!ok) break;
+      if (threadIdx.x == 0) gamma_step(&S, tot);
+      __syncthreads();
+      if (S.done) break;
+    }
+    // Alg. 3: x and r updates, delta_{k+1}, stopping test, next precisions
+    {
+      double rr = 0.0;
+      Dot2 d2;
+      unsigned long long mx = 0ull;
+      update_rows<UZ, UR, V, Part>(B, n, &S, rr, d2, mx);
+      double v[1];
+      if constexpr (UR != P64) {
+        v[0] = block_sum_dot2(d2, S.inv_sig2);
+      } else {
+        v[0] = rr;
+        block_sum<1>(v);
+      }
+      mx = block_max(mx);
+      ok = grid_reduce_barrier<2>(bar, B.part, B.pmax, nb, v[0], mx, tot, mtot);
+      if (!ok) break;
+      if (threadIdx.x == 0) {
+        const double d = update_step(&S, tot, mtot);
+        if (blockIdx.x == 0) S.delta_hist[S.k] = d;
+      }
+      __syncthreads();
+      if (S.done || S.uz != UZ || S.ur != UR) break;
+    }
+  }
+  if (!ok && threadIdx.x == 0) {
+    S.status = ST_INTERNAL;
+    S.done = 1;
+  }
+  if (blockIdx.x == 0) state_store(st, &S);
 }
 
 // Loop graph control (one thread each).  The outer loop picks the precision
@@ -1666,13 +1970,13 @@ template <int UZ, int UR>
 __global__ void __launch_bounds__(256) k_cheb_init(Bufs B, Cheb C, int64_t n, DevState* st) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
-  if (st->done) return;
-  if (phase_mismatch(st, UZ, UR)) return;
+  __shared__ DevState S;
+  if (!state_enter(&S, st, UZ, UR)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->phase_runs[2 * UZ + UR] += 1;
-  const int r_cast = st->r_cast;
-  const double om = st->omega;
-  const float omf = st->omega_f;
-  const int pow2 = st->omega_pow2, oe = st->omega_e;
+  const int r_cast = S.r_cast;
+  const double om = S.omega;
+  const float omf = S.omega_f;
+  const int pow2 = S.omega_pow2, oe = S.omega_e;
   const bool om_one = pow2 && oe == 0;
   TZ* res = (TZ*)C.res;
   TZ* d0 = (TZ*)C.d[0];
@@ -1706,7 +2010,7 @@ __global__ void __launch_bounds__(256) k_cheb_init(Bufs B, Cheb C, int64_t n, De
     d0[i] = dd;
     u[i] = dd;
   }
-  if (st->p_cast) cast_p<UZ>(B, n, st);
+  if (S.p_cast) cast_p<UZ>(B, n, &S);
 }
 
 // One Chebyshev step j >= 1: t = Ahat d_{j-1} (accumulated in u_z's compute
@@ -1746,8 +2050,11 @@ template <int UZ, int UR, int IT>
 __global__ void __launch_bounds__(256) k_cheb_step(Sell A, Cheb C, DevState* st, int j, double c1,
                                                    double c2) {
   using TZ = typename Store<UZ>::T;
-  if (st->done) return;
-  if (phase_mismatch(st, UZ, UR)) return;
+  {
+    // one round of loads for the entry test (no other state is read)
+    const int dn = st->done, uz = st->uz, ur = st->ur;
+    if (dn || uz != UZ || ur != UR) return;
+  }
   const TZ* __restrict__ dp = (const TZ*)(((j - 1) & 1) ? C.d[1] : C.d[0]);
   TZ* dn = (TZ*)((j & 1) ? C.d[1] : C.d[0]);
   TZ* res = (TZ*)C.res;
@@ -1796,12 +2103,12 @@ template <int UZ, int UR>
 __global__ void __launch_bounds__(256) k_cheb_final(Bufs B, Cheb C, int64_t n, DevState* st) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
-  if (st->done) return;
-  if (phase_mismatch(st, UZ, UR)) return;
+  __shared__ DevState S;
+  if (!state_enter(&S, st, UZ, UR)) return;
   constexpr bool kSmall = (UR != P64) && (UZ != P64);
   const TZ* u = (const TZ*)C.u;
   TZ* z = (TZ*)B.z;
-  const float sigf = st->sig_f;
+  const float sigf = S.sig_f;
   double rho = 0.0;
   Dot2 d2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1816,14 +2123,13 @@ __global__ void __launch_bounds__(256) k_cheb_final(Bufs B, Cheb C, int64_t n, D
   }
   double v[1];
   if constexpr (kSmall) {
-    v[0] = block_sum_dot2(d2, st->inv_sig);
+    v[0] = block_sum_dot2(d2, S.inv_sig);
   } else {
     v[0] = rho;
     block_sum<1>(v);
   }
   if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
   if (!last_block(&st->ticket[0])) return;
-  __shared__ DevState S;
   state_load(&S, st);
   double tot[1];
   final_sum<1>(B.part, gridDim.x, 1, tot);

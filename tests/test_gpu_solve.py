@@ -160,7 +160,8 @@ def test_loop_graph_equals_kernel_by_kernel(kind):
 
 def test_loop_graph_launch_count():
     # one precision pair, no replacement: k_init, one outer body (k_phase,
-    # k_loop_ctl), ceil(iters / chunk) chunks of chunk x 4 launches plus
+    # k_loop_ctl), ceil(iters / chunk) chunks, each one k_loop launch (Jacobi,
+    # narrow slices: the whole chunk in one cooperative launch) plus
     # k_chunk_ctl, and the true residual
     a = W.diffusion3d(16, 1.0, 3)
     b = torch.as_tensor(W.rhs_uniform(a.n, 2), device="cuda")
@@ -169,7 +170,7 @@ def test_loop_graph_launch_count():
         pol = P.Policy.pcg64(graph_chunk=chunk)
         _, info = s.solve(b, tol=TOL, maxit=5000, policy=pol)
         chunks = -(-info.iters // chunk)
-        assert info.kernel_launches == 1 + 2 + chunks * (4 * chunk + 1) + 1
+        assert info.kernel_launches == 1 + 2 + chunks * 2 + 1
     s.close()
 
 
