@@ -64,10 +64,11 @@ def config_dict(a, extra=None):
     return d
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
-# it is now (profiles/iteration_kernels_diffusion128.md); a kernel missing
-# here reports null.
-NCU_TRAFFIC = {"amp:spmv_gamma:uz16_ur64": 161.9e6, "amp:spmv_gamma:uz16_ur32": 96.3e6}
+# DRAM bytes (read + write) per launch (one iteration of k_loop) from one ncu
+# capture of the kernel as it is now (profiles/k_loop_diffusion128.md); a
+# kernel missing here reports null.
+NCU_TRAFFIC = {"amp:iteration:uz16_ur64": 238.6e6, "amp:iteration:uz16_ur32": 139.1e6,
+               "fp64:iteration:uz64_ur64": 284.1e6}
 
 
 def peaks():
@@ -141,6 +142,9 @@ def alg_bytes(kernel: str, phase: str, n: int, nnz: int, nslices: int, idx_bytes
     if kernel == "precond":
         # Jacobi: r, D^-1, p_{k-1} read, p_k written (z_k stays in registers)
         return n * (rb + 3 * zb)
+    if kernel == "iteration":
+        # k_loop: the precondition + direction, SpMV and update rows
+        return sum(alg_bytes(k, phase, n, nnz, nslices, idx_bytes) for k in ("precond", "spmv_gamma", "update_norm"))
     if kernel == "search_dir":
         return n * 3 * zb
     if kernel == "spmv_gamma":
@@ -287,6 +291,29 @@ def run_ours(args, rank, world):
                 "frac": round(achieved / peak, 3), "traffic": NCU_TRAFFIC.get(dk), "kernel": dk,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
+    # per-iteration device time inside the loop graph, per precision pair:
+    # fixed-pair solves of FIXED_ITERS iterations (tolerance out of reach), L2
+    # flushed before each, CUDA events around the solve
+    FIXED_ITERS = 400
+    graph_iter = {}
+    for ph, pol in (("uz16_ur64", P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64)),
+                    ("uz16_ur32", P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32)),
+                    ("uz64_ur64", P.Policy.pcg64())):
+        best = None
+        for _ in range(3):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            _, fi = s.solve(bd, torch.zeros_like(bd), tol=1e-300, maxit=FIXED_ITERS, policy=pol, history=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e3 / max(fi.iters, 1)
+            best = t if best is None else min(best, t)
+        by = alg_bytes("iteration", ph, a.n, a.nnz, nslices, idx_bytes)
+        graph_iter[ph] = {"us": round(best, 2), "alg_bytes": int(by), "gbs": round(by / (best * 1e-6) / 1e9, 1),
+                          "frac": round(by / (best * 1e-6) / 1e9 / peak, 3)}
+
     # end to end through the C ABI with pinned host buffers
     bh = torch.as_tensor(b).pin_memory()
     xh = torch.zeros(a.n, dtype=torch.float64).pin_memory()
@@ -323,6 +350,7 @@ def run_ours(args, rank, world):
                "true_relres_amp64_window": w_info[-1].true_relres,
                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": clocks, "gpu_launches": launches,
+               "iteration_in_graph": graph_iter,
                "gpu_launches_note": "library kernels in the timed region (all timed solves), counted by the library"}
         print(json.dumps(out), flush=True)
     s.close()

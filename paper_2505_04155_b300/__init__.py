@@ -60,9 +60,12 @@ class KernelTimesC(C.Structure):
     _fields_ = [("ms", (C.c_double * 6) * 4), ("launches", (C.c_int * 6) * 4), ("total_ms", C.c_double)]
 
 
-# event-timed slots of an iteration: the precondition step (with Jacobi or no
-# preconditioner also rho, beta and the search direction, one cooperative
-# kernel), the search direction (Chebyshev only), SpMV + gamma, update + norm
+# event-timed slots of an iteration in the launch-by-launch mode: the
+# precondition step (with Jacobi or no preconditioner also rho, beta and the
+# search direction, one cooperative kernel), the search direction (Chebyshev
+# only), SpMV + gamma, update + norm.  Where the whole iteration is one
+# cooperative launch (k_loop: Jacobi or none, narrow slices) its time is
+# reported as "iteration".
 KERNEL_NAMES = ("precond", "search_dir", "spmv_gamma", "update_norm")
 
 
@@ -310,9 +313,14 @@ class Solver:
                          res.updated_relres, tuple(res.switch_iter), res.seconds,
                          res.kernel_launches, rh[: it + 1].copy() if history else None, ph[:it].copy() if history else None)
         if timed:
-            info.kernel_ms = {(KERNEL_NAMES[j], phase_name(ph_)): kt.ms[j][ph_]
+            def slot_name(j, ph_):
+                # one launch in slot 0 only: the whole iteration (k_loop)
+                if j == 0 and not any(kt.launches[i][ph_] for i in (1, 2, 3)):
+                    return "iteration"
+                return KERNEL_NAMES[j]
+            info.kernel_ms = {(slot_name(j, ph_), phase_name(ph_)): kt.ms[j][ph_]
                               for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
-            info.kernel_launches_by = {(KERNEL_NAMES[j], phase_name(ph_)): kt.launches[j][ph_]
+            info.kernel_launches_by = {(slot_name(j, ph_), phase_name(ph_)): kt.launches[j][ph_]
                                     for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
             info.kernel_total_ms = kt.total_ms
         return x, info
