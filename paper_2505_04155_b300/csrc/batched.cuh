@@ -79,7 +79,7 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
       v[0] = block_sum_dot2(d2, S->inv_sig);
     } else {
       v[0] = rho;
-      block_sum<1>(v);
+      block_sum_wide<1>(v);
     }
     if (threadIdx.x == 0) {
       S->phase_runs[2 * UZ + UR] += 1;
@@ -102,7 +102,7 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
       v[0] = block_sum_dot2(d2, 1.0);
     } else {
       v[0] = gam;
-      block_sum<1>(v);
+      block_sum_wide<1>(v);
     }
     if (threadIdx.x == 0) gamma_step(S, v[0]);
     __syncthreads();
@@ -119,7 +119,7 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
       v[0] = block_sum_dot2(d2, S->inv_sig2);
     } else {
       v[0] = rr;
-      block_sum<1>(v);
+      block_sum_wide<1>(v);
     }
     mx = block_max(mx);
     if (threadIdx.x == 0) {

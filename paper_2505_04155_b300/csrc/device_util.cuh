@@ -280,6 +280,42 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   }
 }
 
+// block_sum for blocks of 1024 threads (blockDim.x a multiple of 256, at most
+// 1024).  The values go through shared memory: thread r < 256 adds values
+// r, r + 256, ... in that order, each of those 8 warps reduces by a shuffle
+// tree, and warp 0 adds the 8 warp totals with 3 more levels.  At 1024
+// threads it issues 67 FP64 warp-instructions per value against 165 for a
+// shuffle tree in every warp, which matters on B300, whose FP64 pipe takes
+// 16 cycles per warp-instruction.
+template <int NV>
+__device__ __forceinline__ void block_sum_wide(double (&v)[NV]) {
+  __shared__ double sh[NV][1024];
+  __shared__ double sw[NV][8];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) sh[j][t] = v[j];
+  __syncthreads();
+  if (t < 256) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double a = sh[j][t];
+      for (int u = t + 256; u < (int)blockDim.x; u += 256) a += sh[j][u];
+      a = warp_sum(a);
+      if (lane == 0) sw[j][wid] = a;
+    }
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double a = lane < 8 ? sw[j][lane] : 0.0;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+      v[j] = a;
+    }
+  }
+}
+
 // Block total of per-thread Dot2 pairs, scaled by `scale` (a power of two);
 // valid in thread 0.  Binary64 work: one add per warp plus warp 0's tree.
 __device__ __forceinline__ double block_sum_dot2(Dot2 d, double scale) {

@@ -1398,7 +1398,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
         v[0] = block_sum_dot2(d2, S.inv_sig);
       } else {
         v[0] = rho;
-        block_sum<1>(v);
+        block_sum_wide<1>(v);
       }
       ok = grid_reduce_barrier<1>(bar, B.part, nullptr, nb, v[0], 0ull, tot, mtot);
       if (!ok) break;
@@ -1463,7 +1463,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
         v[0] = block_sum_dot2(d2, 1.0);
       } else {
         v[0] = gam;
-        block_sum<1>(v);
+        block_sum_wide<1>(v);
       }
       ok = grid_reduce_barrier<1>(bar, B.part, nullptr, nb, v[0], 0ull, tot, mtot);
       if (!ok) break;
@@ -1482,7 +1482,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
         v[0] = block_sum_dot2(d2, S.inv_sig2);
       } else {
         v[0] = rr;
-        block_sum<1>(v);
+        block_sum_wide<1>(v);
       }
       mx = block_max(mx);
       ok = grid_reduce_barrier<2>(bar, B.part, B.pmax, nb, v[0], mx, tot, mtot);
