@@ -121,6 +121,7 @@ struct ampcg_ctx {
   std::vector<Launch> seq[6];
   // k_loop per precision pair (Jacobi or none, slices at most kStageW wide):
   // the device loop and the timed path launch it instead of seq
+  int stream_hint = 0;    // Sell::stream_hint
   Launch loop[6];
   bool loop_ok = true;    // every pair's k_loop configured (set while building)
   bool use_loop = false;
@@ -161,6 +162,7 @@ struct ampcg_ctx {
     A.coff = idx16 ? coff : nullptr;
     A.v64 = v64;
     A.v32 = v32;
+    A.stream_hint = stream_hint;
     return A;
   }
   Bufs bufs() const {
@@ -368,6 +370,12 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   CTRY(cudaStreamSynchronize(s));
   long long stored = tot2[0];
   c->maxw = (int)tot2[1];
+  {
+    // the matrix (binary32 copy) and ~40 bytes per row of vectors would not
+    // fit in L2 together: stream the matrix with an evict-first hint
+    const double mbytes = (double)stored * (4 + (c->idx16 ? 2 : 4)) + 40.0 * (double)n;
+    c->stream_hint = mbytes > 96.0 * (1 << 20) ? 1 : 0;
+  }
   if (c->idx16) TRY(dalloc(&c->coff, stored));
   else TRY(dalloc(&c->cabs, stored));
   TRY(dalloc(&c->v64, stored));

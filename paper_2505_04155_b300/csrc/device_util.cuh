@@ -169,6 +169,62 @@ __device__ __forceinline__ void vldcg(const T* __restrict__ p, T (&o)[V]) {
   }
 }
 
+// Accesses with an L2 evict-last hint (createpolicy; the policy is computed
+// once and reused: the asm is not volatile).  The iteration vectors, re-read
+// every iteration, are kept in L2 ahead of the streamed matrix.
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint4 ld16_keep(const void* p, unsigned long long pol) {
+  uint4 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;\n"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st16_keep(void* p, uint4 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(p), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+// scalar load through L2 with the hint; T of 2, 4 or 8 bytes
+template <class T>
+__device__ __forceinline__ T ld_keep(const T* p, unsigned long long pol) {
+  if constexpr (sizeof(T) == 2) {
+    unsigned short u;
+    asm volatile("ld.global.cg.L2::cache_hint.u16 %0, [%1], %2;\n" : "=h"(u) : "l"(p), "l"(pol));
+    return *reinterpret_cast<T*>(&u);
+  } else if constexpr (sizeof(T) == 4) {
+    unsigned u;
+    asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;\n" : "=r"(u) : "l"(p), "l"(pol));
+    return *reinterpret_cast<T*>(&u);
+  } else {
+    unsigned long long u;
+    asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;\n" : "=l"(u) : "l"(p), "l"(pol));
+    return *reinterpret_cast<T*>(&u);
+  }
+}
+template <int V, class T>
+__device__ __forceinline__ void vld_keep(const T* p, T (&o)[V], unsigned long long pol) {
+  if constexpr ((V * sizeof(T)) % 16 == 0) {
+    constexpr int NQ = (int)(V * sizeof(T) / 16);
+#pragma unroll
+    for (int j = 0; j < NQ; ++j)
+      reinterpret_cast<uint4*>(o)[j] = ld16_keep(reinterpret_cast<const uint4*>(p) + j, pol);
+  } else if constexpr (V * sizeof(T) == 8) {
+    uint2 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;\n"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(p), "l"(pol));
+    *reinterpret_cast<uint2*>(o) = v;
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) o[j] = __ldcg(p + j);
+  }
+}
+
 // Stores the first m of V elements (all V with one vector store when m == V).
 template <int V, class T>
 __device__ __forceinline__ void vst(T* __restrict__ p, const T (&o)[V], int m) {

@@ -144,6 +144,7 @@ struct Sell {
   const short* coff;     // int16 offsets, or null
   const double* v64;
   const float* v32;
+  int stream_hint;       // matrix larger than L2's share: staged loads marked evict-first
 };
 
 // Scalar-side pieces of the algorithm, evaluated by one thread -------------
@@ -919,6 +920,19 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
+// The same copy with an L2 eviction-priority hint (createpolicy).  A matrix
+// streamed once per iteration and larger than L2 is marked evict-first, so
+// that the iteration vectors (re-read every iteration) stay in L2.
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void cp_async16_hint(void* sdst, const void* gsrc, unsigned long long pol) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "l"(pol)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -958,6 +972,8 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
   const int64_t nw = Part::count() >> 5;
   const int64_t spw = (A.nslices + nw - 1) / nw;
   const int64_t s1 = gw * spw + spw < A.nslices ? gw * spw + spw : A.nslices;
+  const bool hint = A.stream_hint != 0;
+  const unsigned long long pol = hint ? l2_policy_evict_first() : 0ull;
   // chunks of at most 32 slices (one header per lane); one chunk in the
   // single-system launch, whose grid gives every warp at most 32 slices
   for (int64_t s0 = gw * spw; s0 < s1; s0 += 32) {
@@ -979,7 +995,10 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
   #pragma unroll
         for (int u = 0; u < kStageW * (int)sizeof(TR) / 16; ++u) {
           const int c = lane + 32 * u;
-          if (c < nv) cp_async16(dv + 16 * c, gv + 16 * c);
+          if (c < nv) {
+            if (hint) cp_async16_hint(dv + 16 * c, gv + 16 * c, pol);
+            else cp_async16(dv + 16 * c, gv + 16 * c);
+          }
         }
         const char* gi = (const char*)(ia + o);
         char* di = (char*)(si + stg * SE);
@@ -987,7 +1006,10 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
   #pragma unroll
         for (int u = 0; u < (kStageW * (int)sizeof(TI) + 15) / 16; ++u) {
           const int c = lane + 32 * u;
-          if (c < ni) cp_async16(di + 16 * c, gi + 16 * c);
+          if (c < ni) {
+            if (hint) cp_async16_hint(di + 16 * c, gi + 16 * c, pol);
+            else cp_async16(di + 16 * c, gi + 16 * c);
+          }
         }
       }
       cp_async_commit();
@@ -1317,12 +1339,14 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st)
 struct LoopPart {
   __device__ static __forceinline__ int64_t first() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
   __device__ static __forceinline__ int64_t count() { return (int64_t)gridDim.x * blockDim.x; }
+  // the loads carry an L2 evict-last hint: the vectors stay in L2 across
+  // iterations while the matrix streams through (evict-first)
   template <class T>
-  __device__ static __forceinline__ T ldm(const T* p) { return __ldcg(p); }
+  __device__ static __forceinline__ T ldm(const T* p) { return ld_keep(p, l2_policy_evict_last()); }
   template <int V, class T>
-  __device__ static __forceinline__ void vldm(const T* p, T (&o)[V]) { vldcg<V>(p, o); }
+  __device__ static __forceinline__ void vldm(const T* p, T (&o)[V]) { vld_keep<V>(p, o, l2_policy_evict_last()); }
   template <int V, class T>
-  __device__ static __forceinline__ void vldo(const T* p, T (&o)[V]) { vldcg<V>(p, o); }
+  __device__ static __forceinline__ void vldo(const T* p, T (&o)[V]) { vld_keep<V>(p, o, l2_policy_evict_last()); }
 };
 
 // One block of kLoopBlock threads per SM: fewer blocks meet at each grid
