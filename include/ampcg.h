@@ -96,7 +96,9 @@ typedef struct {
                          this many times.  0: stop on the updated residual. */
   int fixed_uz;       /* FIXED criterion only */
   int fixed_ur;       /* FIXED criterion only: AMPCG_FP64 or AMPCG_FP32 */
-  int graph_chunk;    /* iterations per body of the device-side loop (>= 1; 0 = default) */
+  int graph_chunk;    /* iterations per chunk of the device-side loop: per launch of the
+                         persistent iteration kernel (Jacobi or none), or per repeat of
+                         the kernel sequence (>= 1; 0 = default 16) */
 } ampcg_policy;
 
 typedef struct {
@@ -198,9 +200,13 @@ ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, const double*
 /* Per-kernel device time of one solve, split by the precision pair of the
  * iteration, as the paper reports per-kernel time for each phase of
  * AMP-PCG (Sec. 5.5).  Index [kernel][phase]: kernel 0 = scale+precondition
- * +rho+beta, 1 = search direction, 2 = SpMV+gamma+alpha, 3 = x/r
+ * +rho+beta (with Jacobi or no preconditioner also the search direction),
+ * 1 = search direction (Chebyshev), 2 = SpMV+gamma+alpha, 3 = x/r
  * update+norm+stopping test+selector (the steps of Alg. 3); phase =
- * 2*u_z + u_r (u_z in {FP64, FP32, FP16}, u_r in {FP64, FP32}). */
+ * 2*u_z + u_r (u_z in {FP64, FP32, FP16}, u_r in {FP64, FP32}).  Where the
+ * whole iteration is one launch of the persistent iteration kernel (Jacobi
+ * or none, slices at most 8 entries wide), it is timed in slot 0, one
+ * iteration per launch, and slots 1-3 stay empty. */
 typedef struct {
   double ms[4][6];     /* summed CUDA-event durations */
   int launches[4][6];  /* launches that did work */
@@ -208,8 +214,9 @@ typedef struct {
 } ampcg_kernel_times;
 
 /* Same as ampcg_solve, computing the same iterates bit for bit, but the
- * iteration kernels are launched one by one (no graph) with a CUDA event pair
- * around each launch, and their durations are returned in *kt.  Slower than
+ * iteration kernels are launched one by one (no graph; the persistent kernel
+ * with one iteration per launch) with a CUDA event pair around each launch,
+ * and their durations are returned in *kt.  Slower than
  * ampcg_solve by the launch overhead; meant for measurement. */
 ampcg_status ampcg_solve_timed(ampcg_t ctx, const double* b, double* x, double tol, int maxit,
                                const ampcg_policy* policy, ampcg_result* res,
