@@ -67,8 +67,8 @@ def config_dict(a, extra=None):
 # DRAM bytes (read + write) per launch (one iteration of k_loop) from one ncu
 # capture of the kernel as it is now (profiles/k_loop_diffusion128.md); a
 # kernel missing here reports null.
-NCU_TRAFFIC = {"amp:iteration:uz16_ur64": 238.6e6, "amp:iteration:uz16_ur32": 139.1e6,
-               "fp64:iteration:uz64_ur64": 284.1e6}
+NCU_TRAFFIC = {"amp:iteration:uz16_ur64": 169.9e6, "amp:iteration:uz16_ur32": 102.2e6,
+               "fp64:iteration:uz64_ur64": 217.4e6}
 
 
 def peaks():
@@ -134,9 +134,12 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def alg_bytes(kernel: str, phase: str, n: int, nnz: int, nslices: int, idx_bytes: int) -> float:
+def alg_bytes(kernel: str, phase: str, n: int, nnz: int, nslices: int, idx_bytes: int,
+              uniform: float = 0.0) -> float:
     """Algorithmic bytes of one launch (each array the step must read or write,
-    once, in the storage precision the iteration uses)."""
+    once, in the storage precision the iteration uses).  `uniform`: the
+    fraction of slices stored with uniform offsets (their 8 offsets are read
+    once per slice instead of an offset per entry)."""
     sz = {"64": 8, "32": 4, "16": 2}
     zb, rb = sz[phase[2:4]], sz[phase[7:9]]
     if kernel == "precond":
@@ -144,11 +147,13 @@ def alg_bytes(kernel: str, phase: str, n: int, nnz: int, nslices: int, idx_bytes
         return n * (rb + 3 * zb)
     if kernel == "iteration":
         # k_loop: the precondition + direction, SpMV and update rows
-        return sum(alg_bytes(k, phase, n, nnz, nslices, idx_bytes) for k in ("precond", "spmv_gamma", "update_norm"))
+        return sum(alg_bytes(k, phase, n, nnz, nslices, idx_bytes, uniform)
+                   for k in ("precond", "spmv_gamma", "update_norm"))
     if kernel == "search_dir":
         return n * 3 * zb
     if kernel == "spmv_gamma":
-        return nnz * (rb + idx_bytes) + n * (zb + rb) + nslices * 12
+        return (nnz * (rb + idx_bytes * (1.0 - uniform)) + n * (zb + rb) + nslices * 12
+                + nslices * uniform * 16)
     if kernel == "update_norm":
         return n * (16 + zb + 3 * rb)
     raise KeyError(kernel)
@@ -270,14 +275,16 @@ def run_ours(args, rank, world):
     _, tinfo64 = s.solve(bd, torch.zeros_like(bd), tol=TOL, maxit=MAXIT, policy=f64, history=False, timed=True)
     peak, peak_kind = peaks()
     nslices = (a.n + 31) // 32
-    idx_bytes = 2  # int16 column offsets (7-point offsets fit)
+    lay = s.layout()
+    idx_bytes = 2 if lay["idx16"] else 4
+    uniform = lay["stored_uniform"] / max(lay["stored"], 1)
     kernels = {}
     for tag, ti in (("amp", tinfo), ("fp64", tinfo64)):
         ksum = sum(ti.kernel_ms.values())   # shares of kernel time, as in an ncu launch list
         for (kn, ph), ms in ti.kernel_ms.items():
             L = ti.kernel_launches_by[(kn, ph)]
             us = ms / L * 1e3
-            by = alg_bytes(kn, ph, a.n, a.nnz, nslices, idx_bytes)
+            by = alg_bytes(kn, ph, a.n, a.nnz, nslices, idx_bytes, uniform)
             kernels[f"{tag}:{kn}:{ph}"] = {"launches": L, "avg_us": round(us, 2), "alg_bytes": int(by),
                                            "gbs": round(by / (us * 1e-6) / 1e9, 1),
                                            "frac": round(by / (us * 1e-6) / 1e9 / peak, 3),
@@ -310,7 +317,7 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) * 1e3 / max(fi.iters, 1)
             best = t if best is None else min(best, t)
-        by = alg_bytes("iteration", ph, a.n, a.nnz, nslices, idx_bytes)
+        by = alg_bytes("iteration", ph, a.n, a.nnz, nslices, idx_bytes, uniform)
         graph_iter[ph] = {"us": round(best, 2), "alg_bytes": int(by), "gbs": round(by / (best * 1e-6) / 1e9, 1),
                           "frac": round(by / (best * 1e-6) / 1e9 / peak, 3)}
 
@@ -350,7 +357,7 @@ def run_ours(args, rank, world):
                "true_relres_amp64_window": w_info[-1].true_relres,
                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": clocks, "gpu_launches": launches,
-               "iteration_in_graph": graph_iter,
+               "iteration_in_graph": graph_iter, "layout": lay,
                "gpu_launches_note": "library kernels in the timed region (all timed solves), counted by the library"}
         print(json.dumps(out), flush=True)
     s.close()

@@ -307,6 +307,26 @@ ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy, const doub
 /* Number of rows of the context's matrix, or -1 for NULL. */
 int64_t ampcg_rows(ampcg_t ctx);
 
+/* Storage statistics of the context's matrix in the sliced layout (slices of
+ * 32 rows, entry j of a slice's rows stored together; column offsets in int16
+ * when they fit).  A slice whose rows all have their entries at one set of
+ * offsets is stored with that set (added entries hold exact zeros) and the
+ * SpMV reads its 8 offsets once instead of per entry: stored_uniform counts
+ * the entries of such slices.  For byte models; not from the paper.  Returns
+ * AMPCG_ERR_INVALID_ARG for NULL arguments; synchronises the context's
+ * stream. */
+typedef struct {
+  int64_t n;               /* rows */
+  int64_t nslices;         /* slices of 32 rows */
+  int64_t stored;          /* stored entries (32 x width summed over slices) */
+  int64_t stored_uniform;  /* of these, in slices with uniform offsets */
+  int32_t maxw;            /* largest slice width */
+  int32_t idx16;           /* 1: int16 column offsets, 0: int32 columns */
+  int32_t stream_hint;     /* 1: matrix loads carry an L2 evict-first hint */
+  int32_t reserved;
+} ampcg_layout;
+ampcg_status ampcg_layout_stats(ampcg_t ctx, ampcg_layout* out);
+
 /* Static strings: a status name, and the last error of this thread. */
 const char* ampcg_status_string(int status);
 const char* ampcg_last_error(void);

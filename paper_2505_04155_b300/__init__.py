@@ -41,6 +41,12 @@ class PrecondSpec(C.Structure):
     _fields_ = [("type", C.c_int), ("degree", C.c_int), ("lmin", C.c_double), ("lmax", C.c_double)]
 
 
+class LayoutC(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nslices", C.c_int64), ("stored", C.c_int64),
+                ("stored_uniform", C.c_int64), ("maxw", C.c_int32), ("idx16", C.c_int32),
+                ("stream_hint", C.c_int32), ("reserved", C.c_int32)]
+
+
 class PolicyC(C.Structure):
     _fields_ = [("u0", C.c_int), ("criterion", C.c_int), ("d", C.c_int), ("ell", C.c_int),
                 ("C", C.c_double), ("tau_zs", C.c_double), ("tau_zh", C.c_double),
@@ -129,6 +135,8 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_selector_trace_noalloc.restype = C.c_int
     lib.ampcg_rows.argtypes = [vp]
     lib.ampcg_rows.restype = i64
+    lib.ampcg_layout_stats.argtypes = [vp, C.POINTER(LayoutC)]
+    lib.ampcg_layout_stats.restype = C.c_int
     lib.ampcg_status_string.argtypes = [C.c_int]
     lib.ampcg_status_string.restype = C.c_char_p
     lib.ampcg_last_error.argtypes = []
@@ -324,6 +332,12 @@ class Solver:
                                     for j in range(4) for ph_ in range(6) if kt.launches[j][ph_]}
             info.kernel_total_ms = kt.total_ms
         return x, info
+
+    def layout(self) -> dict:
+        """Storage statistics of the sliced layout (ampcg_layout_stats)."""
+        out = LayoutC()
+        _check(load_library().ampcg_layout_stats(self._h, C.byref(out)))
+        return {k: getattr(out, k) for k, _ in LayoutC._fields_ if k != "reserved"}
 
     def interval(self):
         """The Chebyshev interval (lmin, lmax) in use (ampcg_precond_interval)."""

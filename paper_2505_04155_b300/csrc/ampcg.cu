@@ -122,6 +122,9 @@ struct ampcg_ctx {
   // k_loop per precision pair (Jacobi or none, slices at most kStageW wide):
   // the device loop and the timed path launch it instead of seq
   int stream_hint = 0;    // Sell::stream_hint
+  int64_t stored = 0;     // stored entries of the sliced layout
+  short* pat = nullptr;   // Sell::pat
+  unsigned char* rmask = nullptr;  // Sell::rmask
   Launch loop[6];
   bool loop_ok = true;    // every pair's k_loop configured (set while building)
   bool use_loop = false;
@@ -163,6 +166,8 @@ struct ampcg_ctx {
     A.v64 = v64;
     A.v32 = v32;
     A.stream_hint = stream_hint;
+    A.pat = idx16 ? pat : nullptr;
+    A.rmask = idx16 ? rmask : nullptr;
     return A;
   }
   Bufs bufs() const {
@@ -191,7 +196,7 @@ static void release(ampcg_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
   void* ptrs[] = {c->ah64, c->ah32, c->ah16, c->ahp, c->ds64, c->ds32, c->ds16, c->cres, c->cd0, c->cd1, c->cu,
-                  c->rowptr, c->off, c->width, c->cabs, c->coff, c->v64, c->v32, c->dinv64, c->dinv32,
+                  c->rowptr, c->off, c->width, c->cabs, c->coff, c->pat, c->rmask, c->v64, c->v32, c->dinv64, c->dinv32,
                   c->dinv16, c->x, c->b, c->r64, c->t, c->r32, c->z, c->p0, c->p1, c->q,
                   c->part, c->pmax, c->bar, c->st, c->dhist, c->phist};
   for (void* p : ptrs)
@@ -255,6 +260,27 @@ const char* ampcg_status_string(int s) {
 const char* ampcg_last_error(void) { return g_err.c_str(); }
 
 int64_t ampcg_rows(ampcg_t c) { return c ? c->n : -1; }
+
+ampcg_status ampcg_layout_stats(ampcg_t c, ampcg_layout* out) {
+  if (!c || !out) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  memset(out, 0, sizeof(*out));
+  out->n = c->n;
+  out->nslices = c->nslices;
+  out->stored = c->stored;
+  out->maxw = c->maxw;
+  out->idx16 = c->idx16;
+  out->stream_hint = c->stream_hint;
+  if (c->pat) {
+    std::vector<short> pat((size_t)c->nslices * kStageW);
+    std::vector<int> w((size_t)c->nslices);
+    CUDA_TRY(cudaMemcpyAsync(pat.data(), c->pat, pat.size() * sizeof(short), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(w.data(), c->width, w.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int64_t s = 0; s < c->nslices; ++s)
+      if (pat[(size_t)s * kStageW] != kNoPat) out->stored_uniform += 32ll * w[(size_t)s];
+  }
+  return AMPCG_OK;
+}
 
 void ampcg_destroy(ampcg_t c) {
   if (!c) return;
@@ -369,6 +395,7 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   CTRY(cudaMemcpyAsync(tot2, total, sizeof(tot2), cudaMemcpyDeviceToHost, s));
   CTRY(cudaStreamSynchronize(s));
   long long stored = tot2[0];
+  c->stored = stored;
   c->maxw = (int)tot2[1];
   {
     // the matrix (binary32 copy) and ~40 bytes per row of vectors would not
@@ -381,8 +408,13 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   TRY(dalloc(&c->v64, stored));
   TRY(dalloc(&c->v32, stored));
   int64_t rows_pad = c->nslices * 32;
+  if (c->idx16) {
+    TRY(dalloc(&c->pat, (size_t)c->nslices * kStageW));
+    TRY(dalloc(&c->rmask, (size_t)rows_pad));
+    k_slice_pattern<<<gs, kBlock, 0, s>>>(n, c->nslices, d_rp, d_ci, c->width, c->pat);
+  }
   k_fill_sell<<<(int)((rows_pad + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-      n, d_rp, d_ci, d_v, c->off, c->width, c->cabs, c->coff, c->v64, c->v32);
+      n, d_rp, d_ci, d_v, c->off, c->width, c->pat, c->cabs, c->coff, c->v64, c->v32, c->rmask);
   int64_t npad = (n + 63) / 64 * 64;  // per-row arrays: whole 8-element vectors in bounds
   TRY(dalloc(&c->dinv64, npad));
   TRY(dalloc(&c->dinv32, npad));

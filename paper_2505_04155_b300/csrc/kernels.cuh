@@ -145,7 +145,18 @@ struct Sell {
   const double* v64;
   const float* v32;
   int stream_hint;       // matrix larger than L2's share: staged loads marked evict-first
+  // slice-uniform offsets (int16 layout only, else null): pat[8 s + j] is the
+  // column offset of entry j of every row of slice s, or pat[8 s] = kNoPat
+  // when the rows of the slice differ (then coff holds them, as always)
+  const short* pat;
+  // uniform slices only: bit j of rmask[row] set iff entry j of the row is
+  // one of its stored CSR entries (the others are the added zeros)
+  const unsigned char* rmask;
 };
+constexpr short kNoPat = (short)-32768;
+__device__ __forceinline__ bool slice_uniform(const Sell& A, int64_t s) {
+  return A.pat != nullptr && A.pat[s * 8] != kNoPat;
+}
 
 // Scalar-side pieces of the algorithm, evaluated by one thread -------------
 
@@ -974,16 +985,22 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
   const int64_t s1 = gw * spw + spw < A.nslices ? gw * spw + spw : A.nslices;
   const bool hint = A.stream_hint != 0;
   const unsigned long long pol = hint ? l2_policy_evict_first() : 0ull;
+  // slice-uniform offsets (int16 layout): such a slice stages its values only
+  const bool upat = IT == 1 && A.pat != nullptr;
   // chunks of at most 32 slices (one header per lane); one chunk in the
   // single-system launch, whose grid gives every warp at most 32 slices
   for (int64_t s0 = gw * spw; s0 < s1; s0 += 32) {
     const int cnt = (int)(s1 - s0 < 32 ? s1 - s0 : 32);
     long long hoff = 0;
     int hw = 0;
+    uint4 hp = make_uint4(0u, 0u, 0u, 0u);   // the slice's 8 offsets, 2 per word
     if (lane < cnt) {
       hoff = __ldg(A.off + s0 + lane);
       hw = __ldg(A.width + s0 + lane);
+      if (upat) hp = __ldg(reinterpret_cast<const uint4*>(A.pat) + s0 + lane);
     }
+    const bool hu = upat && (short)(hp.x & 0xffffu) != kNoPat;
+    const unsigned umask = __ballot_sync(0xffffffffu, hu);   // bit t: slice s0 + t uniform
     auto issue = [&](int t) {
       if (t < cnt) {
         const long long o = __shfl_sync(0xffffffffu, hoff, t);
@@ -1002,7 +1019,7 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
         }
         const char* gi = (const char*)(ia + o);
         char* di = (char*)(si + stg * SE);
-        const int ni = 2 * w * (int)sizeof(TI);
+        const int ni = ((umask >> t) & 1u) ? 0 : 2 * w * (int)sizeof(TI);
   #pragma unroll
         for (int u = 0; u < (kStageW * (int)sizeof(TI) + 15) / 16; ++u) {
           const int c = lane + 32 * u;
@@ -1018,16 +1035,18 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
     for (int t = 0; t < K - 1; ++t) issue(t);
     // one row's product over a slice held in stage stg (w entries, w known at
     // compile time: no per-entry predicates)
-    auto rowprod = [&](auto wc, int stg, int64_t row, TR& acc) {
+    auto rowprod = [&](auto wc, int stg, int64_t row, TR& acc, bool uni, const uint4& pw) {
       constexpr int W = decltype(wc)::value;
       const TR* sa = sv + stg * SE + lane;
       const TI* sc = si + stg * SE + lane;
       TR a[W];
       int cc[W];
+      const unsigned pws[4] = {pw.x, pw.y, pw.z, pw.w};
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         a[j] = sa[32 * j];
-        cc[j] = IT ? (int)row + (int)sc[32 * j] : (int)sc[32 * j];
+        if (uni) cc[j] = (int)row + (int)(short)((pws[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+        else cc[j] = IT ? (int)row + (int)sc[32 * j] : (int)sc[32 * j];
       }
       TZ g[W];
 #pragma unroll
@@ -1057,6 +1076,14 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
     };
     // Invariant at the top of a trip at slice t: groups 0 .. t + K - 2 issued
     // (each issue commits one group, group i holding slice i in stage i % K).
+    auto pat_of = [&](int t) {
+      uint4 v;
+      v.x = __shfl_sync(0xffffffffu, hp.x, t);
+      v.y = __shfl_sync(0xffffffffu, hp.y, t);
+      v.z = __shfl_sync(0xffffffffu, hp.z, t);
+      v.w = __shfl_sync(0xffffffffu, hp.w, t);
+      return v;
+    };
     for (int t = 0; t < cnt;) {
       const int w0 = __shfl_sync(0xffffffffu, hw, t);
       const int w1 = __shfl_sync(0xffffffffu, hw, t + 1 < cnt ? t + 1 : t);
@@ -1065,10 +1092,12 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
         issue(t + K - 1);          // into the stage of slice t - 1 (consumed)
         cp_async_wait<K - 2>();    // slices t and t + 1 have landed
         __syncwarp();
+        const bool u0 = (umask >> t) & 1u, u1 = (umask >> (t + 1)) & 1u;
+        const uint4 p0 = upat ? pat_of(t) : hp, p1 = upat ? pat_of(t + 1) : hp;
         dispatch(w0, [&](auto wc) {
           TR acc0, acc1;
-          rowprod(wc, t % K, row, acc0);
-          rowprod(wc, (t + 1) % K, row + 32, acc1);
+          rowprod(wc, t % K, row, acc0, u0, p0);
+          rowprod(wc, (t + 1) % K, row + 32, acc1, u1, p1);
           finish(row, acc0);
           finish(row + 32, acc1);
         });
@@ -1079,10 +1108,12 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
         issue(t + K - 1);
         cp_async_wait<K - 1>();
         __syncwarp();
+        const bool u0 = (umask >> t) & 1u;
+        const uint4 p0 = upat ? pat_of(t) : hp;
         if (row < A.n) {
           dispatch(w0, [&](auto wc) {
             TR acc;
-            rowprod(wc, t % K, row, acc);
+            rowprod(wc, t % K, row, acc, u0, p0);
             finish(row, acc);
           });
         }
@@ -1749,9 +1780,47 @@ __global__ void k_slice_offsets(int64_t nslices, const int* width, long long* of
   for (int64_t i = a; i < b; ++i) { off[i] = run; run += 32ll * width[i]; }
 }
 
+// Slice-uniform offset patterns (int16 layout): a slice whose 32 rows (all
+// below n) have entries only at the offsets of one sorted set U with |U| equal
+// to the slice width, every r + u a valid column, is stored with entry j of
+// every row at offset U[j] (value 0 where the row has no entry there: the
+// row's products and their order are unchanged, the added terms are exact
+// zeros).  Its gathers then need U only (one 16-byte pattern per slice), not
+// the slice's offsets.  7-point stencils: every slice but the first and the
+// last.  One thread per slice.
+__global__ void k_slice_pattern(int64_t n, int64_t nslices, const int* rowptr, const int* col,
+                                const int* width, short* pat) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nslices) return;
+  const int w = width[s];
+  int u[kStageW];
+  int m = 0;
+  bool ok = w >= 1 && w <= kStageW && s * 32 + 32 <= n;
+  for (int l = 0; l < 32 && ok; ++l) {
+    const int64_t r = s * 32 + l;
+    for (int e = rowptr[r]; e < rowptr[r + 1] && ok; ++e) {
+      const int o = col[e] - (int)r;
+      int i = 0;
+      while (i < m && u[i] < o) ++i;
+      if (i < m && u[i] == o) continue;
+      if (m == w) { ok = false; break; }
+      for (int k = m; k > i; --k) u[k] = u[k - 1];
+      u[i] = o;
+      ++m;
+    }
+  }
+  ok = ok && m == w;
+  for (int i = 0; i < m && ok; ++i) {
+    const int64_t lo = s * 32 + u[i], hi = s * 32 + 31 + u[i];
+    ok = lo >= 0 && hi < n && u[i] >= -32767 && u[i] <= 32767;
+  }
+  for (int j = 0; j < kStageW; ++j) pat[s * kStageW + j] = (ok && j < m) ? (short)u[j] : (short)0;
+  if (!ok) pat[s * kStageW] = kNoPat;
+}
+
 __global__ void k_fill_sell(int64_t n, const int* rowptr, const int* col, const double* val,
-                            const long long* off, const int* width, int* cabs, short* coff,
-                            double* v64, float* v32) {
+                            const long long* off, const int* width, const short* pat, int* cabs,
+                            short* coff, double* v64, float* v32, unsigned char* rmask) {
   int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t s = row >> 5;
   int lane = (int)(row & 31);
@@ -1760,6 +1829,26 @@ __global__ void k_fill_sell(int64_t n, const int* rowptr, const int* col, const 
   long long base = off[s] + lane;
   int a = 0, len = 0;
   if (row < n) { a = rowptr[row]; len = rowptr[row + 1] - a; }
+  if (pat && pat[s * kStageW] != kNoPat) {
+    // uniform slice (every row < n): entry j at offset pat[j], merged with the
+    // row's sorted entries
+    int e = 0;
+    unsigned mk = 0u;
+    for (int j = 0; j < w; ++j) {
+      const int o = pat[s * kStageW + j];
+      double v = 0.0;
+      if (e < len && col[a + e] - (int)row == o) {
+        v = val[a + (e++)];
+        mk |= 1u << j;
+      }
+      const long long q = base + 32ll * j;
+      coff[q] = (short)o;
+      v64[q] = v;
+      v32[q] = __double2float_rn(v);
+    }
+    rmask[row] = (unsigned char)mk;
+    return;
+  }
   for (int j = 0; j < w; ++j) {
     long long e = base + 32ll * j;
     int c = (int)(row < n ? row : 0);
@@ -1821,9 +1910,15 @@ __global__ void k_update_vals(Sell A, const int* rowptr, const double* vals, dou
     int a = rowptr[row], len = rowptr[row + 1] - a;
     double dg = 0.0;
     int f = 0;
-    for (int j = 0; j < len; ++j) {
+    // entry j of the row holds CSR entry j, or (uniform slices) the next CSR
+    // entry when bit j of the row's mask is set
+    const bool uni = slice_uniform(A, s);
+    const unsigned mk = uni ? A.rmask[row] : 0u;
+    const int w = uni ? A.width[s] : len;
+    for (int j = 0, k = 0; j < w; ++j) {
+      if (uni && !((mk >> j) & 1u)) continue;
       long long e = base + 32ll * j;
-      double v = vals[a + j];
+      double v = vals[a + (k++)];
       if (!isfinite(v)) f |= 8;
       v64[e] = v;
       v32[e] = __double2float_rn(v);
@@ -1852,9 +1947,13 @@ __global__ void k_grad_pattern(Sell A, const int* rowptr, const double* lam, con
     long long base = A.off[s] + lane;
     int a = rowptr[row], len = rowptr[row + 1] - a;
     double li = lam[row];
-    for (int j = 0; j < len; ++j) {
+    const bool uni = slice_uniform(A, s);
+    const unsigned mk = uni ? A.rmask[row] : 0u;
+    const int w = uni ? A.width[s] : len;
+    for (int j = 0, k = 0; j < w; ++j) {
+      if (uni && !((mk >> j) & 1u)) continue;
       int c = col_at<IT>(A, base + 32ll * j, row);
-      dLdA[a + j] = -(li * x[c]);
+      dLdA[a + (k++)] = -(li * x[c]);
     }
   }
 }
@@ -1877,7 +1976,10 @@ __global__ void k_assemble_logcoeff(Sell A, const double* theta, const int* nb, 
     int w = A.width[s];
     double ti = theta[row], sum = 0.0;
     long long ed = -1;
+    const bool uni = slice_uniform(A, s);
+    const unsigned mk = uni ? A.rmask[row] : 0u;
     for (int j = 0; j < w; ++j) {
+      if (uni && !((mk >> j) & 1u)) continue;   // an added zero stays zero
       long long e = base + 32ll * j;
       int c = col_at<IT>(A, e, row);
       if (c == row) {
@@ -1918,7 +2020,10 @@ __global__ void k_grad_logcoeff(Sell A, const double* x, const double* lam, doub
     int w = A.width[s];
     double xi = x[row], li = lam[row], g = 0.0, rowsum = 0.0;
     bool seen_diag = false;
+    const bool uni = slice_uniform(A, s);
+    const unsigned mk = uni ? A.rmask[row] : 0u;
     for (int j = 0; j < w; ++j) {
+      if (uni && !((mk >> j) & 1u)) continue;
       long long e = base + 32ll * j;
       int c = col_at<IT>(A, e, row);
       double a = A.v64[e];

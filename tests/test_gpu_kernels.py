@@ -180,3 +180,44 @@ def test_selector_threshold_edges(crit, side, latch):
     want = oracle.selector_trace(delta, 1.0, tol, op)
     assert np.array_equal(got, want)
     assert (want[25] >> 4) == P.FP64 and (want[26] >> 4) == P.FP32
+
+
+def test_uniform_slice_layout():
+    # a 7-point stencil: nearly every slice holds its rows at one set of
+    # offsets (the added entries are exact zeros, so the
+    # products are unchanged); the staged SpMV of the solve reads those
+    # offsets once per slice.  PCG(FP64) through that layout follows the
+    # oracle's residual history.
+    a = W.diffusion3d(24, 2.0, 11)
+    s = P.Solver(a.rowptr, a.col, a.val)
+    lay = s.layout()
+    assert lay["idx16"] == 1 and lay["n"] == a.n and lay["nslices"] == (a.n + 31) // 32
+    assert 0 < lay["stored_uniform"] < lay["stored"]
+    # the rule, restated: 32 rows below n, the union of their offsets as large
+    # as the longest row, every row plus every offset a column of the matrix
+    want = 0
+    for sl in range(lay["nslices"]):
+        r0 = 32 * sl
+        if r0 + 32 > a.n:
+            continue
+        offs = [set((a.col[a.rowptr[r]:a.rowptr[r + 1]] - r).tolist()) for r in range(r0, r0 + 32)]
+        u = set().union(*offs)
+        w = max(len(o) for o in offs)
+        if len(u) == w and all(r0 + o >= 0 and r0 + 31 + o < a.n for o in u):
+            want += 32 * w
+    assert lay["stored_uniform"] == want
+    assert lay["stored"] - lay["stored_uniform"] <= 2 * 32 * 7     # first and last slice
+    b = np.random.default_rng(5).uniform(-1, 1, a.n)
+    x, info = s.solve(_dev(b), tol=1e-10, maxit=2000, policy=P.Policy.pcg64(), history=True)
+    ref = oracle.ampcg(a.rowptr, a.col, a.val, b, tol=1e-10, maxit=2000,
+                       policy=oracle.Policy(criterion=oracle.FIXED, fixed_uz=oracle.FP64,
+                                            fixed_ur=oracle.FP64, scale=oracle.SCALE_NONE))
+    assert abs(info.iters - ref.iters) <= 1
+    k = min(30, info.iters)
+    assert np.allclose(info.relres_hist[:k], ref.relres_hist[:k], rtol=1e-9, atol=0)
+    s.close()
+    # rows of irregular lengths: no slice is uniform
+    r = _varlen(200, 4)
+    s2 = P.Solver(r.rowptr, r.col, r.val)
+    assert s2.layout()["stored_uniform"] == 0
+    s2.close()
