@@ -135,19 +135,25 @@ def test_repeated_solves_are_deterministic():
         assert torch.equal(x, outs[0][0])
 
 
-@pytest.mark.parametrize("kind", ["amp16", "amp64_window", "cheb"])
+@pytest.mark.parametrize("kind", ["amp16", "amp64_window", "cheb", "wide_jacobi"])
 def test_loop_graph_equals_kernel_by_kernel(kind):
     # the loop graph (SWITCH per precision change, inner loop of chunks) runs
     # the same kernels in the same order as the host-driven launches, for any
-    # chunk length, including chunks that straddle a precision change or the stop
-    a = W.diffusion3d(20, 2.0, 6)
+    # chunk length, including chunks that straddle a precision change or the
+    # stop: the persistent iteration kernel (Jacobi, narrow slices), the
+    # Chebyshev sequence, and the sequence with the cooperative precondition
+    # + direction kernel (Jacobi, slices wider than 8)
+    if kind == "wide_jacobi":
+        a = W.elasticity_q1(7, seed=2).to_csr()
+    else:
+        a = W.diffusion3d(20, 2.0, 6)
     b = torch.as_tensor(W.rhs_uniform(a.n, 8), device="cuda")
     kw = dict(precond=P.M_CHEBYSHEV, degree=4) if kind == "cheb" else {}
     s = P.Solver(a.rowptr, a.col, a.val, **kw)
     pol = (P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3) if kind == "amp64_window"
            else P.Policy(verify_refresh=3))
     x0, i0 = s.solve(b, tol=TOL, maxit=5000, policy=pol, timed=True)
-    assert i0.converged and (kind == "cheb" or any(k >= 0 for k in i0.switch_iter))
+    assert i0.converged and (kind in ("cheb", "wide_jacobi") or any(k >= 0 for k in i0.switch_iter))
     for chunk in (1, 3, 16, 64):
         pol.graph_chunk = chunk
         x1, i1 = s.solve(b, tol=TOL, maxit=5000, policy=pol)
@@ -156,6 +162,25 @@ def test_loop_graph_equals_kernel_by_kernel(kind):
         assert np.array_equal(i1.prec_hist, i0.prec_hist)
         assert torch.equal(x1, x0)
     s.close()
+
+
+@pytest.mark.parametrize("variant", ["pcg64", "amp16"])
+def test_wide_rows_jacobi_matches_oracle(variant):
+    # Jacobi on rows wider than the staged SpMV's slices (Q1 elasticity, ~81
+    # entries per row): the kernel sequence with the cooperative precondition
+    # + direction kernel, against the oracle
+    a = W.elasticity_q1(7, seed=3).to_csr()
+    b = W.rhs_uniform(a.n, 4)
+    gp = P.Policy.pcg64() if variant == "pcg64" else P.Policy(verify_refresh=3)
+    x, info = _gpu_solve(a, b, gp, tol=1e-8)
+    ref = oracle.ampcg(a.rowptr, a.col, a.val, b, tol=1e-8, maxit=5000, policy=_opol(gp))
+    assert info.converged and ref.converged
+    if variant == "pcg64":
+        assert abs(info.iters - ref.iters) <= 1
+    else:
+        assert abs(info.iters - ref.iters) <= max(2, 0.05 * ref.iters)
+    t = oracle.residual64(a.rowptr, a.col, a.val, b, x)
+    assert np.linalg.norm(t) / np.linalg.norm(b) <= (1.01e-8 if variant == "pcg64" else 1e-8)
 
 
 def test_loop_graph_launch_count():
