@@ -61,42 +61,40 @@ __device__ __forceinline__ double to_f64(float v) { return f2d(v); }
 __device__ __forceinline__ double to_f64(__half v) { return h2d(v); }
 
 // ---------------------------------------------------------------------------
-// Round-to-nearest-even of v * 2^sc into binary16, from the IEEE 754
-// definition, with integer operations.  Valid for |sc| < 900 (binary64
-// subnormal inputs then lie far below binary16's range and give +-0).
+// Round-to-nearest-even of v * 2^sc into binary16.  Two steps: v * 2^sc is
+// rounded to binary32 with round-to-odd (truncate the 52-bit fraction to 23
+// bits and set the last bit when any discarded bit is set; 32-bit integer
+// operations), then the hardware converts binary32 to binary16 with
+// round-to-nearest-even.  Rounding to odd in a format with at least p + 2
+// digits followed by round-to-nearest into p digits equals direct
+// round-to-nearest (Boldo and Melquiond, "Emulation of FMA and correctly
+// rounded sums: proved algorithms using rounding to odd", IEEE Trans.
+// Computers 57, 2008); binary32 has 24 digits against binary16's 11.  Valid
+// for |sc| < 900 (binary64 subnormal inputs lie far below binary16's range
+// and give +-0).
 __device__ __forceinline__ __half d2h_scaled(double v, int sc) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  unsigned short s = (unsigned short)((b >> 48) & 0x8000u);
-  int E = (int)((b >> 52) & 0x7ffu);
-  unsigned long long M = b & 0x000FFFFFFFFFFFFFull;
-  unsigned short bits;
-  if (E == 0x7ff) {
-    bits = (unsigned short)(s | (M ? 0x7e00u : 0x7c00u));
-  } else if (E == 0) {
-    bits = s;
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned s = hi & 0x80000000u;
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  if (E == 0x7ff)
+    return __ushort_as_half((unsigned short)((s >> 16) | (((hi & 0xfffffu) | lo) ? 0x7e00u : 0x7c00u)));
+  if (E == 0) return __ushort_as_half((unsigned short)(s >> 16));
+  const int e = E - 1023 + sc;                  // v * 2^sc = 1.f * 2^e
+  if (e > 127) return __ushort_as_half((unsigned short)((s >> 16) | 0x7c00u));   // beyond binary32
+  if (e < -150) return __ushort_as_half((unsigned short)(s >> 16));              // below binary16's
+  const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned sticky = (lo & 0x1fffffffu) != 0u ? 1u : 0u;
+  unsigned f;
+  if (e >= -126) {
+    f = s | ((unsigned)(e + 127) << 23) | m23 | sticky;
   } else {
-    M |= 1ull << 52;                        // value = M * 2^(e - 52)
-    int e = E - 1023 + sc;
-    if (e > 15) {
-      bits = (unsigned short)(s | 0x7c00u);
-    } else {
-      int shift = (e >= -14) ? 42 : 28 - e; // bits below the binary16 quantum
-      unsigned q;
-      if (shift >= 54) {
-        q = 0u;                             // below half the smallest subnormal
-      } else {
-        unsigned long long qq = M >> shift;
-        unsigned long long rem = M & ((1ull << shift) - 1ull);
-        unsigned long long half = 1ull << (shift - 1);
-        if (rem > half || (rem == half && (qq & 1ull))) qq++;
-        q = (unsigned)qq;
-      }
-      unsigned r = (e >= -14) ? ((unsigned)(e + 14) << 10) + q : q;
-      if (r >= 0x7c00u) r = 0x7c00u;
-      bits = (unsigned short)(s | r);
-    }
+    // binary32 subnormal: shift the significand (hidden bit included) right
+    const int sh = -126 - e;                    // 1 .. 24
+    const unsigned full = (1u << 23) | m23;
+    const unsigned lost = (full & ((1u << sh) - 1u)) != 0u ? 1u : 0u;
+    f = s | (full >> sh) | sticky | lost;
   }
-  return __ushort_as_half(bits);
+  return __float2half_rn(__uint_as_float(f));
 }
 
 __device__ __forceinline__ __half d2h(double v) { return d2h_scaled(v, 0); }
