@@ -98,7 +98,8 @@ typedef struct {
   int fixed_ur;       /* FIXED criterion only: AMPCG_FP64 or AMPCG_FP32 */
   int graph_chunk;    /* iterations per chunk of the device-side loop: per launch of the
                          persistent iteration kernel (Jacobi or none), or per repeat of
-                         the kernel sequence (>= 1; 0 = default 16) */
+                         the kernel sequence (>= 1; 0 = automatic: 256 for the
+                         persistent kernel, 16 for the sequence) */
 } ampcg_policy;
 
 typedef struct {

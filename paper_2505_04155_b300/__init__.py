@@ -196,7 +196,7 @@ class Policy:
     verify_refresh: int = 0
     fixed_uz: int = FP64
     fixed_ur: int = FP64
-    graph_chunk: int = 16
+    graph_chunk: int = 0     # 0: automatic (256 with the persistent kernel, else 16)
 
     def to_c(self) -> PolicyC:
         return PolicyC(self.u0, self.criterion, self.d, self.ell, self.C, self.tau_zs, self.tau_zh,
