@@ -67,8 +67,8 @@ def config_dict(a, extra=None):
 # DRAM bytes (read + write) per launch (one iteration of k_loop) from one ncu
 # capture of the kernel as it is now (profiles/k_loop_diffusion128.md); a
 # kernel missing here reports null.
-NCU_TRAFFIC = {"amp:iteration:uz16_ur64": 169.7e6, "amp:iteration:uz16_ur32": 101.7e6,
-               "fp64:iteration:uz64_ur64": 215.6e6}
+NCU_TRAFFIC = {"amp:iteration:uz16_ur64": 169.9e6, "amp:iteration:uz16_ur32": 102.1e6,
+               "fp64:iteration:uz64_ur64": 216.7e6}
 
 
 def peaks():
