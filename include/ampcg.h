@@ -172,7 +172,9 @@ ampcg_status ampcg_update_values(ampcg_t ctx, const double* vals);
  * res (may be NULL) receives counts, final residuals, switch points and, when
  * its history pointers are set, the per-iteration residual and precision
  * histories.  Returns the solve's status (AMPCG_OK, AMPCG_NOT_CONVERGED,
- * AMPCG_ERR_BREAKDOWN, AMPCG_ERR_NONFINITE) or an error; x holds the last
+ * AMPCG_ERR_BREAKDOWN, AMPCG_ERR_NONFINITE) or an error (AMPCG_ERR_TIMEOUT:
+ * a bounded grid-barrier wait of the persistent iteration kernel ran out, a
+ * block never arrived; the solve stops instead of hanging); x holds the last
  * iterate in every non-error case.  Synchronises the context's stream. */
 ampcg_status ampcg_solve(ampcg_t ctx, const double* b, double* x, double tol, int maxit,
                          const ampcg_policy* policy, ampcg_result* res);
@@ -280,7 +282,9 @@ ampcg_status ampcg_residual(ampcg_t ctx, const double* b, const double* x, doubl
  * indicator chosen by policy->criterion, latching as in the policy) over a
  * given residual-norm sequence delta[0..m] (host array), as the solver
  * would at iterations k = 0..m; writes (u_z << 4) | u_r for each k into
- * out[m+1] (host).  nb = ||b||, tol as in ampcg_solve.  Synchronous. */
+ * out[m+1] (host).  nb = ||b||, tol as in ampcg_solve.  0 <= m < 2^28
+ * (AMPCG_ERR_INVALID_ARG otherwise, checked before any CUDA call).
+ * Synchronous; allocates its device scratch per call. */
 ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const double* delta, int m,
                                   double nb, double tol, uint8_t* out);
 
@@ -294,9 +298,12 @@ ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const double* delt
  * where cudaMalloc's implicit device synchronisation is not acceptable.
  *   - m + 1 must be at most 65536; larger m is rejected with
  *     AMPCG_ERR_INVALID_ARG and nothing is run.
- *   - The first call on a device (with that device current) looks up the
- *     array's device address once; make that first call before any stream
- *     capture.
+ *   - The first call in a device's context (with that device current)
+ *     looks up the array's device address and caches it with the context's
+ *     identity; a call in a later context of the device (after a reset of
+ *     its primary context) looks it up again.  Make the first call on each
+ *     device, and the first after a reset, before any stream capture.
+ *   - m + 1 is checked against the limit before any CUDA call.
  *   - All calls share the one array: calls that overlap on the GPU (for
  *     example from two host threads) race and must be serialised by the
  *     caller.  Each call writes everything it reads before reading it.
@@ -304,6 +311,21 @@ ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const double* delt
  * The paper has no counterpart to this entry point. */
 ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy, const double* delta, int m,
                                           double nb, double tol, uint8_t* out);
+
+/* Failure detection without a GPU fault (not from the paper).  Runs one grid
+ * barrier of the kind the persistent iteration kernel uses (every block
+ * publishes a partial, takes a ticket and polls the ticket counter with at
+ * most `spin_limit` polls per polling warp, then all blocks sum the partials)
+ * in a cooperative launch of `nblocks` blocks, 2 <= nblocks <= 64,
+ * 1 <= spin_limit <= 2^21 (about a second).  absent_block in [0, nblocks):
+ * that block returns without arriving, so the other blocks' waits run out;
+ * -1: every block arrives.  Returns AMPCG_OK when every arriving block
+ * passed the barrier with the correct grid sum; AMPCG_ERR_TIMEOUT when a
+ * wait ran out -- the status ampcg_solve returns when a barrier wait of its
+ * iteration kernel runs out; AMPCG_ERR_INVALID_ARG for bad arguments
+ * (checked before any CUDA call).  Allocates a few bytes of device memory;
+ * synchronous on the legacy default stream. */
+ampcg_status ampcg_barrier_check(int nblocks, int absent_block, long long spin_limit);
 
 /* Number of rows of the context's matrix, or -1 for NULL. */
 int64_t ampcg_rows(ampcg_t ctx);

@@ -133,6 +133,8 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_selector_trace_noalloc.argtypes = [C.POINTER(PolicyC), dp, C.c_int, C.c_double,
                                                  C.c_double, C.POINTER(C.c_uint8)]
     lib.ampcg_selector_trace_noalloc.restype = C.c_int
+    lib.ampcg_barrier_check.argtypes = [C.c_int, C.c_int, C.c_longlong]
+    lib.ampcg_barrier_check.restype = C.c_int
     lib.ampcg_rows.argtypes = [vp]
     lib.ampcg_rows.restype = i64
     lib.ampcg_layout_stats.argtypes = [vp, C.POINTER(LayoutC)]
@@ -453,3 +455,11 @@ def solve_batched(solvers, bs, xs, tol: float = 1e-10, maxit: int = 2000,
                              rh[: r.iters + 1].copy() if history else None,
                              ph[: r.iters].copy() if history else None))
     return out
+
+
+def barrier_check(nblocks: int = 2, absent_block: int = -1, spin_limit: int = 1 << 21) -> int:
+    """One bounded grid barrier of the iteration kernel's kind (ampcg_barrier_check):
+    returns OK when every arriving block passed, ERR_TIMEOUT when a wait ran out
+    (absent_block in [0, nblocks) never arrives).  Other statuses raise."""
+    return _check(load_library().ampcg_barrier_check(nblocks, absent_block, spin_limit),
+                  ok=(OK, ERR_TIMEOUT))

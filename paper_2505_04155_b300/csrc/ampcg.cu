@@ -9,6 +9,7 @@
 // of the current precision pair until the device sets `done`; then an FP64
 // true-residual launch and one read of the state block.  The host synchronises once per solve (plus once per optional
 // residual replacement).
+#include <cuda.h>   // driver types only (context identity); no driver library is linked
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -1066,6 +1067,9 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
     return fail(st, "internal error: device loop made no progress or ran a kernel for the wrong "
                 "precision pair (iteration %d)", iters);
   }
+  if (h.status == ST_TIMEOUT)
+    return fail(AMPCG_ERR_TIMEOUT, "a grid-barrier wait of the iteration kernel ran out at iteration %d "
+                "(a block never arrived)", iters);
   if (st != AMPCG_OK && st != AMPCG_NOT_CONVERGED)
     fail(st, "solve stopped at iteration %d: %s", iters, ampcg_status_string(st));
   return st;
@@ -1155,9 +1159,16 @@ extern "C" ampcg_status ampcg_precond_apply(ampcg_t c, int uz, int ur, double om
   return AMPCG_OK;
 }
 
+// Longest residual-norm sequence ampcg_selector_trace replays: delta[0..m]
+// with m < kTraceMax, so (m + 1) * sizeof(double) cannot overflow.
+constexpr int kTraceMax = 1 << 28;
+
 extern "C" ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const double* delta,
                                              int m, double nb, double tol, uint8_t* out) {
   if (!policy || !delta || !out || m < 0) return fail(AMPCG_ERR_INVALID_ARG, "bad argument");
+  if (m > kTraceMax - 1)
+    return fail(AMPCG_ERR_INVALID_ARG, "selector replay takes at most %d residual norms (m <= %d); got m = %d",
+                kTraceMax, kTraceMax - 1, m);
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();
@@ -1174,21 +1185,22 @@ extern "C" ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const d
   h.nb = nb;
   h.tol_nb = tol * nb;
   h.maxr = 1.0;
-  cudaError_t e = cudaMalloc(&d_delta, (m + 1) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&d_out, m + 1);
-  if (e == cudaSuccess) e = cudaMalloc(&d_ph, m + 1);
+  const size_t cnt = (size_t)m + 1;
+  cudaError_t e = cudaMalloc(&d_delta, cnt * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, cnt);
+  if (e == cudaSuccess) e = cudaMalloc(&d_ph, cnt);
   if (e == cudaSuccess) e = cudaMalloc(&d_st, sizeof(DevState));
   if (e == cudaSuccess) {
     h.delta_hist = d_delta;
     h.prec_hist = d_ph;
-    e = cudaMemcpy(d_delta, delta, (m + 1) * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(d_delta, delta, cnt * sizeof(double), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMemcpy(d_st, &h, sizeof(DevState), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     k_selector_trace<<<1, 32>>>(d_st, m, d_out);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, m + 1, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, cnt, cudaMemcpyDeviceToHost);
   cudaFree(d_delta);
   cudaFree(d_out);
   cudaFree(d_ph);
@@ -1206,8 +1218,10 @@ extern "C" ampcg_status ampcg_selector_trace(const ampcg_policy* policy, const d
 // callers that must not allocate device memory can use it.  Every GPU that
 // loads the library holds the array (kNoAllocTraceBytes) until process exit.
 // Host code cannot use the array's name as a device address: the address is
-// looked up per device with cudaGetSymbolAddress, on the first call made with
-// that device current, and cached.
+// looked up with cudaGetSymbolAddress on the first call made in a device's
+// context (that device current) and cached together with the context's
+// identity, so a call in a later context of the device (after a reset of its
+// primary context) looks the address up again instead of using a stale one.
 
 namespace {
 
@@ -1226,24 +1240,65 @@ static __device__ __align__(256) unsigned char g_noalloc_trace_scratch[kNoAllocT
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices] = {nullptr};
+struct NoAllocSlot {
+  unsigned long long ctx_id;  // identity of the context the address belongs to
+  void* addr;
+};
+NoAllocSlot g_noalloc[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set-up once per
-// device, with that device current).
+// Identity of the calling thread's current context (driver entry points
+// resolved through the runtime, so the library does not link the driver
+// library itself).  False when there is no current context or the driver
+// cannot tell; the caller then does not reuse a cached address.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+bool current_ctx_id(unsigned long long* id) {
+  static std::once_flag once;
+  static PfnCtxGetCurrent get_cur = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  std::call_once(once, []() {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = (PfnCtxGetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (PfnCtxGetId)f;
+    cudaGetLastError();
+  });
+  if (!get_cur || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array in the current device's context: looked
+// up once per context (with that device current) and cached.
 ampcg_status noalloc_scratch(NoAllocTraceScratch** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(AMPCG_ERR_UNSUPPORTED, "device index %d too large", dev);
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_trace_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(AMPCG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-    g_noalloc_addr[dev] = p;
+  unsigned long long id = 0;
+  NoAllocSlot& slot = g_noalloc[dev];
+  if (slot.addr && current_ctx_id(&id) && id == slot.ctx_id) {
+    *out = (NoAllocTraceScratch*)slot.addr;
+    return AMPCG_OK;
   }
-  *out = (NoAllocTraceScratch*)g_noalloc_addr[dev];
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_trace_scratch);   // makes the device's context current if needed
+  if (e != cudaSuccess || !p)
+    return fail(AMPCG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+  if (current_ctx_id(&id)) {
+    slot.ctx_id = id;
+    slot.addr = p;
+  } else {
+    slot.addr = nullptr;   // identity unknown: look the address up on every call
+  }
+  *out = (NoAllocTraceScratch*)p;
   return AMPCG_OK;
 }
 
@@ -1253,7 +1308,7 @@ extern "C" ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy,
                                                      const double* delta, int m, double nb,
                                                      double tol, uint8_t* out) {
   if (!policy || !delta || !out || m < 0) return fail(AMPCG_ERR_INVALID_ARG, "bad argument");
-  if (m + 1 > kNoAllocTraceMax)
+  if (m > kNoAllocTraceMax - 1)
     return fail(AMPCG_ERR_INVALID_ARG,
                 "selector replay without allocation takes at most %d residual norms (m <= %d); got m = %d",
                 kNoAllocTraceMax, kNoAllocTraceMax - 1, m);
@@ -1289,6 +1344,55 @@ extern "C" ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy,
   return AMPCG_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Failure detection of the grid barriers without a GPU fault: one barrier of
+// the kind the persistent iteration kernel uses, with a short caller-given
+// poll limit, optionally with one block that never arrives.
+
+extern "C" ampcg_status ampcg_barrier_check(int nblocks, int absent_block, long long spin_limit) {
+  if (nblocks < 2 || nblocks > 64) return fail(AMPCG_ERR_INVALID_ARG, "nblocks must be in [2, 64]");
+  if (absent_block < -1 || absent_block >= nblocks)
+    return fail(AMPCG_ERR_INVALID_ARG, "absent_block must be -1 or in [0, nblocks)");
+  if (spin_limit < 1 || spin_limit > kBarrierSpin)
+    return fail(AMPCG_ERR_INVALID_ARG, "spin_limit must be in [1, %lld]", kBarrierSpin);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(AMPCG_ERR_NO_DEVICE, "no CUDA device visible");
+  }
+  int coop = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return fail(AMPCG_ERR_UNSUPPORTED, "device has no cooperative launch");
+  GridSumBarrier* g = nullptr;
+  double* part = nullptr;
+  int* out = nullptr;
+  cudaError_t e = cudaMalloc(&g, sizeof(GridSumBarrier));
+  if (e == cudaSuccess) e = cudaMalloc(&part, 2 * (size_t)nblocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)nblocks * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g, 0, sizeof(GridSumBarrier));
+  if (e == cudaSuccess) e = cudaMemset(out, 0, (size_t)nblocks * sizeof(int));
+  std::vector<int> h(nblocks, 0);
+  if (e == cudaSuccess) {
+    void* args[5] = {&g, &part, &absent_block, &spin_limit, &out};
+    e = cudaLaunchCooperativeKernel((const void*)k_barrier_check, dim3(nblocks), dim3(256), args, 0, nullptr);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), out, (size_t)nblocks * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(g);
+  cudaFree(part);
+  cudaFree(out);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "barrier check: %s", cudaGetErrorString(e));
+  int passed = 0, timed_out = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    if (h[b] == 1) ++passed;
+    else if (h[b] == 0) ++timed_out;
+  }
+  if (timed_out > 0)
+    return fail(AMPCG_ERR_TIMEOUT, "grid barrier: %d of %d arriving blocks gave up after %lld polls",
+                timed_out, passed + timed_out, spin_limit);
+  return AMPCG_OK;
+}
 
 // ---------------------------------------------------------------------------
 // New values on the same pattern, and the adjoint solve.

@@ -441,7 +441,7 @@ constexpr int kPollers = 4;   // warps of a block polling a grid barrier (blocks
 template <int MODE>
 __device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* part, unsigned long long* pmax,
                                                     int& nb, double v, unsigned long long mx, double& tot,
-                                                    unsigned long long& mtot);
+                                                    unsigned long long& mtot, long long spin = kBarrierSpin);
 
 // Fixed-order sum of G partials (block g's value j at part[g*stride + j]) in
 // the last block; thread 0 gets the totals.  Thread t adds partials t, t + B,
@@ -517,12 +517,13 @@ __device__ __forceinline__ unsigned long long final_sum_max(const double* part, 
 }
 
 // v, mx: the block's partials, valid in thread 0; tot, mtot: the grid
-// totals, in every thread (MODE >= 1, MODE 2).
+// totals, in every thread (MODE >= 1, MODE 2).  spin: polls per polling warp
+// before the wait gives up.  The block passes the barrier when any of its
+// pollers saw it complete; it fails only when every poller ran out.
 template <int MODE>
 __device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* part, unsigned long long* pmax,
                                                     int& nb, double v, unsigned long long mx, double& tot,
-                                                    unsigned long long& mtot) {
-  __shared__ int s_ok;
+                                                    unsigned long long& mtot, long long spin) {
   __shared__ double s_tot;
   __shared__ unsigned long long s_max;
   const int half = (nb++ & 1) * (int)gridDim.x;
@@ -539,7 +540,6 @@ __device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* p
     const unsigned long long a = atomicAdd(&g->arrive, 1ull);
     s_target = (a / G + 1) * G;
     s_seen = 0;
-    s_ok = 1;
   }
   __syncthreads();
   // kPollers warps poll, started a quarter of a round trip apart, so that the
@@ -557,14 +557,13 @@ __device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* p
         s_seen = 1;
         break;
       }
-      if (it >= kBarrierSpin) {
-        s_ok = 0;
-        break;
-      }
+      if (it >= spin) break;
     }
     __threadfence();
   }
   __syncthreads();
+  const bool ok = s_seen != 0;
+  if (!ok) return false;   // uniform across the block: s_seen is read after the barrier
   if constexpr (MODE >= 1) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
@@ -597,7 +596,7 @@ __device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* p
     tot = s_tot;
     if constexpr (MODE == 2) mtot = s_max;
   }
-  return s_ok != 0;
+  return true;
 }
 
 }  // namespace ampcg

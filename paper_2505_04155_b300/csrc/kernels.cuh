@@ -28,7 +28,10 @@ namespace ampcg {
 enum { CRIT_WINDOW = 0, CRIT_LINEAR = 1, CRIT_FIXED = 2 };
 enum { SCALE_NONE = 0, SCALE_L2 = 1, SCALE_LINF_POW2 = 2 };
 enum { M_NONE = 0, M_JACOBI = 1, M_CHEBYSHEV = 2 };
-enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = -3, ST_NONFINITE = -4, ST_INTERNAL = -5 };
+// ST_TIMEOUT: a bounded grid-barrier wait ran out (every block of a cooperative
+// launch is resident, so this means a block never arrived)
+enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = -3, ST_NONFINITE = -4, ST_INTERNAL = -5,
+       ST_TIMEOUT = -7 };
 
 // Switch value for an iteration that must not run (solve finished): matches
 // no body of the SWITCH node, so nothing is launched.
@@ -868,7 +871,7 @@ __global__ void __launch_bounds__(256) k_precond_dir(Bufs B, int64_t n, DevState
     if (ok) {
       rho_step(&S, tot);
     } else {
-      S.status = ST_INTERNAL;
+      S.status = ST_TIMEOUT;
       S.done = 1;
     }
     S.phase_runs[2 * UZ + UR] += 1;
@@ -1551,7 +1554,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
     }
   }
   if (!ok && threadIdx.x == 0) {
-    S.status = ST_INTERNAL;
+    S.status = ST_TIMEOUT;
     S.done = 1;
   }
   if (blockIdx.x == 0) state_store(st, &S);
@@ -2358,6 +2361,24 @@ __global__ void __launch_bounds__(256) k_precond_step(Bufs B, int64_t n, const D
   double rho = 0.0;
   Dot2 d2;
   precond_rows<UZ, UR, MT, 1>(B, n, st, rho, d2);
+}
+
+// Failure-detection check of the grid barrier: a cooperative launch of
+// gridDim.x blocks meets at one grid_reduce_barrier with a caller-given poll
+// limit; block `absent` (if in range) returns without arriving, so the others'
+// wait runs out after `spin` polls and they report it.  out[b] = 1 when block b
+// passed the barrier, 0 when its wait ran out, -1 when it did not arrive.
+__global__ void __launch_bounds__(256) k_barrier_check(GridSumBarrier* g, double* part, int absent,
+                                                       long long spin, int* out) {
+  if ((int)blockIdx.x == absent) {
+    if (threadIdx.x == 0) out[blockIdx.x] = -1;
+    return;
+  }
+  int nb = 0;
+  double tot = 0.0;
+  unsigned long long mtot = 0ull;
+  const bool ok = grid_reduce_barrier<1>(g, part, nullptr, nb, 1.0, 0ull, tot, mtot, spin);
+  if (threadIdx.x == 0) out[blockIdx.x] = (ok && tot == (double)gridDim.x) ? 1 : 0;
 }
 
 // Selector replay over a residual-norm sequence (one thread).

@@ -87,3 +87,26 @@ def test_no_device_reports_status(lib):
     s = lib.ampcg_create_csr(C.byref(h), 1, 1, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, None, None)
     assert s == P.ERR_NO_DEVICE
     assert "device" in lib.ampcg_last_error().decode()
+
+
+def test_size_limits_are_checked_before_any_cuda_call(lib):
+    # m = INT_MAX would overflow (m + 1) in a size computation; both selector
+    # replays reject it before touching the device, so on a machine without a
+    # GPU the status is INVALID_ARG, not NO_DEVICE
+    import numpy as np
+    import paper_2505_04155_b300 as P
+    delta = np.ones(4)
+    out = np.zeros(4, dtype=np.uint8)
+    pol = P.Policy().to_c()
+    for name in ("ampcg_selector_trace", "ampcg_selector_trace_noalloc"):
+        st = getattr(lib, name)(C.byref(pol), delta.ctypes.data_as(C.POINTER(C.c_double)), 2**31 - 1,
+                                1.0, 1e-10, out.ctypes.data_as(C.POINTER(C.c_uint8)))
+        assert st == P.ERR_INVALID_ARG, name
+        assert "m <=" in lib.ampcg_last_error().decode()
+    assert not out.any()
+
+
+def test_barrier_check_rejects_bad_arguments_before_any_cuda_call(lib):
+    import paper_2505_04155_b300 as P
+    for args in ((1, -1, 100), (65, -1, 100), (4, 4, 100), (4, -2, 100), (4, 0, 0), (4, 0, 2**21 + 1)):
+        assert lib.ampcg_barrier_check(*args) == P.ERR_INVALID_ARG, args
