@@ -98,6 +98,8 @@ def _load():
         lib.oracle_scale_precond.argtypes = [i64, ip, ip, dp, C.c_int, C.c_int, C.c_int, C.c_double,
                                              dp, dp]
         lib.oracle_grad_log_coeff.argtypes = [i64, ip, ip, dp, dp, dp, dp]
+        lib.oracle_direction.argtypes = [i64, C.c_int, C.c_int, C.c_double, dp, dp]
+        lib.oracle_update_xr.argtypes = [i64, C.c_int, C.c_double, dp, dp, dp, dp]
         lib.oracle_scale_cheb.restype = C.c_int
         lib.oracle_scale_cheb.argtypes = [i64, ip, ip, dp, C.c_int, C.c_double, C.c_double, C.c_int,
                                           C.c_int, C.c_double, dp, dp]
@@ -222,6 +224,22 @@ def scale_cheb(rowptr, col, val, degree, lmin, lmax, uz, ur, omega, r):
                                    omega, _d(r), _d(z))
     assert st == 0
     return z
+
+
+def direction(uz, first, beta, z, p_prev):
+    """Alg. 3 search direction p = z + beta p_prev in u_z (p_prev rounded to u_z first)."""
+    z = _f64(z)
+    p = _f64(p_prev).copy()
+    _load().oracle_direction(z.size, uz, int(first), beta, _d(z), _d(p))
+    return p
+
+
+def update_xr(ur, alpha, p, q, x, r):
+    """Alg. 3 updates: returns (x + alpha p in FP64, r - alpha q in u_r)."""
+    p, q = _f64(p), _f64(q)
+    x, r = _f64(x).copy(), _f64(r).copy()
+    _load().oracle_update_xr(p.size, ur, alpha, _d(p), _d(q), _d(x), _d(r))
+    return x, r
 
 
 def grad_log_coeff(rowptr, col, val, x, lam):

@@ -437,6 +437,33 @@ int oracle_scale_cheb(int64_t n, const int32_t* rowptr, const int32_t* col,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Alg. 3 search direction p_k = z_k + beta_{k-1} p_{k-1} in u_z (R7).  p holds
+ * p_{k-1} in the precision of the previous iteration; it is first rounded to
+ * u_z (a u_z change).  FP64: one FP64 fma.  FP32/FP16: one binary32 fma with
+ * beta rounded to binary32, the result rounded once to u_z.  first: p_0 = z_0. */
+void oracle_direction(int64_t n, int uz, int first, double beta, const double* z, double* p) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (first) { p[i] = z[i]; continue; }
+    double pold = oracle_round(uz, p[i]);
+    if (uz == OR_FP64) p[i] = fma(beta, pold, z[i]);
+    else p[i] = oracle_round(uz, fma32(oracle_round32(beta), pold, z[i]));
+  }
+}
+
+/* Alg. 3 updates x_{k+1} = x_k + alpha p_k (FP64 fma; x is FP64) and
+ * r_{k+1} = r_k - alpha q_k in u_r: FP64 fma, or one binary32 fma with alpha
+ * rounded to binary32 and the result rounded to u_r (R7).                   */
+void oracle_update_xr(int64_t n, int ur, double alpha, const double* p, const double* q,
+                      double* x, double* r) {
+  for (int64_t i = 0; i < n; ++i) x[i] = fma(alpha, p[i], x[i]);
+  double alpha_r = oracle_round(ur == OR_FP64 ? OR_FP64 : OR_FP32, alpha);
+  for (int64_t i = 0; i < n; ++i) {
+    if (ur == OR_FP64) r[i] = fma(-alpha, q[i], r[i]);
+    else r[i] = oracle_round(ur, fma32(-alpha_r, q[i], r[i]));
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* PCG, Algorithm 1, native FP64, Jacobi or identity M.  Stops on the updated
  * residual ||r_{k+1}|| <= tol ||b||.  Returns iterations in res->iters.     */
 int oracle_pcg64(int64_t n, const int32_t* rowptr, const int32_t* col,
@@ -595,12 +622,7 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
     /* beta_{k-1} = rho_k/rho_{k-1}; p_k = z_k + beta p_{k-1} in u_z;
        p_{k-1} is first brought to u_z when u_z changed.                   */
     double beta = first ? 0.0 : rho / rho_prev;
-    for (int64_t i = 0; i < n; ++i) {
-      if (first) { p[i] = z[i]; continue; }
-      double pold = oracle_round(uz, p[i]);
-      if (uz == OR_FP64) p[i] = fma(beta, pold, z[i]);
-      else p[i] = oracle_round(uz, fma32(oracle_round32(beta), pold, z[i]));
-    }
+    oracle_direction(n, uz, first, beta, z, p);
     p_prec = uz;
     first = 0;
     /* q_k = A p_k in u_r (R7); gamma_k = q_k^T p_k (FP64) */
@@ -610,12 +632,7 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
     if (!(gamma > 0.0)) { status = OR_ERR_BREAKDOWN; break; }
     /* alpha_k, x_{k+1}, r_{k+1} */
     double alpha = rho / gamma;
-    for (int64_t i = 0; i < n; ++i) x[i] = fma(alpha, p[i], x[i]);
-    double alpha_r = oracle_round(ur == OR_FP64 ? OR_FP64 : OR_FP32, alpha);
-    for (int64_t i = 0; i < n; ++i) {
-      if (ur == OR_FP64) r[i] = fma(-alpha, q[i], r[i]);
-      else r[i] = oracle_round(ur, fma32(-alpha_r, q[i], r[i]));
-    }
+    oracle_update_xr(n, ur, alpha, p, q, x, r);
     ur_prev = ur; uz_prev = uz;
     rho_prev = rho;
     /* delta_{k+1} = ||r_{k+1}|| (FP64); max|r| for the next scale */
