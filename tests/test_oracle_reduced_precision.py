@@ -295,7 +295,7 @@ def test_spmv_crafted_ties(prec):
 def test_dot_is_a_recursive_binary64_sum(lo, hi):
     # (0, 0): terms of one magnitude, where rounding each product before the
     # add (no fma contraction) changes the sum's rounding every ~100 terms
-    rng = np.random.default_rng(7 + lo)
+    rng = np.random.default_rng(7 + abs(lo))
     a, b = spread(rng, 4000, lo, hi), spread(rng, 4000, lo, hi)
     s = F(0)
     for ai, bi in zip(a, b):
