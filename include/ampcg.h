@@ -273,6 +273,19 @@ ampcg_status ampcg_spmv(ampcg_t ctx, int prec, const void* p, void* q);
 ampcg_status ampcg_precond_apply(ampcg_t ctx, int uz, int ur, double omega, const void* r,
                                  void* z);
 
+/* The matrix product of Alg. 3 as the persistent iteration kernel computes
+ * it: q = A p with A's copy in u_r (FP64 or FP32 values, one fma per stored
+ * entry in ascending column order, accumulated in u_r) and p stored in u_z
+ * (double, float or IEEE half as uint16, widened exactly, or rounded to
+ * binary32 when u_z = FP64 and u_r = FP32), launched with that kernel's grid,
+ * shared-memory stages and per-warp slice runs, so the code path under test
+ * is the solve's own.  p: device array of n values in u_z; q: device array of
+ * n values in u_r.  gamma (host, may be NULL) receives q^T p accumulated as
+ * the iteration kernel does (per-block partials summed in block order).
+ * AMPCG_ERR_UNSUPPORTED for contexts that do not run that kernel (Chebyshev
+ * or slices wider than 8 entries).  Synchronises the context's stream. */
+ampcg_status ampcg_spmv_loop_step(ampcg_t ctx, int uz, int ur, const void* p, void* q, double* gamma);
+
 /* r = b - A x in FP64 (the initial residual of Alg. 3): per row, an FP64 fused multiply-add
  * chain over the stored entries in ascending column order, subtracted from
  * b.  Device arrays of doubles.  Asynchronous on the context's stream. */

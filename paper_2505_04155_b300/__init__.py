@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_spmv.restype = C.c_int
     lib.ampcg_precond_apply.argtypes = [vp, C.c_int, C.c_int, C.c_double, vp, vp]
     lib.ampcg_precond_apply.restype = C.c_int
+    lib.ampcg_spmv_loop_step.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.POINTER(C.c_double)]
+    lib.ampcg_spmv_loop_step.restype = C.c_int
     lib.ampcg_residual.argtypes = [vp, vp, vp, vp]
     lib.ampcg_residual.restype = C.c_int
     lib.ampcg_selector_trace.argtypes = [C.POINTER(PolicyC), dp, C.c_int, C.c_double, C.c_double,
@@ -391,6 +393,14 @@ class Solver:
         """q = A p in FP64 or FP32 (device arrays)."""
         _check(load_library().ampcg_spmv(self._h, prec, _ptr(p), _ptr(q)))
         return q
+
+    def spmv_loop_step(self, p, q, uz: int, ur: int) -> float:
+        """q = A p as the persistent iteration kernel computes it (its launch
+        shape and work split): p in u_z, q in u_r (device arrays); returns
+        gamma = q^T p as that kernel accumulates it (ampcg_spmv_loop_step)."""
+        g = C.c_double()
+        _check(load_library().ampcg_spmv_loop_step(self._h, uz, ur, _ptr(p), _ptr(q), C.byref(g)))
+        return g.value
 
     def precond_apply(self, r, z, uz: int, ur: int, omega: float = 1.0):
         """z = M^-1 round_uz(omega r) with r in u_r and z in u_z (device arrays)."""

@@ -1095,6 +1095,53 @@ extern "C" ampcg_status ampcg_spmv(ampcg_t c, int prec, const void* p, void* q) 
   return AMPCG_OK;
 }
 
+template <int UZ, int UR, int IT>
+static cudaError_t launch_spmv_loop_step(ampcg_ctx* c, const Bufs& B) {
+  const void* fn = (const void*)k_spmv_loop_step<UZ, UR, IT>;
+  const int smem = LoopStageCfg<UR, IT>::kBytes;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  Sell A = c->sell();
+  Bufs Bc = B;
+  DevState* st = c->st;
+  void* args[3] = {&A, &Bc, &st};
+  return cudaLaunchKernel(fn, dim3(c->loop[2 * UZ + UR].grid), dim3(kLoopBlock), args, (size_t)smem, c->stream);
+}
+
+template <int UZ, int UR>
+static cudaError_t spmv_loop_step_t(ampcg_ctx* c, const Bufs& B) {
+  return c->idx16 ? launch_spmv_loop_step<UZ, UR, 1>(c, B) : launch_spmv_loop_step<UZ, UR, 0>(c, B);
+}
+
+extern "C" ampcg_status ampcg_spmv_loop_step(ampcg_t c, int uz, int ur, const void* p, void* q,
+                                             double* gamma) {
+  if (!c || !p || !q) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  if (uz < 0 || uz > 2 || ur < 0 || ur > 1) return fail(AMPCG_ERR_INVALID_ARG, "bad precision");
+  if (!c->use_loop)
+    return fail(AMPCG_ERR_UNSUPPORTED, "the context does not run the persistent iteration kernel "
+                "(Chebyshev preconditioner or slices wider than %d)", kStageW);
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  Bufs B = c->bufs();
+  B.p[0] = const_cast<void*>(p);
+  B.p[1] = const_cast<void*>(p);
+  B.q = q;
+  cudaError_t e;
+  if (uz == P64) e = ur == P64 ? spmv_loop_step_t<P64, P64>(c, B) : spmv_loop_step_t<P64, P32>(c, B);
+  else if (uz == P32) e = ur == P64 ? spmv_loop_step_t<P32, P64>(c, B) : spmv_loop_step_t<P32, P32>(c, B);
+  else e = ur == P64 ? spmv_loop_step_t<P16, P64>(c, B) : spmv_loop_step_t<P16, P32>(c, B);
+  CUDA_TRY(e);
+  const int G = c->loop[2 * uz + ur].grid;
+  std::vector<double> part((size_t)G);
+  CUDA_TRY(cudaMemcpyAsync(part.data(), c->part, (size_t)G * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (gamma) {
+    double g = 0.0;
+    for (int i = 0; i < G; ++i) g += part[(size_t)i];
+    *gamma = g;
+  }
+  return AMPCG_OK;
+}
+
 extern "C" ampcg_status ampcg_residual(ampcg_t c, const double* b, const double* x, double* r) {
   if (!c || !b || !x || !r) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
   Sell A = c->sell();

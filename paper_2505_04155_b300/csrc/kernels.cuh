@@ -1560,6 +1560,29 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
   if (blockIdx.x == 0) state_store(st, &S);
 }
 
+// The staged SpMV of k_loop on its own, launched with k_loop's grid and
+// shared memory, so its work split (each warp a contiguous run of
+// ceil(nslices / warps) slices, LoopStageCfg stages per warp, the two-slice
+// overlapped trip, the L2 hint of the matrix stream) is the one the solve
+// runs: q = A p in u_r; part[b] = block b's partial of gamma = q^T p.  B.p[0]
+// and B.p[1] both hold p.  For parity tests of that code path.
+template <int UZ, int UR, int IT>
+__global__ void __launch_bounds__(kLoopBlock, 1) k_spmv_loop_step(Sell A, Bufs B, const DevState* st) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+  double gam = 0.0;
+  Dot2 d2;
+  spmv_rows_staged<UZ, UR, IT, LoopPart, LoopStageCfg<UR, IT>::K>(A, B, st, gam, d2, dsm);
+  double v[1];
+  if constexpr (kSmall) {
+    v[0] = block_sum_dot2(d2, 1.0);
+  } else {
+    v[0] = gam;
+    block_sum_wide<1>(v);
+  }
+  if (threadIdx.x == 0) B.part[blockIdx.x] = v[0];
+}
+
 // Loop graph control (one thread each).  The outer loop picks the precision
 // pair's body with a SWITCH; the body repeats chunks of that pair's
 // iterations in an inner loop while the pair stays current, so a SWITCH is

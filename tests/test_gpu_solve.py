@@ -10,8 +10,12 @@ trajectories agree to rounding, not bit for bit.  Bars:
     residual <= tol;
   - status codes for the failure modes (breakdown, non-finite input, maxit,
     invalid or non-SPD matrices)."""
+import functools
+
 import numpy as np
 import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 import oracle
 import workloads as W
@@ -40,6 +44,35 @@ def _opol(gp: "P.Policy"):
                          verify_refresh=gp.verify_refresh, fixed_uz=gp.fixed_uz, fixed_ur=gp.fixed_ur)
 
 
+def _kappa(a):
+    """2-norm condition number of A (extreme eigenvalues by Lanczos; the
+    smallest through shift-invert at 0, A being SPD)."""
+    m = sp.csr_matrix((a.val, a.col, a.rowptr), shape=(a.n, a.n))
+    lmax = spla.eigsh(m, k=1, which="LA", return_eigenvectors=False)[0]
+    lmin = spla.eigsh(m.tocsc(), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0]
+    return float(lmax / lmin)
+
+
+@functools.lru_cache(maxsize=None)
+def _problem(prob):
+    if prob == "poisson64":
+        a, b = W.poisson2d(64), W.rhs_uniform(4096, 0)
+    else:
+        a = W.diffusion3d(24, 2.0, 0)
+        b = W.rhs_uniform(a.n, 1)
+    return a, b, _kappa(a)
+
+
+def _x_error_ok(x, ref, kappa, relres_gpu):
+    """Solution error against the oracle's (reading R11): at most 1e-8, or the
+    bound kappa(A) (relres_gpu + relres_oracle) that two solutions with these
+    true residuals can be apart by."""
+    err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+    bound = max(1e-8, kappa * (relres_gpu + ref.true_relres))
+    assert err <= bound, (err, bound)
+    return err
+
+
 def test_pcg64_config1_matches_oracle():
     a = W.poisson2d(64)
     b = W.rhs_uniform(a.n, 0)
@@ -54,16 +87,16 @@ def test_pcg64_config1_matches_oracle():
     assert all(v == (P.FP64 << 4 | P.FP64) for v in info.prec_hist)
 
 
-@pytest.mark.parametrize("variant", ["amp16_linear", "amp16_window", "amp64_window", "amp_ur", "ds16"])
+@pytest.mark.parametrize("variant", ["amp16_linear", "amp16_window", "amp64_window", "amp_ur", "ds16",
+                                     "amp16_l2", "amp64_window_l2"])
 @pytest.mark.parametrize("prob", ["poisson64", "diffusion24"])
 def test_ampcg_matches_oracle(variant, prob):
-    if prob == "poisson64":
-        a, b = W.poisson2d(64), W.rhs_uniform(4096, 0)
-    else:
-        a = W.diffusion3d(24, 2.0, 0)
-        b = W.rhs_uniform(a.n, 1)
+    a, b, kappa = _problem(prob)
     gp = {
         "amp16_linear": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR),
+        # omega_k = 1/||r_k|| as printed in Alg. 3 (reading R5's paper-faithful mode)
+        "amp16_l2": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, scale=P.SCALE_L2),
+        "amp64_window_l2": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, scale=P.SCALE_L2),
         "amp16_window": P.Policy(u0=P.FP16, criterion=P.CRIT_WINDOW),
         "amp64_window": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW),
         "amp_ur": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, tau_zs=0.0, tau_zh=0.0),
@@ -79,6 +112,7 @@ def test_ampcg_matches_oracle(variant, prob):
         else:
             assert abs(info.switch_iter[j] - ref.switch_iter[j]) <= 2
     assert info.true_relres <= 2 * TOL * 1.5 or info.true_relres <= 2 * ref.true_relres
+    _x_error_ok(x, ref, kappa, info.true_relres)
     # the early trajectory agrees closely (reductions differ only in order)
     m = min(20, info.iters, ref.iters)
     np.testing.assert_allclose(info.relres_hist[:m], ref.relres_hist[:m], rtol=1e-6)
@@ -100,6 +134,37 @@ def test_first_iterations_close_to_oracle():
             assert info.iters == ref.iters == k
             assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) < 1e-12
             np.testing.assert_allclose(info.relres_hist, ref.relres_hist, rtol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def bench_system():
+    a = W.diffusion3d(128, 2.0, seed=0)
+    b = W.rhs_uniform(a.n, seed=1)
+    s = P.Solver(a.rowptr, a.col, a.val)
+    yield a, b, s
+    s.close()
+
+
+@pytest.mark.parametrize("which", ["amp16_linear", "phase2", "pcg64"])
+def test_first_iterations_at_benchmark_size(bench_system, which):
+    # the 128^3 benchmark system: every warp of the persistent kernel owns 14
+    # slices (two-slice trips, stage refills) and the matrix streams with the
+    # L2 evict-first hint; x and the residual history after 1, 2 and 5
+    # iterations agree with the oracle to rounding
+    a, b, s = bench_system
+    gp = {"amp16_linear": P.Policy(verify_refresh=3),
+          "phase2": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32),
+          "pcg64": P.Policy.pcg64()}[which]
+    assert s.layout()["stream_hint"] == 1
+    bd = torch.as_tensor(b, device="cuda")
+    for k in (1, 2, 5):
+        x, info = s.solve(bd, tol=TOL, maxit=k, policy=gp)
+        ref = oracle.ampcg(a.rowptr, a.col, a.val, b, tol=TOL, maxit=k, policy=_opol(gp))
+        assert info.iters == ref.iters == k
+        xg = x.cpu().numpy()
+        assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) < 1e-12
+        np.testing.assert_allclose(info.relres_hist, ref.relres_hist, rtol=1e-12)
+        assert np.array_equal(info.prec_hist, ref.prec_hist)
 
 
 def test_refresh_gives_fp64_verified_tolerance():
