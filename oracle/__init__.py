@@ -28,7 +28,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 
 FP64, FP32, FP16 = 0, 1, 2
 WINDOW, LINEAR, FIXED = 0, 1, 2
-SCALE_NONE, SCALE_L2, SCALE_LINF_POW2 = 0, 1, 2
+SCALE_NONE, SCALE_L2, SCALE_LINF_POW2, SCALE_LINF_POW2_LAG = 0, 1, 2, 3
 M_NONE, M_JACOBI, M_CHEBYSHEV = 0, 1, 2
 OK, NOT_CONVERGED, ERR_INVALID, ERR_BREAKDOWN, ERR_NONFINITE = 0, 1, -1, -3, -4
 
@@ -55,7 +55,8 @@ class _Policy(C.Structure):
 class _Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("converged", C.c_int),
                 ("refreshes", C.c_int), ("true_relres", C.c_double),
-                ("updated_relres", C.c_double), ("switch_iter", C.c_int * 3)]
+                ("updated_relres", C.c_double), ("switch_iter", C.c_int * 3),
+                ("scale_retries", C.c_int)]
 
 
 _lib = None
@@ -161,6 +162,7 @@ class Result:
     x: np.ndarray
     relres_hist: np.ndarray = field(repr=False)
     prec_hist: np.ndarray = field(repr=False)
+    scale_retries: int = 0
 
 
 def round16(v):
@@ -299,7 +301,7 @@ def _result(res, x, rh, ph):
     it = res.iters
     return Result(res.status, it, bool(res.converged), res.refreshes, res.true_relres,
                   res.updated_relres, tuple(res.switch_iter), x, rh[: it + 1].copy(),
-                  ph[:it].copy())
+                  ph[:it].copy(), res.scale_retries)
 
 
 def pcg64(rowptr, col, val, b, x0=None, tol=1e-10, maxit=2000, jacobi=True) -> Result:

@@ -28,6 +28,12 @@
  *   R5  scale modes: NONE (omega=1), L2 (omega = 1/delta_k as in Alg. 3),
  *       LINF_POW2 (omega = 2^-ceil(log2 max|r_k|), an exact power of two;
  *       Sec. 3.3 allows any nonzero omega).
+ *       LINF_POW2_LAG: the same power of two taken from the previous
+ *       iteration's residual, omega_k = 2^-ceil(log2 max|r_{k-1}|) for k >= 1
+ *       (omega_0 from r_0); Sec. 3.3 names a lagged factor (1/||z_{k-1}||)
+ *       as a practical choice.  If rho_k comes out non-finite (y overflowed
+ *       u_z because r grew), y_k, z_k and rho_k are formed once more with
+ *       omega_k = 2^-ceil(log2 max|r_k|)                        (R20)
  *   R6  y_i = round_uz( fl_ur(omega * r_i) ): one multiply, computed in u_r,
  *       stored in u_z.
  *   R7  FP16 quantities are computed in FP32 (with fma where the formula is a
@@ -59,6 +65,7 @@
 #define OR_SCALE_NONE 0
 #define OR_SCALE_L2 1
 #define OR_SCALE_LINF_POW2 2
+#define OR_SCALE_LINF_POW2_LAG 3
 
 #define OR_M_NONE 0
 #define OR_M_JACOBI 1
@@ -190,7 +197,7 @@ static void csr_diag(int64_t n, const int32_t* rowptr, const int32_t* col,
  * so max|omega r| lies in (0.5, 1].                                        */
 double oracle_scale(int mode, double delta, double maxabs) {
   if (mode == OR_SCALE_L2) return 1.0 / delta;
-  if (mode == OR_SCALE_LINF_POW2) {
+  if (mode == OR_SCALE_LINF_POW2 || mode == OR_SCALE_LINF_POW2_LAG) {
     if (!(maxabs > 0.0) || isinf(maxabs)) return 1.0;
     int E;
     double f = frexp(maxabs, &E);
@@ -279,6 +286,7 @@ typedef struct {
   double true_relres;
   double updated_relres;
   int switch_iter[3]; /* u_z -> FP32, u_z -> FP16, u_r -> FP32; -1 if none */
+  int scale_retries;  /* R20: iterations whose scaling was formed again */
 } oracle_result;
 
 /* Chebyshev data for M^-1 = D^-1/2 P(Ahat) D^-1/2 (see oracle_cheb_apply). */
@@ -571,6 +579,7 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
   double tol_nb = tol * nb;
   delta[0] = oracle_nrm2(n, r);
   double maxr = oracle_maxabs(n, r);
+  double maxr_prev = maxr;   /* max|r_{k-1}| (R20); r_0 for k = 0 */
   if (relres_hist) relres_hist[0] = delta[0] / nb;
   int status = OR_NOT_CONVERGED;
   if (!isfinite(nb) || !isfinite(delta[0])) status = OR_ERR_NONFINITE;
@@ -607,16 +616,24 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
     if (ur != ur_prev)
       for (int64_t i = 0; i < n; ++i) r[i] = oracle_round(ur, r[i]);
 
-    /* scaling: y_k = omega_k r_k, computed in u_r, stored in u_z (R5, R6) */
-    double omega = oracle_scale(pol->scale, delta[k], maxr);
-    scale_to_y(n, uz, ur, omega, r, y);
-    /* preconditioning: z_k = M^-1 y_k in u_z */
-    if (mtype == OR_M_CHEBYSHEV)
-      oracle_cheb_apply(n, rowptr, col, &ch, uz, y, z, w0, w1, w2, w3);
-    else
-      apply_precond(mtype, n, uz, dinv[uz], y, z);
-    /* rho_k = r_k^T z_k (FP64) */
-    double rho = oracle_dot(n, r, z);
+    /* scaling: y_k = omega_k r_k, computed in u_r, stored in u_z (R5, R6,
+       R20: the lagged mode takes max|r_{k-1}|, and max|r_k| on a retry) */
+    int lag = pol->scale == OR_SCALE_LINF_POW2_LAG;
+    double omega = oracle_scale(pol->scale, delta[k], lag ? maxr_prev : maxr);
+    double rho = 0.0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      scale_to_y(n, uz, ur, omega, r, y);
+      /* preconditioning: z_k = M^-1 y_k in u_z */
+      if (mtype == OR_M_CHEBYSHEV)
+        oracle_cheb_apply(n, rowptr, col, &ch, uz, y, z, w0, w1, w2, w3);
+      else
+        apply_precond(mtype, n, uz, dinv[uz], y, z);
+      /* rho_k = r_k^T z_k (FP64) */
+      rho = oracle_dot(n, r, z);
+      if (isfinite(rho) || !lag || attempt == 1) break;
+      omega = oracle_scale(OR_SCALE_LINF_POW2, delta[k], maxr);
+      res->scale_retries++;
+    }
     if (!isfinite(rho)) { status = OR_ERR_NONFINITE; break; }
     if (!(rho > 0.0)) { status = OR_ERR_BREAKDOWN; break; }
     /* beta_{k-1} = rho_k/rho_{k-1}; p_k = z_k + beta p_{k-1} in u_z;
@@ -637,6 +654,7 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
     rho_prev = rho;
     /* delta_{k+1} = ||r_{k+1}|| (FP64); max|r| for the next scale */
     delta[k + 1] = oracle_nrm2(n, r);
+    maxr_prev = maxr;
     maxr = oracle_maxabs(n, r);
     if (relres_hist) relres_hist[k + 1] = delta[k + 1] / nb;
     if (!isfinite(delta[k + 1])) { status = OR_ERR_NONFINITE; k++; break; }

@@ -94,14 +94,17 @@ def test_ampcg_fixed64_equals_alg1_bitwise():
     assert np.array_equal(amp.relres_hist, ref.relres_hist)
 
 
+@pytest.mark.parametrize("scale", [oracle.SCALE_LINF_POW2, oracle.SCALE_LINF_POW2_LAG])
 @pytest.mark.parametrize("prec", [oracle.FP64, oracle.FP32])
-def test_dspcg_pow2_scaling_is_bitwise_pcg(prec):
-    # Theorem 3.2: every DS-PCG quantity is PCG's times an exact power of two
+def test_dspcg_pow2_scaling_is_bitwise_pcg(prec, scale):
+    # Theorem 3.2: every DS-PCG quantity is PCG's times an exact power of two,
+    # whichever powers of two the omega_k are (the current or the previous
+    # iteration's max|r|, reading R20)
     a = W.diffusion3d(12, 1.0, 3)
     b = W.rhs_uniform(a.n, 2) * 1e3
     base = dict(criterion=oracle.FIXED, fixed_uz=prec, fixed_ur=prec, tol=1e-6)
     plain = _amp(a, b, scale=oracle.SCALE_NONE, **base)
-    scaled = _amp(a, b, scale=oracle.SCALE_LINF_POW2, **base)
+    scaled = _amp(a, b, scale=scale, **base)
     assert plain.iters == scaled.iters
     assert np.array_equal(plain.x, scaled.x)
     assert np.array_equal(plain.relres_hist, scaled.relres_hist)
@@ -142,3 +145,37 @@ def test_refresh_reaches_true_residual():
     assert fixed.converged
     assert fixed.true_relres <= 1e-10 or fixed.refreshes == 3
     assert fixed.iters >= plain.iters
+
+
+def _growth_system():
+    """A 2 x 2 SPD matrix on which one Jacobi-PCG step takes the residual norm
+    from 1 to 8.9e4, beyond binary16's 65504: draw 13211 (from 0) of a seeded
+    random family Q diag(e^u) Q^T scaled by D A D, b with spread magnitudes."""
+    rng = np.random.default_rng(1)
+    for _ in range(13212):
+        th = rng.uniform(0, np.pi)
+        ev = np.exp(rng.uniform(-12, 2, 2))
+        sc = np.exp(rng.uniform(-6, 6, 2))
+        b = rng.standard_normal(2) * np.exp(rng.uniform(-6, 0, 2))
+    q = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    m = q @ np.diag(ev) @ q.T
+    m = (m + m.T) / 2 * np.outer(sc, sc)
+    a = W.CSR(2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32), m.ravel().copy(), {})
+    return a, b
+
+
+def test_lagged_scale_retries_with_the_exact_power_after_overflow():
+    # reading R20: omega_1 from max|r_0| makes y_1 overflow binary16; rho_1 is
+    # then formed again with omega_1 = 2^-ceil(log2 max|r_1|), the non-lagged
+    # mode's omega_1, so both runs agree bit for bit (no binary16 subnormals
+    # occur here, so the different powers of two of iteration 0 change nothing)
+    a, b = _growth_system()
+    assert np.all(np.linalg.eigvalsh(a.val.reshape(2, 2)) > 0)
+    base = dict(criterion=oracle.FIXED, fixed_uz=oracle.FP16, fixed_ur=oracle.FP64, tol=1e-30,
+                maxit=2, precond=oracle.M_JACOBI)
+    lag = _amp(a, b, scale=oracle.SCALE_LINF_POW2_LAG, **base)
+    exact = _amp(a, b, scale=oracle.SCALE_LINF_POW2, **base)
+    assert lag.relres_hist[1] / lag.relres_hist[0] > 65504
+    assert lag.scale_retries == 1 and exact.scale_retries == 0
+    assert lag.status == exact.status == oracle.NOT_CONVERGED and lag.iters == 2
+    assert np.array_equal(lag.x, exact.x) and np.array_equal(lag.relres_hist, exact.relres_hist)
