@@ -231,6 +231,7 @@ def run_ours(args, rank, world):
     amp = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3)
     f64 = P.Policy.pcg64(verify_refresh=3)
     amp64w = P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3)   # the paper's general variant
+    amp_lag = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3, scale=P.SCALE_LINF_POW2_LAG)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -258,12 +259,14 @@ def run_ours(args, rank, world):
     timed(amp, args.warmup)
     timed(f64, args.warmup)
     timed(amp64w, args.warmup)
+    timed(amp_lag, args.warmup)
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
         amp_ms, amp_info, x_amp = timed(amp, args.steps)
         f64_ms, f64_info, x_64 = timed(f64, args.steps)
         w_ms, w_info, _ = timed(amp64w, args.steps)
+        lag_ms, lag_info, _ = timed(amp_lag, args.steps)
     barrier()
     clocks = clk.summary()
     t_amp, t_64, t_w = max_over_ranks([statistics.mean(amp_ms), statistics.mean(f64_ms), statistics.mean(w_ms)],
@@ -303,8 +306,11 @@ def run_ours(args, rank, world):
     # flushed before each, CUDA events around the solve
     FIXED_ITERS = 400
     graph_iter = {}
+    lagp = dict(scale=P.SCALE_LINF_POW2_LAG)
     for ph, pol in (("uz16_ur64", P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64)),
                     ("uz16_ur32", P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32)),
+                    ("uz16_ur64_lag", P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64, **lagp)),
+                    ("uz16_ur32_lag", P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32, **lagp)),
                     ("uz64_ur64", P.Policy.pcg64())):
         best = None
         for _ in range(3):
@@ -317,7 +323,7 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) * 1e3 / max(fi.iters, 1)
             best = t if best is None else min(best, t)
-        by = alg_bytes("iteration", ph, a.n, a.nnz, nslices, idx_bytes, uniform)
+        by = alg_bytes("iteration", ph[:9], a.n, a.nnz, nslices, idx_bytes, uniform)
         graph_iter[ph] = {"us": round(best, 2), "alg_bytes": int(by), "gbs": round(by / (best * 1e-6) / 1e9, 1),
                           "frac": round(by / (best * 1e-6) / 1e9 / peak, 3)}
 
@@ -342,7 +348,7 @@ def run_ours(args, rank, world):
         cpu = None
         if world == 1 and not args.no_cpu:
             _, cpu = cpu_oracle_sample(a, b, ia.iters)
-        launches = int(sum(i.kernel_launches for i in amp_info + f64_info + w_info))
+        launches = int(sum(i.kernel_launches for i in amp_info + f64_info + w_info + lag_info))
         out = {"metric": METRIC, "value": round(t_amp, 3), "unit": "ms", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_amp, 3),
                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -352,6 +358,8 @@ def run_ours(args, rank, world):
                "iters_amp": ia.iters, "iters_fp64": i64.iters, "refreshes_amp": ia.refreshes,
                "true_relres_amp": ia.true_relres, "true_relres_fp64": i64.true_relres,
                "switch_iter_amp": list(ia.switch_iter),
+               "amp_lag_ms": round(statistics.mean(lag_ms), 3), "iters_amp_lag": lag_info[-1].iters,
+               "switch_iter_amp_lag": list(lag_info[-1].switch_iter), "true_relres_amp_lag": lag_info[-1].true_relres,
                "amp64_window_ms": round(t_w, 3), "iters_amp64_window": w_info[-1].iters,
                "switch_iter_amp64_window": list(w_info[-1].switch_iter),
                "true_relres_amp64_window": w_info[-1].true_relres,

@@ -78,7 +78,16 @@ typedef enum {
 typedef enum {
   AMPCG_SCALE_NONE = 0,      /* omega = 1 (plain PCG) */
   AMPCG_SCALE_L2 = 1,        /* omega = 1/||r_k||, as printed in Alg. 3 */
-  AMPCG_SCALE_LINF_POW2 = 2  /* omega = 2^-ceil(log2 max|r_k|): exact, max|y| in (0.5, 1] */
+  AMPCG_SCALE_LINF_POW2 = 2, /* omega = 2^-ceil(log2 max|r_k|): exact, max|y| in (0.5, 1] */
+  AMPCG_SCALE_LINF_POW2_LAG = 3 /* omega_k = 2^-ceil(log2 max|r_{k-1}|) (k >= 1; omega_0 from r_0):
+                                 the previous iteration's power of two, a lagged factor as
+                                 Sec. 3.3 allows; if rho_k comes out non-finite (y_k overflowed
+                                 u_z), y_k, z_k and rho_k are formed again with
+                                 2^-ceil(log2 max|r_k|).  Known before delta_{k+1} is reduced,
+                                 so the persistent iteration kernel forms z_{k+1} and rho_{k+1}
+                                 in its update step (three grid barriers per iteration instead
+                                 of four).  Not with the Chebyshev preconditioner
+                                 (AMPCG_ERR_UNSUPPORTED). */
 } ampcg_scale;
 
 typedef struct {

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libampcg.so")
 
 FP64, FP32, FP16 = 0, 1, 2
 CRIT_WINDOW, CRIT_LINEAR, CRIT_FIXED = 0, 1, 2
-SCALE_NONE, SCALE_L2, SCALE_LINF_POW2 = 0, 1, 2
+SCALE_NONE, SCALE_L2, SCALE_LINF_POW2, SCALE_LINF_POW2_LAG = 0, 1, 2, 3
 M_NONE, M_JACOBI, M_CHEBYSHEV = 0, 1, 2
 
 OK, NOT_CONVERGED = 0, 1

@@ -26,8 +26,17 @@
 
 #include "../../include/ampcg.h"
 #include "batched.cuh"
+#include "kernel_table.h"
 
 using namespace ampcg;
+
+namespace ampcg {
+const void* loop_kernel(int uz, int ur, int mt, int it, bool fused) {
+  if (mt == M_JACOBI) return fused ? loop_kernel_jacobi_fused(uz, ur, it) : loop_kernel_jacobi_plain(uz, ur, it);
+  return fused ? loop_kernel_none_fused(uz, ur, it) : loop_kernel_none_plain(uz, ur, it);
+}
+const void* batched_kernel(int it) { return it ? batched_kernel_idx16() : batched_kernel_idx32(); }
+}  // namespace ampcg
 
 namespace {
 
@@ -129,9 +138,10 @@ struct ampcg_ctx {
   int64_t stored = 0;     // stored entries of the sliced layout
   short* pat = nullptr;   // Sell::pat
   unsigned char* rmask = nullptr;  // Sell::rmask
-  Launch loop[6];
+  Launch loop[2][6];      // [fused][pair]: four or three grid barriers per iteration
   bool loop_ok = true;    // every pair's k_loop configured (set while building)
   bool use_loop = false;
+  bool fused = false;     // the current solve's scale mode lets k_loop fuse (SCALE_NONE, LINF_POW2_LAG)
   // Chebyshev preconditioner data (reading R8)
   int cheb_m = 0;
   int cheb_auto = 0;            // interval from the Gershgorin bound
@@ -157,6 +167,7 @@ struct ampcg_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_chunk = 0;
+  bool graph_fused = false;
 
   Sell sell() const {
     Sell A;
@@ -463,7 +474,8 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   for (int ph = 0; ph < 6; ++ph) {
     for (const Launch& L : c->seq[ph])
       if (L.grid > c->g_max) c->g_max = L.grid;
-    if (c->use_loop && c->loop[ph].grid > c->g_max) c->g_max = c->loop[ph].grid;
+    for (int f = 0; f < 2; ++f)
+      if (c->use_loop && c->loop[f][ph].grid > c->g_max) c->g_max = c->loop[f][ph].grid;
   }
   int gi = occ_grid((const void*)k_init<0>, sms, rows_pad);
   if (gi > c->g_max) c->g_max = gi;
@@ -599,20 +611,22 @@ static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
       // the whole iteration loop in one cooperative launch, one block of
       // kLoopBlock threads per SM (a context whose pairs cannot all be
       // configured keeps the kernel sequences)
-      const void* fn = (const void*)k_loop<UZ, UR, MT, IT>;
-      const int lsm = LoopStageCfg<UR, IT>::kBytes;
-      int per_sm = 0;
-      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLoopBlock, lsm) != cudaSuccess ||
-          per_sm < 1) {
-        cudaGetLastError();
-        c->loop_ok = false;
-      } else {
-        Launch L;
-        L.fn = fn; L.kind = KA_LOOP; L.slot = 0; L.j = 0; L.c1 = 0; L.c2 = 0; L.smem = lsm; L.coop = true;
-        L.block = kLoopBlock;
-        L.grid = occ_grid(fn, sms, c->nslices * 32, lsm, kLoopBlock);
-        c->loop[2 * UZ + UR] = L;
+      for (int f = 0; f < 2; ++f) {
+        const void* fn = loop_kernel(UZ, UR, MT, IT, f != 0);
+        const int lsm = LoopStageCfg<UR, IT>::kBytes;
+        int per_sm = 0;
+        if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lsm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLoopBlock, lsm) != cudaSuccess ||
+            per_sm < 1) {
+          cudaGetLastError();
+          c->loop_ok = false;
+        } else {
+          Launch L;
+          L.fn = fn; L.kind = KA_LOOP; L.slot = 0; L.j = 0; L.c1 = 0; L.c2 = 0; L.smem = lsm; L.coop = true;
+          L.block = kLoopBlock;
+          L.grid = occ_grid(fn, sms, c->nslices * 32, lsm, kLoopBlock);
+          c->loop[f][2 * UZ + UR] = L;
+        }
       }
     } else {
       c->loop_ok = false;
@@ -726,7 +740,7 @@ struct ArgPack {
 // The launches of one iteration of phase ph: k_loop (one iteration) where it
 // applies, else the phase's kernel sequence.
 static std::vector<Launch> iteration_launches(const ampcg_ctx* c, int ph) {
-  if (c->use_loop) return {c->loop[ph]};
+  if (c->use_loop) return {c->loop[c->fused ? 1 : 0][ph]};
   return c->seq[ph];
 }
 
@@ -774,7 +788,7 @@ static cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const c
 // chunk, the chunk's remaining launches return at entry (phase_mismatch,
 // done).
 static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
-  if (c->gexec && c->graph_chunk == chunk) return AMPCG_OK;
+  if (c->gexec && c->graph_chunk == chunk && c->graph_fused == c->fused) return AMPCG_OK;
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
   CUDA_TRY(cudaGraphCreate(&c->graph, 0));
@@ -840,6 +854,7 @@ static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
   CUDA_TRY(add_kernel_node(&cnode, body, &snode, (const void*)k_loop_ctl, 1, 1, actl));
   CUDA_TRY(cudaGraphInstantiate(&c->gexec, c->graph, 0));
   c->graph_chunk = chunk;
+  c->graph_fused = c->fused;
   return AMPCG_OK;
 }
 
@@ -848,7 +863,7 @@ static ampcg_status check_policy(const ampcg_policy* p) {
       p->fixed_ur > 1)
     return fail(AMPCG_ERR_INVALID_ARG, "precision codes: u0/fixed_uz in {0,1,2}, fixed_ur in {0,1}");
   if (p->criterion < 0 || p->criterion > 2) return fail(AMPCG_ERR_INVALID_ARG, "bad criterion");
-  if (p->scale < 0 || p->scale > 2) return fail(AMPCG_ERR_INVALID_ARG, "bad scale mode");
+  if (p->scale < 0 || p->scale > 3) return fail(AMPCG_ERR_INVALID_ARG, "bad scale mode");
   if (p->d < 0 || p->ell < 1 || p->d > kRing - 2 || p->ell > kRing - 1)
     return fail(AMPCG_ERR_INVALID_ARG, "need 0 <= d <= %d and 1 <= ell <= %d", kRing - 2, kRing - 1);
   if (p->verify_refresh < 0 || p->graph_chunk < 0)
@@ -940,11 +955,17 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   else ampcg_policy_default(&pol);
   ampcg_status ps = check_policy(&pol);
   if (ps != AMPCG_OK) return ps;
+  if (pol.scale == AMPCG_SCALE_LINF_POW2_LAG && c->mtype == M_CHEBYSHEV)
+    return fail(AMPCG_ERR_UNSUPPORTED, "the lagged scale is not offered with the Chebyshev preconditioner "
+                "(use AMPCG_SCALE_LINF_POW2)");
   // default chunk: long for the persistent kernel (a launch ends at the stop
   // or a precision change anyway; 256 measured 0.8 ms faster than 16 on the
   // 128^3 solves), short for the kernel sequence (its launches after the stop
   // return at entry but still cost a launch each)
   int chunk = pol.graph_chunk > 0 ? pol.graph_chunk : (c->use_loop ? kLoopChunk : kSeqChunk);
+  // the persistent kernel's three-barrier form where omega_{k+1} is known
+  // before delta_{k+1} is reduced
+  c->fused = pol.scale == AMPCG_SCALE_NONE || pol.scale == AMPCG_SCALE_LINF_POW2_LAG;
   cudaSetDevice(c->device);
   cudaStream_t s = s_override ? s_override : c->stream;
   ampcg_status hs = ensure_hist(c, maxit);
@@ -1097,7 +1118,7 @@ extern "C" ampcg_status ampcg_spmv(ampcg_t c, int prec, const void* p, void* q) 
 
 template <int UZ, int UR, int IT>
 static cudaError_t launch_spmv_loop_step(ampcg_ctx* c, const Bufs& B) {
-  const void* fn = (const void*)k_spmv_loop_step<UZ, UR, IT>;
+  const void* fn = loop_spmv_kernel(UZ, UR, IT);
   const int smem = LoopStageCfg<UR, IT>::kBytes;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -1105,7 +1126,7 @@ static cudaError_t launch_spmv_loop_step(ampcg_ctx* c, const Bufs& B) {
   Bufs Bc = B;
   DevState* st = c->st;
   void* args[3] = {&A, &Bc, &st};
-  return cudaLaunchKernel(fn, dim3(c->loop[2 * UZ + UR].grid), dim3(kLoopBlock), args, (size_t)smem, c->stream);
+  return cudaLaunchKernel(fn, dim3(c->loop[0][2 * UZ + UR].grid), dim3(kLoopBlock), args, (size_t)smem, c->stream);
 }
 
 template <int UZ, int UR>
@@ -1130,7 +1151,7 @@ extern "C" ampcg_status ampcg_spmv_loop_step(ampcg_t c, int uz, int ur, const vo
   else if (uz == P32) e = ur == P64 ? spmv_loop_step_t<P32, P64>(c, B) : spmv_loop_step_t<P32, P32>(c, B);
   else e = ur == P64 ? spmv_loop_step_t<P16, P64>(c, B) : spmv_loop_step_t<P16, P32>(c, B);
   CUDA_TRY(e);
-  const int G = c->loop[2 * uz + ur].grid;
+  const int G = c->loop[0][2 * uz + ur].grid;
   std::vector<double> part((size_t)G);
   CUDA_TRY(cudaMemcpyAsync(part.data(), c->part, (size_t)G * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1416,7 +1437,7 @@ extern "C" ampcg_status ampcg_barrier_check(int nblocks, int absent_block, long 
   double* part = nullptr;
   int* out = nullptr;
   cudaError_t e = cudaMalloc(&g, sizeof(GridSumBarrier));
-  if (e == cudaSuccess) e = cudaMalloc(&part, 2 * (size_t)nblocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&part, 4 * (size_t)nblocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)nblocks * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g, 0, sizeof(GridSumBarrier));
   if (e == cudaSuccess) e = cudaMemset(out, 0, (size_t)nblocks * sizeof(int));
@@ -1745,7 +1766,7 @@ static ampcg_status batched_persistent(const std::vector<int>& idx, ampcg_t cons
       int* dcnt = (int*)(dev + off_cnt) + g;
       first += cnt;
       if (cnt == 0) continue;
-      const void* kern = g ? (const void*)k_batched<1> : (const void*)k_batched<0>;
+      const void* kern = batched_kernel(g);
       const int smem = g ? batch_smem_bytes<1>() : batch_smem_bytes<0>();
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) break;
@@ -1755,9 +1776,8 @@ static ampcg_status batched_persistent(const std::vector<int>& idx, ampcg_t cons
         per_sm = 1;
       }
       const int grid = sms * per_sm < cnt ? sms * per_sm : cnt;
-      if (g) k_batched<1><<<grid, kBatchBlock, smem, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
-      else k_batched<0><<<grid, kBatchBlock, smem, s>>>(dsys, dord, cnt, dcnt, dtmp, vr, dout);
-      e = cudaGetLastError();
+      void* kargs[7] = {&dsys, &dord, const_cast<int*>(&cnt), &dcnt, &dtmp, const_cast<int*>(&vr), &dout};
+      e = cudaLaunchKernel(kern, dim3(grid), dim3(kBatchBlock), kargs, (size_t)smem, s);
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out.data(), dev + off_out, sizeof(BatchOut) * m, cudaMemcpyDeviceToHost, s);

@@ -69,8 +69,9 @@ template <int UZ, int UR, int MT, int IT>
 __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int64_t n, DevState* S,
                                               unsigned char* dsm) {
   using Part = TeamPart;
-  // Alg. 3: scale, precondition, rho_k and beta
-  {
+  // Alg. 3: scale, precondition, rho_k and beta (a second pass only when the
+  // lagged scale made rho_k non-finite, reading R20)
+  for (int attempt = 0; attempt < 2; ++attempt) {
     double rho = 0.0;
     Dot2 d2;
     precond_and_cast<UZ, UR, MT, 8, Part>(B, n, S, rho, d2);
@@ -81,13 +82,13 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
       v[0] = rho;
       block_sum_wide<1>(v);
     }
-    if (threadIdx.x == 0) {
-      S->phase_runs[2 * UZ + UR] += 1;
-      rho_step(S, v[0]);
-    }
+    if (threadIdx.x == 0) rho_step(S, v[0]);
     __syncthreads();
-    if (S->done) return;
+    if (!S->redo) break;
   }
+  if (threadIdx.x == 0) S->phase_runs[2 * UZ + UR] += 1;
+  __syncthreads();
+  if (S->done) return;
   // Alg. 3: search direction (p_k is read by other threads' gathers)
   axpy_rows<UZ, 8, Part>(B, n, S);
   __syncthreads();

@@ -233,6 +233,11 @@ __device__ __forceinline__ void vst(T* __restrict__ p, const T (&o)[V], int m) {
       for (int j = 0; j < NQ; ++j) reinterpret_cast<uint4*>(p)[j] = reinterpret_cast<const uint4*>(o)[j];
       return;
     }
+  } else if constexpr (V > 1 && V * sizeof(T) == 8) {
+    if (m == V) {
+      *reinterpret_cast<uint2*>(p) = *reinterpret_cast<const uint2*>(o);
+      return;
+    }
   }
 #pragma unroll
   for (int j = 0; j < V; ++j)
@@ -428,9 +433,10 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
 // it before each solve.  A wait that runs out after kBarrierSpin polls (about
 // a second; it cannot happen with every block resident) returns false in
 // every thread of the block instead of hanging.  The partials alternate
-// between two halves of part/pmax (2 * gridDim.x entries each), selected by
-// the launch's barrier count `nb`: a block that has passed barrier j may
-// publish for barrier j + 1 while another still reads barrier j's partials.
+// between two halves of part (2 * gridDim.x doubles each) and of pmax
+// (gridDim.x each), selected by the launch's barrier count `nb`: a block that
+// has passed barrier j may publish for barrier j + 1 while another still
+// reads barrier j's partials.
 struct GridSumBarrier {
   unsigned long long arrive;   // tickets taken
   unsigned long long pad[3];
@@ -438,10 +444,10 @@ struct GridSumBarrier {
 constexpr long long kBarrierSpin = 1ll << 21;
 constexpr int kPollers = 4;   // warps of a block polling a grid barrier (blocks of >= 128 threads)
 
-template <int MODE>
-__device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* part, unsigned long long* pmax,
-                                                    int& nb, double v, unsigned long long mx, double& tot,
-                                                    unsigned long long& mtot, long long spin = kBarrierSpin);
+template <int NSUM, bool MAX>
+__device__ __forceinline__ bool grid_barrier_sums(GridSumBarrier* g, double* part, unsigned long long* pmax,
+                                                  int& nb, const double* v, unsigned long long mx, double* tot,
+                                                  unsigned long long& mtot, long long spin);
 
 // Fixed-order sum of G partials (block g's value j at part[g*stride + j]) in
 // the last block; thread 0 gets the totals.  Thread t adds partials t, t + B,
@@ -516,25 +522,32 @@ __device__ __forceinline__ unsigned long long final_sum_max(const double* part, 
   return block_max(m);
 }
 
-// v, mx: the block's partials, valid in thread 0; tot, mtot: the grid
-// totals, in every thread (MODE >= 1, MODE 2).  spin: polls per polling warp
-// before the wait gives up.  The block passes the barrier when any of its
-// pollers saw it complete; it fails only when every poller ran out.
-template <int MODE>
-__device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* part, unsigned long long* pmax,
-                                                    int& nb, double v, unsigned long long mx, double& tot,
-                                                    unsigned long long& mtot, long long spin) {
-  __shared__ double s_tot;
+// Grid barrier with NSUM grid-wide sums (0, 1 or 2 per block, v[j] valid in
+// thread 0; block g's partial j at part[parity * 2G + g * NSUM + j], parity =
+// the barrier's count in the launch mod 2; part holds 4G doubles) and, with
+// MAX, the grid-wide maximum of the blocks' mx; tot[j] and mtot end up in
+// every thread.  spin: polls per polling warp before the wait gives up.  The
+// block passes the barrier when any of its pollers saw it complete; it fails
+// only when every poller ran out.
+template <int NSUM, bool MAX>
+__device__ __forceinline__ bool grid_barrier_sums(GridSumBarrier* g, double* part, unsigned long long* pmax,
+                                                  int& nb, const double* v, unsigned long long mx, double* tot,
+                                                  unsigned long long& mtot, long long spin) {
+  static_assert(NSUM >= 0 && NSUM <= 2, "0, 1 or 2 sums");
+  __shared__ double s_tot[2];
   __shared__ unsigned long long s_max;
-  const int half = (nb++ & 1) * (int)gridDim.x;
-  if constexpr (MODE >= 1) part += half;
-  if constexpr (MODE == 2) pmax += half;
+  // consecutive barriers use disjoint halves of 2G entries each (2 G doubles
+  // for up to two sums per block), whatever their number of sums
+  const int parity = nb++ & 1;
+  if constexpr (NSUM >= 1) part += parity * 2 * (int)gridDim.x;
+  if constexpr (MAX) pmax += parity * (int)gridDim.x;
   __shared__ unsigned long long s_target;
   __shared__ volatile int s_seen;
   __syncthreads();
   if (threadIdx.x == 0) {
-    if constexpr (MODE >= 1) part[blockIdx.x] = v;
-    if constexpr (MODE == 2) pmax[blockIdx.x] = mx;
+#pragma unroll
+    for (int j = 0; j < NSUM; ++j) part[blockIdx.x * NSUM + j] = v[j];
+    if constexpr (MAX) pmax[blockIdx.x] = mx;
     __threadfence();
     const unsigned long long G = gridDim.x;
     const unsigned long long a = atomicAdd(&g->arrive, 1ull);
@@ -564,39 +577,58 @@ __device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* p
   __syncthreads();
   const bool ok = s_seen != 0;
   if (!ok) return false;   // uniform across the block: s_seen is read after the barrier
-  if constexpr (MODE >= 1) {
+  if constexpr (NSUM >= 1 || MAX) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
       const int G = gridDim.x;
-      double t = 0.0;
+      double t[2] = {0.0, 0.0};
       unsigned long long m = 0ull;
-      for (int i0 = lane; i0 < G; i0 += 32 * 8) {
-        double pv[8];
-        unsigned long long pw[8];
+      constexpr int U = NSUM == 2 ? 4 : 8;   // loads in flight per lane
+      for (int i0 = lane; i0 < G; i0 += 32 * U) {
+        double pv[U][2];
+        unsigned long long pw[U];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
           const int i = i0 + 32 * u;
-          pv[u] = i < G ? __ldcg(part + i) : 0.0;
-          if constexpr (MODE == 2) pw[u] = i < G ? __ldcg(pmax + i) : 0ull;
+#pragma unroll
+          for (int j = 0; j < NSUM; ++j) pv[u][j] = i < G ? __ldcg(part + (size_t)i * NSUM + j) : 0.0;
+          if constexpr (MAX) pw[u] = i < G ? __ldcg(pmax + i) : 0ull;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (i0 + 32 * u < G) t += pv[u];
-          if constexpr (MODE == 2) m = pw[u] > m ? pw[u] : m;
+        for (int u = 0; u < U; ++u) {
+          if (i0 + 32 * u < G) {
+#pragma unroll
+            for (int j = 0; j < NSUM; ++j) t[j] += pv[u][j];
+          }
+          if constexpr (MAX) m = pw[u] > m ? pw[u] : m;
         }
       }
-      t = warp_sum(t);
-      if constexpr (MODE == 2) m = warp_max(m);
+#pragma unroll
+      for (int j = 0; j < NSUM; ++j) t[j] = warp_sum(t[j]);
+      if constexpr (MAX) m = warp_max(m);
       if (lane == 0) {
-        s_tot = t;
+#pragma unroll
+        for (int j = 0; j < NSUM; ++j) s_tot[j] = t[j];
         s_max = m;
       }
     }
     __syncthreads();
-    tot = s_tot;
-    if constexpr (MODE == 2) mtot = s_max;
+#pragma unroll
+    for (int j = 0; j < NSUM; ++j) tot[j] = s_tot[j];
+    if constexpr (MAX) mtot = s_max;
   }
   return true;
+}
+
+// The single-sum forms: MODE 0 plain barrier, 1 one sum, 2 one sum and the max.
+template <int MODE>
+__device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* part, unsigned long long* pmax,
+                                                    int& nb, double v, unsigned long long mx, double& tot,
+                                                    unsigned long long& mtot, long long spin = kBarrierSpin) {
+  double vv[1] = {v}, tt[1] = {0.0};
+  const bool ok = grid_barrier_sums<MODE == 0 ? 0 : 1, MODE == 2>(g, part, pmax, nb, vv, mx, tt, mtot, spin);
+  if constexpr (MODE >= 1) tot = tt[0];
+  return ok;
 }
 
 }  // namespace ampcg

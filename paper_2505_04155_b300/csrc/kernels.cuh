@@ -26,7 +26,7 @@
 namespace ampcg {
 
 enum { CRIT_WINDOW = 0, CRIT_LINEAR = 1, CRIT_FIXED = 2 };
-enum { SCALE_NONE = 0, SCALE_L2 = 1, SCALE_LINF_POW2 = 2 };
+enum { SCALE_NONE = 0, SCALE_L2 = 1, SCALE_LINF_POW2 = 2, SCALE_LINF_POW2_LAG = 3 };
 enum { M_NONE = 0, M_JACOBI = 1, M_CHEBYSHEV = 2 };
 // ST_TIMEOUT: a bounded grid-barrier wait ran out (every block of a cooperative
 // launch is resident, so this means a block never arrived)
@@ -75,6 +75,11 @@ struct __align__(16) DevState {
   // selector brackets (prep_selector)
   double inv_tol_nb, tzs_lo, tzs_hi, tzh_lo, tzh_hi, c_lin;
   double rho, rho_prev, beta, gamma, alpha, true_relres;
+  double maxr_prev;          // max|r_{k-1}| (lagged scale, reading R20)
+  int z_ready;               // z_k and rho_k already formed (by the previous update step)
+  int omega_exact;           // omega_k retried with max|r_k| (reading R20)
+  int redo;                  // set by the scalar step: form y_k, z_k, rho_k again
+  int pad_state;
   unsigned int ticket[4];
   int phase_runs[8];         // iterations started per phase 2 u_z + u_r
   // histories (device)
@@ -314,6 +319,29 @@ __device__ __forceinline__ int ceil_log2(double m) {
   return eb - 1023 + (f ? 1 : 0);
 }
 
+// omega_k (reading R5): NONE 1, L2 1/delta_k (as printed in Alg. 3), the
+// power-of-two modes 2^-ceil(log2 m) for the given max|r| (none for m = 0 or
+// non-finite).
+__device__ __forceinline__ int omega_exponent(double m) {
+  const bool have = m > 0.0 && m < __longlong_as_double(0x7ff0000000000000ll);
+  return have ? -ceil_log2(m) : 0;
+}
+__device__ __forceinline__ void set_omega(DevState* st, double m) {
+  double om = 1.0;
+  int pow2 = 1, e = 0;
+  if (st->scale == SCALE_L2) {
+    om = 1.0 / st->delta;
+    pow2 = 0;
+  } else if (st->scale == SCALE_LINF_POW2 || st->scale == SCALE_LINF_POW2_LAG) {
+    e = omega_exponent(m);
+    om = pow2_f64(e);
+  }
+  st->omega = om;
+  st->omega_f = pow2 ? pow2_f32(e) : __double2float_rn(om);
+  st->omega_pow2 = pow2;
+  st->omega_e = e;
+}
+
 // Decide the precisions of iteration st->k (Alg. 3, precision selection), the storage
 // conversions they imply, and omega_k (reading R5).  Thread 0 of one block;
 // hist(t) gives delta_t.  Eq. (precision_selector): u_z from nu_k and u0, u_r
@@ -350,24 +378,14 @@ __device__ void decide(DevState* st, H hist) {
   st->uz = uz;
   st->ur = ur;
   if (st->prec_hist) st->prec_hist[k] = (unsigned char)((uz << 4) | ur);
+  // omega_k: the lagged mode takes max|r_{k-1}| (reading R20; init sets
+  // maxr_prev = max|r_0| for k = 0)
+  st->omega_exact = 0;
+  set_omega(st, st->scale == SCALE_LINF_POW2_LAG ? st->maxr_prev : st->maxr);
   // c = ceil(log2 max|r_k|) (none for max|r_k| = 0 or non-finite)
   const double mr = st->maxr;
   const bool have_c = mr > 0.0 && mr < __longlong_as_double(0x7ff0000000000000ll);
   const int cl = have_c ? ceil_log2(mr) : 0;
-  // omega_k
-  double om = 1.0;
-  int pow2 = 1, e = 0;
-  if (st->scale == SCALE_L2) {
-    om = 1.0 / st->delta;
-    pow2 = 0;
-  } else if (st->scale == SCALE_LINF_POW2 && have_c) {
-    e = -cl;
-    om = pow2_f64(e);
-  }
-  st->omega = om;
-  st->omega_f = pow2 ? pow2_f32(e) : __double2float_rn(om);
-  st->omega_pow2 = pow2;
-  st->omega_e = e;
   // sigma_k = 2^-ceil(log2 max|r_k|) (clamped to binary32's normal range):
   // scales r in binary32 inner products so that their terms stay in range
   int se = have_c ? -cl : 0;
@@ -542,9 +560,19 @@ struct Bufs {
 };
 
 // Alg. 3 on the state copy: rho_k, its checks (reading R12) and
-// beta_{k-1} = rho_k / rho_{k-1}; completes the storage conversions.
+// beta_{k-1} = rho_k / rho_{k-1}; completes the storage conversions.  Under
+// the lagged scale a non-finite rho_k (y_k overflowed u_z) is not final:
+// omega_k becomes 2^-ceil(log2 max|r_k|) and s->redo asks the caller to form
+// y_k, z_k and rho_k again (reading R20; once per iteration).
 __device__ __forceinline__ void rho_step(DevState* s, double r) {
   s->rho = r;
+  s->redo = 0;
+  if (!isfinite(r) && s->scale == SCALE_LINF_POW2_LAG && !s->omega_exact) {
+    s->omega_exact = 1;
+    set_omega(s, s->maxr);
+    s->redo = 1;
+    return;
+  }
   if (!isfinite(r)) { s->status = ST_NONFINITE; s->done = 1; return; }
   if (!(r > 0.0)) { s->status = ST_BREAKDOWN; s->done = 1; return; }
   double beta = s->first ? 0.0 : r / s->rho_prev;
@@ -592,6 +620,8 @@ __device__ __forceinline__ double init_step(DevState* s, double bb, double rr, u
   prep_selector(s);
   s->delta = d0;
   s->maxr = __longlong_as_double((long long)m);
+  s->maxr_prev = s->maxr;
+  s->z_ready = 0;
   s->dring[0] = d0;
   s->k = 0;
   s->done = 0;
@@ -663,7 +693,62 @@ struct PrecondScalars {
   __device__ __forceinline__ explicit PrecondScalars(const DevState* st)
       : r_cast(st->r_cast), pow2(st->omega_pow2), oe(st->omega_e),
         om_one(st->omega_pow2 && st->omega_e == 0), om(st->omega), omf(st->omega_f), sigf(st->sig_f) {}
+  // The scalars of iteration k + 1 as the update step of iteration k knows
+  // them, for scale modes whose omega_{k+1} does not depend on r_{k+1}: NONE
+  // (1) and the lagged power of two 2^-ceil(log2 max|r_k|) (reading R20).
+  // The binary32 dot-product scale stays sigma_k (a power of two that only
+  // keeps the terms in range; the block totals are unscaled by it).
+  __device__ __forceinline__ static PrecondScalars next(const DevState* st) {
+    PrecondScalars c(st);
+    const int e = st->scale == SCALE_LINF_POW2_LAG ? omega_exponent(st->maxr) : 0;
+    c.r_cast = 0;
+    c.pow2 = 1;
+    c.oe = e;
+    c.om_one = e == 0;
+    c.om = pow2_f64(e);
+    c.omf = pow2_f32(e);
+    return c;
+  }
 };
+
+// D^-1 of V consecutive rows in u_z (Jacobi; nothing for M = none).
+template <int UZ, int MT, int V>
+__device__ __forceinline__ void dinv_load(const Bufs& B, int64_t i0, typename Store<UZ>::T (&dv)[V]) {
+  if constexpr (MT != M_NONE) {
+    if constexpr (UZ == P64) vldg<V>(B.dinv64 + i0, dv);
+    else if constexpr (UZ == P32) vldg<V>(B.dinv32 + i0, dv);
+    else vldg<V>(B.dinv16 + i0, dv);
+  }
+}
+
+// y = omega r computed in u_r and stored in u_z (reading R6), z = M^-1 y in
+// u_z (Jacobi: one rounding of dinv_i y_i, reading R16), for V elements held
+// in registers (m of them in range), and their rho_k terms.
+template <int UZ, int UR, int MT, int V>
+__device__ __forceinline__ void precond_regs(const PrecondScalars& c, const typename Store<UR>::T (&r)[V],
+                                             const typename Store<UZ>::T (&dv)[V], int m,
+                                             typename Store<UZ>::T (&zz)[V], double& rho, Dot2& d2) {
+  using TZ = typename Store<UZ>::T;
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    TZ y;
+    if constexpr (UR == P64) {
+      if constexpr (UZ == P16) y = c.pow2 ? d2h_scaled(r[j], c.oe) : d2h(__dmul_rn(c.om, r[j]));
+      else y = round_from_f64<UZ>(c.om_one ? r[j] : __dmul_rn(c.om, r[j]));
+    } else {
+      y = round_from_f32<UZ>(__fmul_rn(c.omf, r[j]));
+    }
+    if constexpr (MT == M_NONE) zz[j] = y;
+    else if constexpr (UZ == P64) zz[j] = __dmul_rn(dv[j], y);
+    else if constexpr (UZ == P32) zz[j] = __fmul_rn(dv[j], y);
+    else zz[j] = __float2half_rn(__fmul_rn(h2f(dv[j]), h2f(y)));
+    if (j < m) {
+      if constexpr (kSmall) d2.add(__fmul_rn((float)r[j], c.sigf), (float)zz[j]);
+      else rho = fma(to_f64(r[j]), to_f64(zz[j]), rho);
+    }
+  }
+}
 
 template <int UZ, int UR, int MT, int V, class Part>
 __device__ __forceinline__ void precond_vec(const Bufs& B, const PrecondScalars& c, int64_t i0, int m,
@@ -694,29 +779,8 @@ __device__ __forceinline__ void precond_vec(const Bufs& B, const PrecondScalars&
     }
   }
   alignas(16) TZ dv[V];
-  if constexpr (MT != M_NONE) {
-    if constexpr (UZ == P64) vldg<V>(B.dinv64 + i0, dv);
-    else if constexpr (UZ == P32) vldg<V>(B.dinv32 + i0, dv);
-    else vldg<V>(B.dinv16 + i0, dv);
-  }
-#pragma unroll
-  for (int j = 0; j < V; ++j) {
-    TZ y;
-    if constexpr (UR == P64) {
-      if constexpr (UZ == P16) y = c.pow2 ? d2h_scaled(r[j], c.oe) : d2h(__dmul_rn(c.om, r[j]));
-      else y = round_from_f64<UZ>(c.om_one ? r[j] : __dmul_rn(c.om, r[j]));
-    } else {
-      y = round_from_f32<UZ>(__fmul_rn(c.omf, r[j]));
-    }
-    if constexpr (MT == M_NONE) zz[j] = y;
-    else if constexpr (UZ == P64) zz[j] = __dmul_rn(dv[j], y);
-    else if constexpr (UZ == P32) zz[j] = __fmul_rn(dv[j], y);
-    else zz[j] = __float2half_rn(__fmul_rn(h2f(dv[j]), h2f(y)));
-    if (j < m) {
-      if constexpr (kSmall) d2.add(__fmul_rn((float)r[j], c.sigf), (float)zz[j]);
-      else rho = fma(to_f64(r[j]), to_f64(zz[j]), rho);
-    }
-  }
+  dinv_load<UZ, MT, V>(B, i0, dv);
+  precond_regs<UZ, UR, MT, V>(c, r, dv, m, zz, rho, d2);
 }
 
 // Alg. 3 scaling, preconditioning and rho_k over the thread's vectors; z_k
@@ -831,51 +895,57 @@ __global__ void __launch_bounds__(256) k_precond_dir(Bufs B, int64_t n, DevState
   constexpr bool kSmall = (UR != P64) && (UZ != P64);
   __shared__ DevState S;
   if (!state_enter(&S, st, UZ, UR)) return;
-  const PrecondScalars c(&S);
   TZ* __restrict__ z = (TZ*)B.z;
   const int64_t nv = (n + V - 1) / V;
   const int64_t stride = GridPart::count();
   const int64_t v0 = GridPart::first();
-  double rho = 0.0;
-  Dot2 d2;
   alignas(16) TZ zr[kZreg][V];
+  int nb = 0;
+  // a second pass only when the lagged scale made rho_k non-finite (reading R20)
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const PrecondScalars c(&S);
+    double rho = 0.0;
+    Dot2 d2;
 #pragma unroll
-  for (int t = 0; t < kZreg; ++t) {
-    const int64_t v = v0 + t * stride;
-    if (v < nv) {
+    for (int t = 0; t < kZreg; ++t) {
+      const int64_t v = v0 + t * stride;
+      if (v < nv) {
+        const int64_t i0 = v * V;
+        const int m = (n - i0 < V) ? (int)(n - i0) : V;
+        precond_vec<UZ, UR, MT, V, GridPart>(B, c, i0, m, zr[t], rho, d2);
+      }
+    }
+    for (int64_t v = v0 + kZreg * stride; v < nv; v += stride) {
       const int64_t i0 = v * V;
       const int m = (n - i0 < V) ? (int)(n - i0) : V;
-      precond_vec<UZ, UR, MT, V, GridPart>(B, c, i0, m, zr[t], rho, d2);
+      alignas(16) TZ zz[V];
+      precond_vec<UZ, UR, MT, V, GridPart>(B, c, i0, m, zz, rho, d2);
+      vst<V>(z + i0, zz, m);
     }
-  }
-  for (int64_t v = v0 + kZreg * stride; v < nv; v += stride) {
-    const int64_t i0 = v * V;
-    const int m = (n - i0 < V) ? (int)(n - i0) : V;
-    alignas(16) TZ zz[V];
-    precond_vec<UZ, UR, MT, V, GridPart>(B, c, i0, m, zz, rho, d2);
-    vst<V>(z + i0, zz, m);
-  }
-  if (S.p_cast) cast_p<UZ>(B, n, &S);
-  double v[1];
-  if constexpr (kSmall) {
-    v[0] = block_sum_dot2(d2, S.inv_sig);
-  } else {
-    v[0] = rho;
-    block_sum<1>(v);
-  }
-  double tot;
-  unsigned long long unused;
-  int nb = 0;
-  const bool ok = grid_reduce_barrier<1>(B.bar + 2 * UZ + UR, B.part, nullptr, nb, v[0], 0ull, tot, unused);
-  if (threadIdx.x == 0) {
-    if (ok) {
-      rho_step(&S, tot);
+    if (S.p_cast) cast_p<UZ>(B, n, &S);
+    double v[1];
+    if constexpr (kSmall) {
+      v[0] = block_sum_dot2(d2, S.inv_sig);
     } else {
-      S.status = ST_TIMEOUT;
-      S.done = 1;
+      v[0] = rho;
+      block_sum<1>(v);
     }
-    S.phase_runs[2 * UZ + UR] += 1;
+    double tot;
+    unsigned long long unused;
+    const bool ok = grid_reduce_barrier<1>(B.bar + 2 * UZ + UR, B.part, nullptr, nb, v[0], 0ull, tot, unused);
+    if (threadIdx.x == 0) {
+      if (ok) {
+        rho_step(&S, tot);
+      } else {
+        S.status = ST_TIMEOUT;
+        S.done = 1;
+        S.redo = 0;
+      }
+    }
+    __syncthreads();
+    if (!S.redo) break;
   }
+  if (threadIdx.x == 0) S.phase_runs[2 * UZ + UR] += 1;
   __syncthreads();
   if (!S.done) {
     // p_k = z_k + beta_{k-1} p_{k-1}; p_{k-1} may have been converted by
@@ -1294,13 +1364,77 @@ __device__ __forceinline__ void update_rows(const Bufs& B, int64_t n, const DevS
   if constexpr (UR != P64) mx = abs_key(__uint_as_float((unsigned)mx));
 }
 
+// update_rows, and in the same pass over the vectors the scaling and
+// preconditioning of the new residual for iteration k + 1 with the scalars cn
+// (PrecondScalars::next): z_{k+1} goes to its buffer and its rho_{k+1} terms
+// to rho / d2z.  Valid when iteration k + 1 keeps the precision pair (the
+// caller discards z_{k+1} otherwise).
+template <int UZ, int UR, int MT, int V, class Part = GridPart>
+__device__ __forceinline__ void update_precond_rows(const Bufs& B, int64_t n, const DevState* st,
+                                                    const PrecondScalars& cn, double& rr, Dot2& d2,
+                                                    unsigned long long& mx, double& rho, Dot2& d2z) {
+  using TZ = typename Store<UZ>::T;
+  using TR = typename Store<UR>::T;
+  const TZ* __restrict__ p = (const TZ*)(st->pcur ? B.p[0] : B.p[1]);
+  const TR* __restrict__ q = (const TR*)B.q;
+  TR* __restrict__ rv = UR == P64 ? (TR*)B.r64 : (TR*)B.r32;
+  TZ* __restrict__ z = (TZ*)B.z;
+  const double a = st->alpha;
+  const float af = st->alpha_f;
+  const float sigf = st->sig_f;
+  const int64_t nv = (n + V - 1) / V;
+  const int64_t stride = Part::count();
+  for (int64_t v = Part::first(); v < nv; v += stride) {
+    const int64_t i0 = v * V;
+    const int m = (n - i0 < V) ? (int)(n - i0) : V;
+    alignas(16) TZ pp[V];
+    alignas(16) TR qq[V];
+    alignas(16) TR rr_[V];
+    alignas(16) double xx[V];
+    alignas(16) TZ dv[V];
+    Part::template vldm<V>(p + i0, pp);
+    Part::template vldm<V>(q + i0, qq);
+    Part::template vldo<V>(rv + i0, rr_);
+    Part::template vldo<V>(B.x + i0, xx);
+    dinv_load<UZ, MT, V>(B, i0, dv);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      xx[j] = fma(a, to_f64(pp[j]), xx[j]);
+      if constexpr (UR == P64) {
+        rr_[j] = fma(-a, qq[j], rr_[j]);
+        if (j < m) {
+          rr = fma(rr_[j], rr_[j], rr);
+          unsigned long long kk = abs_key(rr_[j]);
+          mx = kk > mx ? kk : mx;
+        }
+      } else {
+        rr_[j] = __fmaf_rn(-af, qq[j], rr_[j]);
+        if (j < m) {
+          float rs = __fmul_rn(rr_[j], sigf);
+          d2.add(rs, rs);
+          unsigned kk = __float_as_uint(rr_[j]) & 0x7fffffffu;   // order-preserving |r|
+          mx = kk > mx ? kk : mx;
+        }
+      }
+    }
+    vst<V>(B.x + i0, xx, m);
+    vst<V>(rv + i0, rr_, m);
+    alignas(16) TZ zz[V];
+    precond_regs<UZ, UR, MT, V>(cn, rr_, dv, m, zz, rho, d2z);
+    vst<V>(z + i0, zz, m);
+  }
+  if constexpr (UR != P64) mx = abs_key(__uint_as_float((unsigned)mx));
+}
+
 // Alg. 3 on the state copy: delta_{k+1}, the stopping test,
 // k <- k + 1 and the decision for the new iteration; returns delta_{k+1}.
 __device__ __forceinline__ double update_step(DevState* s, double rr, unsigned long long m) {
   double d = sqrt(rr);
   int k1 = s->k + 1;
   s->delta = d;
+  s->maxr_prev = s->maxr;
   s->maxr = __longlong_as_double((long long)m);
+  s->z_ready = 0;
   s->dring[k1 & (kRing - 1)] = d;
   s->rho_prev = s->rho;
   s->first = 0;
@@ -1394,7 +1528,7 @@ template <int UR, int IT> struct LoopStageCfg {
   static constexpr int K = StageCfg<UR>::K < (200 * 1024) / kPer ? StageCfg<UR>::K : (200 * 1024) / kPer;
   static constexpr int kBytes = K * kPer;
 };
-template <int UZ, int UR, int MT, int IT>
+template <int UZ, int UR, int MT, int IT, bool FUSED>
 __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t n, DevState* st, int iters) {
   using TZ = typename Store<UZ>::T;
   using Part = LoopPart;
@@ -1410,63 +1544,78 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
   const int64_t nvz = (n + VZ - 1) / VZ;
   const int64_t stride = Part::count();
   const int64_t v0 = Part::first();
-  double tot;
-  unsigned long long mtot;
+  // FUSED (scale modes whose omega_{k+1} is known before delta_{k+1} is
+  // reduced: no scaling, or the lagged power of two of reading R20): the
+  // update step of iteration k also forms z_{k+1} and rho_{k+1}, reduced
+  // together with delta_{k+1}: three grid barriers per iteration (p_k,
+  // gamma_k, delta_{k+1} + rho_{k+1}) instead of four.  The head step
+  // (scaling, preconditioning, rho_k on their own) then runs only after a
+  // precision change, a residual replacement, at the first iteration, or to
+  // retry a non-finite rho_k with the exact power of two.  A template
+  // parameter rather than a run-time branch: one kernel holding both update
+  // steps spilled 112-172 bytes of registers against 32-100.
+  constexpr bool fused = FUSED;
+  double tot[2] = {0.0, 0.0};
+  unsigned long long mtot = 0ull;
   bool ok = true;
   int nb = 0;   // barriers passed in this launch
   for (int it = 0; it < iters; ++it) {
-    // Alg. 3: scaling, preconditioning, rho_k and beta_{k-1}; with binary16
-    // storage p_{k-1} of the register-held vectors is loaded before the
-    // barrier (it does not depend on beta_{k-1}; not when it is converted)
     alignas(16) TZ zr[kZreg][VZ];
     alignas(16) TZ pr[kZreg][VZ];
-    const bool pre = (UZ == P16) && !S.p_cast && !S.first;
-    {
-      const PrecondScalars c(&S);
-      double rho = 0.0;
-      Dot2 d2;
+    bool have = false;   // z_k of the first kZreg vectors of the thread in registers
+    bool pre = false;    // and p_{k-1} of those vectors
+    if (!S.z_ready) {
+      // Alg. 3: scaling, preconditioning, rho_k and beta_{k-1}; with binary16
+      // storage p_{k-1} of the register-held vectors is loaded before the
+      // barrier (it does not depend on beta_{k-1}; not when it is converted)
+      for (;;) {
+        pre = (UZ == P16) && !S.p_cast && !S.first;
+        const PrecondScalars c(&S);
+        double rho = 0.0;
+        Dot2 d2;
 #pragma unroll
-      for (int t = 0; t < kZreg; ++t) {
-        const int64_t v = v0 + t * stride;
-        if (v < nvz) {
-          const int64_t i0 = v * VZ;
-          precond_vec<UZ, UR, MT, VZ, Part>(B, c, i0, (n - i0 < VZ) ? (int)(n - i0) : VZ, zr[t], rho, d2);
-        }
-      }
-      if constexpr (UZ == P16) {
-        if (pre) {
-          const TZ* po = (const TZ*)(S.pcur ? B.p[1] : B.p[0]);
-#pragma unroll
-          for (int t = 0; t < kZreg; ++t) {
-            const int64_t v = v0 + t * stride;
-            if (v < nvz) vldcg<VZ>(po + v * VZ, pr[t]);
+        for (int t = 0; t < kZreg; ++t) {
+          const int64_t v = v0 + t * stride;
+          if (v < nvz) {
+            const int64_t i0 = v * VZ;
+            precond_vec<UZ, UR, MT, VZ, Part>(B, c, i0, (n - i0 < VZ) ? (int)(n - i0) : VZ, zr[t], rho, d2);
           }
         }
+        if constexpr (UZ == P16) {
+          if (pre) {
+            const TZ* po = (const TZ*)(S.pcur ? B.p[1] : B.p[0]);
+#pragma unroll
+            for (int t = 0; t < kZreg; ++t) {
+              const int64_t v = v0 + t * stride;
+              if (v < nvz) vldcg<VZ>(po + v * VZ, pr[t]);
+            }
+          }
+        }
+        for (int64_t v = v0 + kZreg * stride; v < nvz; v += stride) {
+          const int64_t i0 = v * VZ;
+          const int m = (n - i0 < VZ) ? (int)(n - i0) : VZ;
+          alignas(16) TZ zz[VZ];
+          precond_vec<UZ, UR, MT, VZ, Part>(B, c, i0, m, zz, rho, d2);
+          vst<VZ>(z + i0, zz, m);
+        }
+        if (S.p_cast) cast_p<UZ, Part>(B, n, &S);
+        double v[1];
+        if constexpr (kSmall) {
+          v[0] = block_sum_dot2(d2, S.inv_sig);
+        } else {
+          v[0] = rho;
+          block_sum_wide<1>(v);
+        }
+        ok = grid_reduce_barrier<1>(bar, B.part, nullptr, nb, v[0], 0ull, tot[0], mtot);
+        if (!ok) break;
+        if (threadIdx.x == 0) rho_step(&S, tot[0]);
+        __syncthreads();
+        if (!S.redo) break;   // else: omega_k is now the exact power of two (reading R20)
       }
-      for (int64_t v = v0 + kZreg * stride; v < nvz; v += stride) {
-        const int64_t i0 = v * VZ;
-        const int m = (n - i0 < VZ) ? (int)(n - i0) : VZ;
-        alignas(16) TZ zz[VZ];
-        precond_vec<UZ, UR, MT, VZ, Part>(B, c, i0, m, zz, rho, d2);
-        vst<VZ>(z + i0, zz, m);
-      }
-      if (S.p_cast) cast_p<UZ, Part>(B, n, &S);
-      double v[1];
-      if constexpr (kSmall) {
-        v[0] = block_sum_dot2(d2, S.inv_sig);
-      } else {
-        v[0] = rho;
-        block_sum_wide<1>(v);
-      }
-      ok = grid_reduce_barrier<1>(bar, B.part, nullptr, nb, v[0], 0ull, tot, mtot);
-      if (!ok) break;
-      if (threadIdx.x == 0) {
-        S.phase_runs[2 * UZ + UR] += 1;
-        rho_step(&S, tot);
-      }
-      __syncthreads();
-      if (S.done) break;
+      if (!ok || S.done) break;
+      have = true;
     }
+    if (threadIdx.x == 0) S.phase_runs[2 * UZ + UR] += 1;
     // Alg. 3: search direction p_k = z_k + beta_{k-1} p_{k-1}
     {
       const int pc = S.pcur;
@@ -1475,13 +1624,13 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
       const int first = S.first;
       const double beta = S.beta;
       const float bf = S.beta_f;
-      auto dir = [&](int64_t i0, int m, const TZ (&zz)[VZ], const TZ (&pp0)[VZ], bool have) {
+      auto dir = [&](int64_t i0, int m, const TZ (&zz)[VZ], const TZ (&pp0)[VZ], bool have_p) {
         if (first) {
           vst<VZ>(pn + i0, zz, m);
           return;
         }
         alignas(16) TZ pp[VZ];
-        if (have) {
+        if (have_p) {
 #pragma unroll
           for (int j = 0; j < VZ; ++j) pp[j] = pp0[j];
         } else {
@@ -1494,21 +1643,25 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
         }
         vst<VZ>(pn + i0, pp, m);
       };
+      if (have) {
 #pragma unroll
-      for (int t = 0; t < kZreg; ++t) {
-        const int64_t v = v0 + t * stride;
-        if (v < nvz) {
-          const int64_t i0 = v * VZ;
-          dir(i0, (n - i0 < VZ) ? (int)(n - i0) : VZ, zr[t], pr[t], pre);
+        for (int t = 0; t < kZreg; ++t) {
+          const int64_t v = v0 + t * stride;
+          if (v < nvz) {
+            const int64_t i0 = v * VZ;
+            dir(i0, (n - i0 < VZ) ? (int)(n - i0) : VZ, zr[t], pr[t], pre);
+          }
         }
       }
-      for (int64_t v = v0 + kZreg * stride; v < nvz; v += stride) {
+      // z_k of the other vectors (all of them when the previous update step
+      // formed z_k) is in its buffer, written by other threads before a barrier
+      for (int64_t v = v0 + (have ? kZreg * stride : 0); v < nvz; v += stride) {
         const int64_t i0 = v * VZ;
         alignas(16) TZ zz[VZ];
         vldcg<VZ>(z + i0, zz);
         dir(i0, (n - i0 < VZ) ? (int)(n - i0) : VZ, zz, zz, false);
       }
-      ok = grid_reduce_barrier<0>(bar, nullptr, nullptr, nb, 0.0, 0ull, tot, mtot);   // p_k before the gathers
+      ok = grid_reduce_barrier<0>(bar, nullptr, nullptr, nb, 0.0, 0ull, tot[0], mtot);   // p_k before the gathers
       if (!ok) break;
     }
     // Alg. 3: q_k = A p_k, gamma_k, alpha_k
@@ -1523,31 +1676,63 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
         v[0] = gam;
         block_sum_wide<1>(v);
       }
-      ok = grid_reduce_barrier<1>(bar, B.part, nullptr, nb, v[0], 0ull, tot, mtot);
+      ok = grid_reduce_barrier<1>(bar, B.part, nullptr, nb, v[0], 0ull, tot[0], mtot);
       if (!ok) break;
-      if (threadIdx.x == 0) gamma_step(&S, tot);
+      if (threadIdx.x == 0) gamma_step(&S, tot[0]);
       __syncthreads();
       if (S.done) break;
     }
-    // Alg. 3: x and r updates, delta_{k+1}, stopping test, next precisions
+    // Alg. 3: x and r updates, delta_{k+1}, stopping test, next precisions;
+    // fused: also z_{k+1} and rho_{k+1}
     {
-      double rr = 0.0;
-      Dot2 d2;
+      double rr = 0.0, rho = 0.0;
+      Dot2 d2, d2z;
       unsigned long long mx = 0ull;
-      update_rows<UZ, UR, V, Part>(B, n, &S, rr, d2, mx);
-      double v[1];
+      if constexpr (fused) {
+        const PrecondScalars cn = PrecondScalars::next(&S);
+        update_precond_rows<UZ, UR, MT, V, Part>(B, n, &S, cn, rr, d2, mx, rho, d2z);
+      } else {
+        update_rows<UZ, UR, V, Part>(B, n, &S, rr, d2, mx);
+      }
+      double v[2];
       if constexpr (UR != P64) {
         v[0] = block_sum_dot2(d2, S.inv_sig2);
       } else {
         v[0] = rr;
-        block_sum_wide<1>(v);
+      }
+      if constexpr (kSmall) {
+        if constexpr (fused) v[1] = block_sum_dot2(d2z, S.inv_sig);
+      } else {
+        v[1] = rho;
+      }
+      if constexpr (UR == P64 && !kSmall) {
+        if constexpr (fused) {
+          block_sum_wide<2>(v);
+        } else {
+          double w[1] = {v[0]};
+          block_sum_wide<1>(w);
+          v[0] = w[0];
+        }
+      } else if constexpr (!kSmall) {
+        if constexpr (fused) {
+          double w[1] = {v[1]};
+          block_sum_wide<1>(w);
+          v[1] = w[0];
+        }
       }
       mx = block_max(mx);
-      ok = grid_reduce_barrier<2>(bar, B.part, B.pmax, nb, v[0], mx, tot, mtot);
+      if constexpr (fused) ok = grid_barrier_sums<2, true>(bar, B.part, B.pmax, nb, v, mx, tot, mtot, kBarrierSpin);
+      else ok = grid_barrier_sums<1, true>(bar, B.part, B.pmax, nb, v, mx, tot, mtot, kBarrierSpin);
       if (!ok) break;
       if (threadIdx.x == 0) {
-        const double d = update_step(&S, tot, mtot);
+        const double d = update_step(&S, tot[0], mtot);
         if (blockIdx.x == 0) S.delta_hist[S.k] = d;
+        if (FUSED && !S.done && S.uz == UZ && S.ur == UR) {
+          // the pair is kept: z_{k+1} and rho_{k+1} stand (or are retried by
+          // the head step with the exact power of two)
+          rho_step(&S, tot[1]);
+          S.z_ready = S.redo ? 0 : 1;
+        }
       }
       __syncthreads();
       if (S.done || S.uz != UZ || S.ur != UR) break;
@@ -1589,15 +1774,18 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_spmv_loop_step(Sell A, Bufs B
 // evaluated once per precision change rather than once per iteration.
 
 // Sets the SWITCH value of an outer-loop body: the current pair 2 u_z + u_r.
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_phase(DevState* st, cudaGraphConditionalHandle h) {
   cudaGraphSetConditional(h, st->done ? AMPCG_PHASE_NONE : 2 * st->uz + st->ur);
 }
+#endif
 
 // End of an inner-loop chunk of pair ph: continue while the solve runs and
 // the pair is still ph.  A chunk that ends without the iteration counter
 // having advanced (which the dispatch never produces: the SWITCH chose ph
 // from the same state) stops the solve with an internal error, so the inner
 // loop ends within maxit chunks.
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_chunk_ctl(DevState* st, cudaGraphConditionalHandle h, int ph) {
   st->chunk_runs[ph] += 1;
   if (!st->done && st->k == st->k_chunk) {
@@ -1607,8 +1795,10 @@ __global__ void k_chunk_ctl(DevState* st, cudaGraphConditionalHandle h, int ph) 
   st->k_chunk = st->k;
   cudaGraphSetConditional(h, (!st->done && 2 * st->uz + st->ur == ph) ? 1u : 0u);
 }
+#endif
 
 // Sets the condition of the outer loop; the same progress check per body.
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_loop_ctl(DevState* st, cudaGraphConditionalHandle h) {
   st->loop_runs += 1;
   if (!st->done && st->k == st->k_body) {
@@ -1618,6 +1808,7 @@ __global__ void k_loop_ctl(DevState* st, cudaGraphConditionalHandle h) {
   st->k_body = st->k;
   cudaGraphSetConditional(h, st->done ? 0u : 1u);
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // True residual t = b - A x in FP64 and ||t|| / ||b|| (exit verification).
@@ -1679,6 +1870,7 @@ __device__ __forceinline__ double refresh_step(DevState* s, double rr, unsigned 
   int k = s->k;
   s->delta = d;
   s->maxr = __longlong_as_double((long long)m);
+  s->z_ready = 0;
   s->dring[k & (kRing - 1)] = d;
   s->refreshes += 1;
   if (d <= s->tol_nb) {
@@ -1692,6 +1884,7 @@ __device__ __forceinline__ double refresh_step(DevState* s, double rr, unsigned 
   return d;
 }
 
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st) {
   double rr = 0.0;
   unsigned long long mx = 0ull;
@@ -1720,6 +1913,7 @@ __global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st
     S.delta_hist[k] = d;
   }
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // Create-time preparation (a1): CSR -> sliced layout, value copies, diagonal.
@@ -1727,6 +1921,7 @@ __global__ void __launch_bounds__(256) k_refresh(Bufs B, int64_t n, DevState* st
 // Per row: structure checks, row length, diagonal, max |col - row|.
 // flags bit 0: bad rowptr; bit 1: column out of range / not increasing;
 // bit 2: diagonal missing or <= 0; bit 3: non-finite value.
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_csr_scan_rows(int64_t n, int64_t nnz, const int* rowptr, const int* col,
                                 const double* val, int* rowlen, double* diag, int* flags,
                                 int* maxoff) {
@@ -1759,7 +1954,9 @@ __global__ void k_csr_scan_rows(int64_t n, int64_t nnz, const int* rowptr, const
   diag[i] = dg;
   atomicMax(maxoff, mo);
 }
+#endif
 
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_slice_width(int64_t n, int64_t nslices, const int* rowlen, int* width) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nslices) return;
@@ -1770,9 +1967,11 @@ __global__ void k_slice_width(int64_t n, int64_t nslices, const int* rowlen, int
   }
   width[s] = w;
 }
+#endif
 
 // Exclusive scan of 32 * width into off (one block; chunked sequential scan);
 // total[0] = stored entries, total[1] = largest width.
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_slice_offsets(int64_t nslices, const int* width, long long* off,
                                 long long* total) {
   __shared__ long long sh[1024];
@@ -1805,6 +2004,7 @@ __global__ void k_slice_offsets(int64_t nslices, const int* width, long long* of
   long long run = sh[t];
   for (int64_t i = a; i < b; ++i) { off[i] = run; run += 32ll * width[i]; }
 }
+#endif
 
 // Slice-uniform offset patterns (int16 layout): a slice whose 32 rows (all
 // below n) have entries only at the offsets of one sorted set U with |U| equal
@@ -1814,6 +2014,7 @@ __global__ void k_slice_offsets(int64_t nslices, const int* width, long long* of
 // zeros).  Its gathers then need U only (one 16-byte pattern per slice), not
 // the slice's offsets.  7-point stencils: every slice but the first and the
 // last.  One thread per slice.
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_slice_pattern(int64_t n, int64_t nslices, const int* rowptr, const int* col,
                                 const int* width, short* pat) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1843,7 +2044,9 @@ __global__ void k_slice_pattern(int64_t n, int64_t nslices, const int* rowptr, c
   for (int j = 0; j < kStageW; ++j) pat[s * kStageW + j] = (ok && j < m) ? (short)u[j] : (short)0;
   if (!ok) pat[s * kStageW] = kNoPat;
 }
+#endif
 
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_fill_sell(int64_t n, const int* rowptr, const int* col, const double* val,
                             const long long* off, const int* width, const short* pat, int* cabs,
                             short* coff, double* v64, float* v32, unsigned char* rmask) {
@@ -1886,7 +2089,9 @@ __global__ void k_fill_sell(int64_t n, const int* rowptr, const int* col, const 
     v32[e] = __double2float_rn(v);
   }
 }
+#endif
 
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_jacobi(int64_t n, const double* diag, double* d64, float* d32, __half* d16) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1895,10 +2100,12 @@ __global__ void k_jacobi(int64_t n, const double* diag, double* d64, float* d32,
   d32[i] = __double2float_rn(v);
   d16[i] = d2h(v);
 }
+#endif
 
 // Block CSR (nb block rows of bs x bs blocks, row-major blocks, ascending
 // block columns) expanded to scalar CSR: scalar row I*bs + r holds, for each
 // block k of block row I, the bs entries of the block's row r.
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_bsr_expand(int64_t nb, int bs, const int* browptr, const int* bcol,
                              const double* bval, int* rowptr, int* col, double* val) {
   int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1919,6 +2126,7 @@ __global__ void k_bsr_expand(int64_t nb, int bs, const int* browptr, const int* 
     }
   }
 }
+#endif
 
 // New values on the same pattern: vals in CSR order (rowptr on the device),
 // written into the sliced layout (FP64 and FP32 copies) with the Jacobi
@@ -2291,6 +2499,11 @@ __global__ void __launch_bounds__(256) k_cheb_final(Bufs B, Cheb C, int64_t n, D
   if (threadIdx.x == 0) {
     S.ticket[0] = 0u;
     rho_step(&S, tot[0]);
+    if (S.redo) {   // the lagged scale is not offered with Chebyshev (the host rejects it)
+      S.redo = 0;
+      S.status = ST_NONFINITE;
+      S.done = 1;
+    }
   }
   state_store(st, &S);
 }
@@ -2391,6 +2604,7 @@ __global__ void __launch_bounds__(256) k_precond_step(Bufs B, int64_t n, const D
 // limit; block `absent` (if in range) returns without arriving, so the others'
 // wait runs out after `spin` polls and they report it.  out[b] = 1 when block b
 // passed the barrier, 0 when its wait ran out, -1 when it did not arrive.
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void __launch_bounds__(256) k_barrier_check(GridSumBarrier* g, double* part, int absent,
                                                        long long spin, int* out) {
   if ((int)blockIdx.x == absent) {
@@ -2403,8 +2617,10 @@ __global__ void __launch_bounds__(256) k_barrier_check(GridSumBarrier* g, double
   const bool ok = grid_reduce_barrier<1>(g, part, nullptr, nb, 1.0, 0ull, tot, mtot, spin);
   if (threadIdx.x == 0) out[blockIdx.x] = (ok && tot == (double)gridDim.x) ? 1 : 0;
 }
+#endif
 
 // Selector replay over a residual-norm sequence (one thread).
+#ifndef AMPCG_INSTANTIATION_UNIT
 __global__ void k_selector_trace(DevState* st, int m, unsigned char* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   prep_selector(st);
@@ -2416,5 +2632,6 @@ __global__ void k_selector_trace(DevState* st, int m, unsigned char* out) {
     st->first = 0;
   }
 }
+#endif
 
 }  // namespace ampcg

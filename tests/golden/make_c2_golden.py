@@ -3,16 +3,17 @@
 
 The benchmark system (128^3 7-point variable-coefficient diffusion, the
 seeded recipe of workloads.diffusion3d(128, 2.0, seed=0), b = U[-1,1] seed 1,
-x0 = 0) is solved by the oracle three times:
+x0 = 0) is solved by the oracle four times:
   - AMP-PCG(FP16) with the linear-convergence criterion (ell = 5, C = 1),
-    LINF_POW2 scaling, latching and up to 3 FP64 verify-and-replace steps
-    (the benchmark's policy; Alg. 3 with readings R5, R9), tol 1e-10;
+    latching and up to 3 FP64 verify-and-replace steps (Alg. 3 with readings
+    R5, R9), tol 1e-10, once with LINF_POW2 scaling and once with the lagged
+    power of two (reading R20);
   - PCG (Alg. 1) in FP64, tol 1e-10 (the baseline's iteration count);
   - PCG in FP64 to tol 1e-13: the reference solution x* (reading R11).
 It stores iteration counts, switch points, the first 100 relative residuals,
 the final true residuals, norms, the solutions at 1000 fixed indices and the
 relative errors of the AMP solution against x*.  Nothing here calls the CUDA
-library.  Takes about 12 minutes on one host core.
+library.  Takes about 35 minutes on one host core.
 
     python tests/golden/make_c2_golden.py
 """
@@ -38,11 +39,13 @@ def main():
     a = W.diffusion3d(128, 2.0, seed=0)
     b = W.rhs_uniform(a.n, seed=1)
     idx = np.sort(np.random.default_rng(2024).choice(a.n, NSAMPLE, replace=False))
-    pol = oracle.Policy(u0=oracle.FP16, criterion=oracle.LINEAR, ell=5, C=1.0,
-                        scale=oracle.SCALE_LINF_POW2, latch=1, verify_refresh=3)
-    t0 = time.perf_counter()
-    amp = oracle.ampcg(a.rowptr, a.col, a.val, b, tol=1e-10, maxit=20000, policy=pol)
-    t_amp = time.perf_counter() - t0
+    amps = {}
+    for key, scale in (("amp16_linear", oracle.SCALE_LINF_POW2), ("amp16_linear_lag", oracle.SCALE_LINF_POW2_LAG)):
+        pol = oracle.Policy(u0=oracle.FP16, criterion=oracle.LINEAR, ell=5, C=1.0,
+                            scale=scale, latch=1, verify_refresh=3)
+        t0 = time.perf_counter()
+        amps[key] = (oracle.ampcg(a.rowptr, a.col, a.val, b, tol=1e-10, maxit=20000, policy=pol),
+                     time.perf_counter() - t0)
     t0 = time.perf_counter()
     p64 = oracle.pcg64(a.rowptr, a.col, a.val, b, tol=1e-10, maxit=20000)
     t_p64 = time.perf_counter() - t0
@@ -59,14 +62,15 @@ def main():
                 "seed=0), b = rhs_uniform(n, seed=1), x0 = 0); written by tests/golden/make_c2_golden.py",
         "n": int(a.n), "nnz": int(a.nnz),
         "sample_idx": idx.tolist(),
-        "amp16_linear": {
-            "policy": "AMP-PCG(FP16), linear criterion ell=5 C=1, LINF_POW2, latch, verify_refresh=3, tol 1e-10",
+        **{key: {
+            "policy": "AMP-PCG(FP16), linear criterion ell=5 C=1, " + ("lagged power-of-two scale (R20)"
+                      if key.endswith("lag") else "LINF_POW2") + ", latch, verify_refresh=3, tol 1e-10",
             "status": amp.status, "iters": amp.iters, "switch_iter": list(amp.switch_iter),
-            "refreshes": amp.refreshes, "true_relres": amp.true_relres,
+            "refreshes": amp.refreshes, "true_relres": amp.true_relres, "scale_retries": amp.scale_retries,
             "updated_relres": amp.updated_relres, "relres_hist_100": amp.relres_hist[:100].tolist(),
             "x_norm": float(np.linalg.norm(amp.x)), "x_sample": amp.x[idx].tolist(),
             "err_vs_xstar": rel(amp.x, xs.x), "err_vs_xstar_sampled": rel(amp.x[idx], xs.x[idx]),
-            "host_seconds": round(t_amp, 1)},
+            "host_seconds": round(t_amp, 1)} for key, (amp, t_amp) in amps.items()},
         "pcg64": {"policy": "PCG (Alg. 1) FP64, Jacobi, tol 1e-10", "iters": p64.iters,
                   "true_relres": p64.true_relres, "x_norm": float(np.linalg.norm(p64.x)),
                   "x_sample": p64.x[idx].tolist(), "err_vs_xstar": rel(p64.x, xs.x),
@@ -77,7 +81,8 @@ def main():
     }
     with open(OUT, "w") as f:
         json.dump(out, f, indent=1)
-    print(json.dumps({k: v for k, v in out["amp16_linear"].items() if k not in ("x_sample", "relres_hist_100")}))
+    for key in amps:
+        print(json.dumps({k: v for k, v in out[key].items() if k not in ("x_sample", "relres_hist_100")}))
     print(json.dumps({k: v for k, v in out["pcg64"].items() if k != "x_sample"}))
     print(json.dumps({k: v for k, v in out["xstar"].items() if k != "x_sample"}))
 

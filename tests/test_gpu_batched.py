@@ -30,12 +30,17 @@ def _solve_batched(solvers, rhs, pol, tol=1e-10, maxit=5000):
     return xs, infos
 
 
-@pytest.mark.parametrize("kind", ["amp16", "amp64_window", "fp64"])
+@pytest.mark.parametrize("kind", ["amp16", "amp16_lag", "amp64_window", "fp64"])
 def test_persistent_path_matches_oracle(kind):
     mats, rhs = W.batch_2d(10, seed=3, smin=16, smax=90)
     gp, op = {
         "amp16": (P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3),
                   oracle.Policy(u0=oracle.FP16, criterion=oracle.LINEAR, verify_refresh=3)),
+        # lagged power-of-two scale (reading R20)
+        "amp16_lag": (P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3,
+                               scale=P.SCALE_LINF_POW2_LAG),
+                      oracle.Policy(u0=oracle.FP16, criterion=oracle.LINEAR, verify_refresh=3,
+                                    scale=oracle.SCALE_LINF_POW2_LAG)),
         "amp64_window": (P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3),
                          oracle.Policy(u0=oracle.FP64, criterion=oracle.WINDOW, verify_refresh=3)),
         "fp64": (P.Policy.pcg64(), oracle.Policy(criterion=oracle.FIXED, fixed_uz=oracle.FP64,

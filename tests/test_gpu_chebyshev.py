@@ -96,3 +96,13 @@ def test_cheb_after_value_update():
     assert i1.iters == i2.iters and torch.equal(x1, x2)
     s.close()
     s2.close()
+
+
+def test_lagged_scale_is_refused_with_chebyshev():
+    a = W.diffusion3d(8, 1.0, 0)
+    s = P.Solver(a.rowptr, a.col, a.val, precond=P.M_CHEBYSHEV, degree=4)
+    b = torch.as_tensor(W.rhs_uniform(a.n, 1), device="cuda")
+    with pytest.raises(P.AmpcgError) as e:
+        s.solve(b, tol=1e-10, maxit=100, policy=P.Policy(scale=P.SCALE_LINF_POW2_LAG))
+    assert e.value.status == P.ERR_UNSUPPORTED
+    s.close()

@@ -88,7 +88,8 @@ def test_pcg64_config1_matches_oracle():
 
 
 @pytest.mark.parametrize("variant", ["amp16_linear", "amp16_window", "amp64_window", "amp_ur", "ds16",
-                                     "amp16_l2", "amp64_window_l2"])
+                                     "amp16_l2", "amp64_window_l2", "amp16_lag", "amp64_window_lag",
+                                     "ds16_lag"])
 @pytest.mark.parametrize("prob", ["poisson64", "diffusion24"])
 def test_ampcg_matches_oracle(variant, prob):
     a, b, kappa = _problem(prob)
@@ -97,6 +98,11 @@ def test_ampcg_matches_oracle(variant, prob):
         # omega_k = 1/||r_k|| as printed in Alg. 3 (reading R5's paper-faithful mode)
         "amp16_l2": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, scale=P.SCALE_L2),
         "amp64_window_l2": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, scale=P.SCALE_L2),
+        # lagged power of two (reading R20): the persistent kernel's three-barrier form
+        "amp16_lag": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, scale=P.SCALE_LINF_POW2_LAG),
+        "amp64_window_lag": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, scale=P.SCALE_LINF_POW2_LAG),
+        "ds16_lag": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64,
+                             scale=P.SCALE_LINF_POW2_LAG),
         "amp16_window": P.Policy(u0=P.FP16, criterion=P.CRIT_WINDOW),
         "amp64_window": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW),
         "amp_ur": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, tau_zs=0.0, tau_zh=0.0),
@@ -145,7 +151,7 @@ def bench_system():
     s.close()
 
 
-@pytest.mark.parametrize("which", ["amp16_linear", "phase2", "pcg64"])
+@pytest.mark.parametrize("which", ["amp16_linear", "phase2", "pcg64", "amp16_lag", "phase2_lag"])
 def test_first_iterations_at_benchmark_size(bench_system, which):
     # the 128^3 benchmark system: every warp of the persistent kernel owns 14
     # slices (two-slice trips, stage refills) and the matrix streams with the
@@ -154,7 +160,10 @@ def test_first_iterations_at_benchmark_size(bench_system, which):
     a, b, s = bench_system
     gp = {"amp16_linear": P.Policy(verify_refresh=3),
           "phase2": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32),
-          "pcg64": P.Policy.pcg64()}[which]
+          "pcg64": P.Policy.pcg64(),
+          "amp16_lag": P.Policy(verify_refresh=3, scale=P.SCALE_LINF_POW2_LAG),
+          "phase2_lag": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32,
+                                 scale=P.SCALE_LINF_POW2_LAG)}[which]
     assert s.layout()["stream_hint"] == 1
     bd = torch.as_tensor(b, device="cuda")
     for k in (1, 2, 5):
@@ -200,7 +209,8 @@ def test_repeated_solves_are_deterministic():
         assert torch.equal(x, outs[0][0])
 
 
-@pytest.mark.parametrize("kind", ["amp16", "amp64_window", "cheb", "wide_jacobi"])
+@pytest.mark.parametrize("kind", ["amp16", "amp16_lag", "amp64_window", "amp64_window_lag", "cheb",
+                                  "wide_jacobi", "wide_jacobi_lag", "pcg64"])
 def test_loop_graph_equals_kernel_by_kernel(kind):
     # the loop graph (SWITCH per precision change, inner loop of chunks) runs
     # the same kernels in the same order as the host-driven launches, for any
@@ -208,17 +218,22 @@ def test_loop_graph_equals_kernel_by_kernel(kind):
     # stop: the persistent iteration kernel (Jacobi, narrow slices), the
     # Chebyshev sequence, and the sequence with the cooperative precondition
     # + direction kernel (Jacobi, slices wider than 8)
-    if kind == "wide_jacobi":
+    if kind.startswith("wide_jacobi"):
         a = W.elasticity_q1(7, seed=2).to_csr()
     else:
         a = W.diffusion3d(20, 2.0, 6)
     b = torch.as_tensor(W.rhs_uniform(a.n, 8), device="cuda")
     kw = dict(precond=P.M_CHEBYSHEV, degree=4) if kind == "cheb" else {}
     s = P.Solver(a.rowptr, a.col, a.val, **kw)
-    pol = (P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3) if kind == "amp64_window"
-           else P.Policy(verify_refresh=3))
+    lag = P.SCALE_LINF_POW2_LAG
+    pol = {"amp64_window": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3),
+           "amp64_window_lag": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3, scale=lag),
+           "amp16_lag": P.Policy(verify_refresh=3, scale=lag),
+           "wide_jacobi_lag": P.Policy(verify_refresh=3, scale=lag),
+           "pcg64": P.Policy.pcg64(verify_refresh=3)}.get(kind, P.Policy(verify_refresh=3))
     x0, i0 = s.solve(b, tol=TOL, maxit=5000, policy=pol, timed=True)
-    assert i0.converged and (kind in ("cheb", "wide_jacobi") or any(k >= 0 for k in i0.switch_iter))
+    assert i0.converged
+    assert kind in ("cheb", "wide_jacobi", "wide_jacobi_lag", "pcg64") or any(k >= 0 for k in i0.switch_iter)
     for chunk in (1, 3, 16, 64):
         pol.graph_chunk = chunk
         x1, i1 = s.solve(b, tol=TOL, maxit=5000, policy=pol)
@@ -306,3 +321,40 @@ def test_status_codes():
     with pytest.raises(P.AmpcgError) as e:
         P.Solver(a.rowptr, bad, a.val)
     assert e.value.status == P.ERR_INVALID_ARG
+
+
+def _growth_system():
+    """The 2 x 2 system on which one Jacobi-PCG step takes the residual norm
+    from 1 to 8.9e4 (draw 13211 of the seeded family of the oracle's pin)."""
+    rng = np.random.default_rng(1)
+    for _ in range(13212):
+        th = rng.uniform(0, np.pi)
+        ev = np.exp(rng.uniform(-12, 2, 2))
+        sc = np.exp(rng.uniform(-6, 6, 2))
+        b = rng.standard_normal(2) * np.exp(rng.uniform(-6, 0, 2))
+    q = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    m = q @ np.diag(ev) @ q.T
+    m = (m + m.T) / 2 * np.outer(sc, sc)
+    return W.CSR(2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32), m.ravel().copy(), {}), b
+
+
+@pytest.mark.parametrize("timed", [False, True])
+def test_lagged_scale_retry_after_overflow(timed):
+    # y_1 = omega_1 r_1 with omega_1 from max|r_0| overflows binary16: the
+    # fused update's rho_1 is non-finite, the head step forms y_1, z_1, rho_1
+    # again with the exact power of two (reading R20); the run then equals the
+    # non-lagged one bit for bit, and the oracle's to rounding
+    a, b = _growth_system()
+    s = P.Solver(a.rowptr, a.col, a.val)
+    bd = torch.as_tensor(b, device="cuda")
+    base = dict(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64)
+    xl, il = s.solve(bd, tol=1e-30, maxit=2, policy=P.Policy(scale=P.SCALE_LINF_POW2_LAG, **base), timed=timed)
+    xe, ie = s.solve(bd, tol=1e-30, maxit=2, policy=P.Policy(scale=P.SCALE_LINF_POW2, **base), timed=timed)
+    s.close()
+    ref = oracle.ampcg(a.rowptr, a.col, a.val, b, tol=1e-30, maxit=2, policy=oracle.Policy(
+        scale=oracle.SCALE_LINF_POW2_LAG, criterion=oracle.FIXED, fixed_uz=oracle.FP16, fixed_ur=oracle.FP64))
+    assert ref.scale_retries == 1
+    assert il.status == ie.status == P.NOT_CONVERGED and il.iters == ie.iters == 2
+    assert torch.equal(xl, xe) and np.array_equal(il.relres_hist, ie.relres_hist)
+    np.testing.assert_allclose(il.relres_hist, ref.relres_hist, rtol=1e-12)
+    np.testing.assert_allclose(xl.cpu().numpy(), ref.x, rtol=1e-12)
