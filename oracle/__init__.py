@@ -56,7 +56,7 @@ class _Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("converged", C.c_int),
                 ("refreshes", C.c_int), ("true_relres", C.c_double),
                 ("updated_relres", C.c_double), ("switch_iter", C.c_int * 3),
-                ("scale_retries", C.c_int)]
+                ("scale_retries", C.c_int), ("y16_small", C.c_int64), ("y16_total", C.c_int64)]
 
 
 _lib = None
@@ -163,6 +163,8 @@ class Result:
     relres_hist: np.ndarray = field(repr=False)
     prec_hist: np.ndarray = field(repr=False)
     scale_retries: int = 0
+    y16_small: int = 0      # binary16 y_i below the normal range while r_i != 0 (summed over iterations)
+    y16_total: int = 0      # binary16 y_i with r_i != 0
 
 
 def round16(v):
@@ -301,7 +303,7 @@ def _result(res, x, rh, ph):
     it = res.iters
     return Result(res.status, it, bool(res.converged), res.refreshes, res.true_relres,
                   res.updated_relres, tuple(res.switch_iter), x, rh[: it + 1].copy(),
-                  ph[:it].copy(), res.scale_retries)
+                  ph[:it].copy(), res.scale_retries, res.y16_small, res.y16_total)
 
 
 def pcg64(rowptr, col, val, b, x0=None, tol=1e-10, maxit=2000, jacobi=True) -> Result:

@@ -287,6 +287,8 @@ typedef struct {
   double updated_relres;
   int switch_iter[3]; /* u_z -> FP32, u_z -> FP16, u_r -> FP32; -1 if none */
   int scale_retries;  /* R20: iterations whose scaling was formed again */
+  int64_t y16_small;  /* binary16 y_i below the normal range (subnormal or 0) while r_i != 0 */
+  int64_t y16_total;  /* binary16 y_i with r_i != 0 (both summed over the iterations) */
 } oracle_result;
 
 /* Chebyshev data for M^-1 = D^-1/2 P(Ahat) D^-1/2 (see oracle_cheb_apply). */
@@ -397,13 +399,21 @@ static void apply_precond(int mtype, int64_t n, int uz, const double* dinv_u,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 3 scaling (R6): y_i = round_uz( fl_ur(omega * r_i) ).               */
-static void scale_to_y(int64_t n, int uz, int ur, double omega, const double* r, double* y) {
+/* Alg. 3 scaling (R6): y_i = round_uz( fl_ur(omega * r_i) ).  With binary16
+ * storage, counts[0] += the y_i with r_i != 0 that fall below binary16's
+ * normal range (2^-14: subnormal or flushed to zero), counts[1] += the y_i
+ * with r_i != 0 (diagnostics for the choice of omega; no effect on y).     */
+static void scale_to_y(int64_t n, int uz, int ur, double omega, const double* r, double* y,
+                       int64_t* counts) {
   double omega_r = oracle_round(ur, omega);
   for (int64_t i = 0; i < n; ++i) {
     double prod = (ur == OR_FP64) ? omega * r[i] : mul32(omega_r, r[i]);
     if (ur == OR_FP16) prod = oracle_round16(prod);
     y[i] = oracle_round(uz, prod);
+    if (counts && uz == OR_FP16 && r[i] != 0.0) {
+      counts[1]++;
+      if (fabs(y[i]) < 6.103515625e-05) counts[0]++;   /* 2^-14 */
+    }
   }
 }
 
@@ -418,7 +428,7 @@ int oracle_scale_precond(int64_t n, const int32_t* rowptr, const int32_t* col,
   double *dinv = w, *y = w + n;
   csr_diag(n, rowptr, col, val, dinv);
   for (int64_t i = 0; i < n; ++i) dinv[i] = oracle_round(uz, 1.0 / dinv[i]);
-  scale_to_y(n, uz, ur, omega, r, y);
+  scale_to_y(n, uz, ur, omega, r, y, NULL);
   apply_precond(mtype, n, uz, dinv, y, z);
   free(w);
   return OR_OK;
@@ -438,7 +448,7 @@ int oracle_scale_cheb(int64_t n, const int32_t* rowptr, const int32_t* col,
   for (int64_t i = 0; i < n; ++i)
     for (int32_t kk = rowptr[i]; kk < rowptr[i + 1]; ++kk)
       ah[kk] = dsi[i] * val[kk] * dsi[col[kk]];
-  scale_to_y(n, uz, ur, omega, r, y);
+  scale_to_y(n, uz, ur, omega, r, y, NULL);
   int st = oracle_cheb_apply_public(n, nnz, rowptr, col, ah, dsi, degree, lmin, lmax, uz, y, z);
   free(w);
   return st;
@@ -622,7 +632,10 @@ int oracle_ampcg(int64_t n, const int32_t* rowptr, const int32_t* col,
     double omega = oracle_scale(pol->scale, delta[k], lag ? maxr_prev : maxr);
     double rho = 0.0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-      scale_to_y(n, uz, ur, omega, r, y);
+      int64_t counts[2] = {0, 0};
+      scale_to_y(n, uz, ur, omega, r, y, counts);
+      res->y16_small += counts[0];
+      res->y16_total += counts[1];
       /* preconditioning: z_k = M^-1 y_k in u_z */
       if (mtype == OR_M_CHEBYSHEV)
         oracle_cheb_apply(n, rowptr, col, &ch, uz, y, z, w0, w1, w2, w3);

@@ -179,3 +179,16 @@ def test_lagged_scale_retries_with_the_exact_power_after_overflow():
     assert lag.scale_retries == 1 and exact.scale_retries == 0
     assert lag.status == exact.status == oracle.NOT_CONVERGED and lag.iters == 2
     assert np.array_equal(lag.x, exact.x) and np.array_equal(lag.relres_hist, exact.relres_hist)
+
+
+def test_binary16_underflow_count_of_the_scaling_step():
+    # one iteration on a diagonal system: the counts cover y_0 = round16(omega_0 r_0)
+    # with r_0 = b, omega_0 = 2^-ceil(log2 max|b|) = 2^-1 here
+    b = np.array([1.5, 2.0 ** -20, 2.0 ** -10, 0.0, 3e-5, -1e-6, 0.25, 2.0 ** -13])
+    n = b.size
+    a = W.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n), {})
+    r = _amp(a, b, criterion=oracle.FIXED, fixed_uz=oracle.FP16, fixed_ur=oracle.FP64, maxit=1, tol=1e-30,
+             scale=oracle.SCALE_LINF_POW2, precond=oracle.M_NONE)
+    y = b * 0.5
+    assert r.y16_total == np.count_nonzero(b)
+    assert r.y16_small == np.count_nonzero((b != 0) & (np.abs(y) < 2.0 ** -14))
