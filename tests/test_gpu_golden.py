@@ -1,0 +1,72 @@
+"""The benchmark solve itself (128^3 high-contrast diffusion, 2,097,152
+unknowns) against the oracle's own solves of the same system, stored in
+tests/golden/c2_diffusion128.json by tests/golden/make_c2_golden.py (which
+calls only the oracle).  The bars are the ones the method's parity is judged
+by: iterations within 5% of the oracle's (the reductions run in another order,
+so the trajectories part after hundreds of iterations), the u_r switch within
+the same 5%, an FP64-verified relative residual of 1e-10, and the solution
+within 1e-8 (relative, on 1000 fixed entries) of the oracle's solution and of
+x*, the oracle's FP64 PCG solution at 1e-13 (reading R11)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2505_04155_b300")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_diffusion128.json")
+
+
+@pytest.fixture(scope="module")
+def gold():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def system():
+    a = W.diffusion3d(128, 2.0, seed=0)
+    b = W.rhs_uniform(a.n, seed=1)
+    s = P.Solver(a.rowptr, a.col, a.val)
+    yield a, torch.as_tensor(b, device="cuda"), s
+    s.close()
+
+
+def _rel(u, v):
+    return float(np.linalg.norm(u - v) / np.linalg.norm(v))
+
+
+@pytest.mark.parametrize("key,scale", [("amp16_linear", P.SCALE_LINF_POW2),
+                                       ("amp16_linear_lag", P.SCALE_LINF_POW2_LAG)])
+def test_benchmark_amp_solve_matches_oracle(gold, system, key, scale):
+    a, bd, s = system
+    g = gold[key]
+    assert gold["n"] == a.n
+    x, info = s.solve(bd, tol=1e-10, maxit=20000, policy=P.Policy(verify_refresh=3, scale=scale))
+    assert info.converged and info.true_relres <= 1e-10
+    assert abs(info.iters - g["iters"]) <= 0.05 * g["iters"], (info.iters, g["iters"])
+    assert info.switch_iter[0] == g["switch_iter"][0] == -1 and info.switch_iter[1] == g["switch_iter"][1]
+    assert abs(info.switch_iter[2] - g["switch_iter"][2]) <= 0.05 * g["switch_iter"][2], \
+        (info.switch_iter, g["switch_iter"])
+    np.testing.assert_allclose(info.relres_hist[:100], g["relres_hist_100"], rtol=1e-6)
+    idx = np.asarray(gold["sample_idx"])
+    xs = x.cpu().numpy()[idx]
+    assert _rel(xs, np.asarray(g["x_sample"])) <= 1e-8
+    assert _rel(xs, np.asarray(gold["xstar"]["x_sample"])) <= 1e-8
+
+
+def test_benchmark_fp64_solve_matches_oracle(gold, system):
+    a, bd, s = system
+    g = gold["pcg64"]
+    x, info = s.solve(bd, tol=1e-10, maxit=20000, policy=P.Policy.pcg64())
+    assert info.converged and abs(info.iters - g["iters"]) <= 1, (info.iters, g["iters"])
+    idx = np.asarray(gold["sample_idx"])
+    xs = x.cpu().numpy()[idx]
+    assert _rel(xs, np.asarray(g["x_sample"])) <= 1e-8
+    assert _rel(xs, np.asarray(gold["xstar"]["x_sample"])) <= 1e-8
