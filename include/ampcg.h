@@ -154,7 +154,13 @@ ampcg_status ampcg_create_csr(ampcg_t* out, int64_t n, int64_t nnz, const int32_
  * scalar matrix of n = nb * bs rows (row I*bs + r takes row r of every block
  * of block row I), which then goes through the same validation and
  * preparation as ampcg_create_csr; all other calls see the scalar system
- * (vectors of length nb * bs, dL/dA in the expanded CSR order). */
+ * (vectors of length nb * bs, dL/dA in the expanded CSR order).  With bs = 3
+ * and rows wider than 8 entries the context also keeps a block-row layout
+ * (one block column index and 9 values per block, the values also as
+ * D^-1/2 A D^-1/2 for Chebyshev), which the Chebyshev steps and the
+ * SpMV of the kernel sequence use: one thread per block row gathers each
+ * block's 3 operands once for its 3 rows, in the same order of operations
+ * as the scalar layout (bitwise the same results). */
 ampcg_status ampcg_create_bsr(ampcg_t* out, int64_t nb, int bs, int64_t nnzb, const int32_t* browptr,
                               const int32_t* bcolind, const double* bvals,
                               const ampcg_precond_spec* M, void* cuda_stream);
@@ -295,6 +301,14 @@ ampcg_status ampcg_precond_apply(ampcg_t ctx, int uz, int ur, double omega, cons
  * or slices wider than 8 entries).  Synchronises the context's stream. */
 ampcg_status ampcg_spmv_loop_step(ampcg_t ctx, int uz, int ur, const void* p, void* q, double* gamma);
 
+/* q = A p with the block-row layout of a context created from 3 x 3 block
+ * CSR (ampcg_layout.block3 = 1): the FP64 or FP32 values, one fma per stored
+ * entry in ascending column order per row, accumulated in `prec` -- the same
+ * result as ampcg_spmv on the expanded matrix.  p, q: device arrays of n
+ * values in `prec`.  AMPCG_ERR_UNSUPPORTED without the block layout.
+ * Asynchronous on the context's stream. */
+ampcg_status ampcg_spmv_block(ampcg_t ctx, int prec, const void* p, void* q);
+
 /* r = b - A x in FP64 (the initial residual of Alg. 3): per row, an FP64 fused multiply-add
  * chain over the stored entries in ascending column order, subtracted from
  * b.  Device arrays of doubles.  Asynchronous on the context's stream. */
@@ -349,6 +363,63 @@ ampcg_status ampcg_selector_trace_noalloc(const ampcg_policy* policy, const doub
  * synchronous on the legacy default stream. */
 ampcg_status ampcg_barrier_check(int nblocks, int absent_block, long long spin_limit);
 
+/* Autotuning of the persistent iteration kernel (Jacobi or no
+ * preconditioner, slices at most 8 wide; not from the paper).  For each
+ * precision pair ph = 2 u_z + u_r the kernel runs either the four-barrier
+ * iteration (scaling and preconditioning in their own step) or, where the
+ * scale mode allows it (AMPCG_SCALE_NONE, AMPCG_SCALE_LINF_POW2_LAG), the
+ * three-barrier one (z_{k+1}, rho_{k+1} formed in the update step and reduced
+ * with delta_{k+1}); both compute Alg. 3, their inner products differ only in
+ * summation order.  Without tuning the three-barrier form is used. */
+typedef struct {
+  int fused[6];        /* per pair: 1 three-barrier form, 0 four-barrier, -1 automatic */
+  double us_plain[6];  /* measured device time per iteration, four-barrier form (0: not timed) */
+  double us_fused[6];  /* the same, three-barrier form */
+  int iters;           /* iterations timed per form and pair */
+  int cached;          /* 1: taken from this process's cache of an equal matrix shape */
+  int reserved;        /* pairs measured (bit mask) */
+  int pad;
+} ampcg_tuning;
+
+/* Measures, on the context's own matrix and under the scale mode `scale`
+ * (AMPCG_SCALE_NONE or AMPCG_SCALE_LINF_POW2_LAG, the modes with two forms;
+ * AMPCG_ERR_INVALID_ARG otherwise), `iters` (1..10000) iterations of both
+ * forms for every pair in the bit mask `pairs` (bit ph; 0 = all six), as the
+ * difference of two fixed-pair solves of iters and 2 iters iterations (CUDA
+ * events; fixed costs cancel), keeps the faster form per pair in the context
+ * for later solves under that scale mode, and fills *out.  Results are cached
+ * per matrix shape (rows, entries, layout, preconditioner, device) and scale
+ * mode within the process: a later call for an equal shape reuses them
+ * (out->cached = 1).  Contexts without the persistent kernel get fused[] = -1
+ * and AMPCG_OK.  Allocates two vectors of n doubles; synchronous. */
+ampcg_status ampcg_tune(ampcg_t ctx, int scale, int iters, int pairs, ampcg_tuning* out);
+
+/* Applies the forms of t->fused[] (-1, 0 or 1 per pair) for solves under the
+ * scale mode `scale` (as ampcg_tune; for example a tuning saved from an
+ * earlier process); other fields are ignored. */
+ampcg_status ampcg_set_tuning(ampcg_t ctx, int scale, const ampcg_tuning* t);
+
+/* Autotuning of ampcg_solve_batched's persistent kernel (not from the paper):
+ * its block size, 1024 threads (one system per SM at a time) or 512 (two per
+ * SM, each with half the threads).  Runs the batch twice per candidate (the
+ * first a warm-up) with `iters` (1..10000) iterations per system under
+ * `policy` (NULL: default) on right-hand sides of ones, wall-clock timed, and
+ * stores the faster size in every system's context (the batch uses the size
+ * stored in its first eligible system).  Allocates 2 sum(n_i) doubles;
+ * synchronous. */
+typedef struct {
+  int block[2];      /* candidates: 1024, 512 */
+  double ms[2];      /* measured wall time of the batch per candidate */
+  int chosen;        /* the size stored */
+  int iters;
+} ampcg_batch_tuning;
+ampcg_status ampcg_tune_batched(int nsys, ampcg_t const* systems, const ampcg_policy* policy, int iters,
+                                ampcg_batch_tuning* out);
+
+/* Sets the batched kernel's block size for batches led by these contexts:
+ * 0 (default, 1024), 1024 or 512. */
+ampcg_status ampcg_set_batch_block(int nsys, ampcg_t const* systems, int block);
+
 /* Number of rows of the context's matrix, or -1 for NULL. */
 int64_t ampcg_rows(ampcg_t ctx);
 
@@ -368,7 +439,9 @@ typedef struct {
   int32_t maxw;            /* largest slice width */
   int32_t idx16;           /* 1: int16 column offsets, 0: int32 columns */
   int32_t stream_hint;     /* 1: matrix loads carry an L2 evict-first hint */
-  int32_t reserved;
+  int32_t block3;          /* 1: created from 3 x 3 block CSR; the Chebyshev steps and the
+                              SpMV of the kernel sequence use the block-row layout (one block
+                              column and 9 values per block, one thread per block row) */
 } ampcg_layout;
 ampcg_status ampcg_layout_stats(ampcg_t ctx, ampcg_layout* out);
 

@@ -44,7 +44,7 @@ class PrecondSpec(C.Structure):
 class LayoutC(C.Structure):
     _fields_ = [("n", C.c_int64), ("nslices", C.c_int64), ("stored", C.c_int64),
                 ("stored_uniform", C.c_int64), ("maxw", C.c_int32), ("idx16", C.c_int32),
-                ("stream_hint", C.c_int32), ("reserved", C.c_int32)]
+                ("stream_hint", C.c_int32), ("block3", C.c_int32)]
 
 
 class PolicyC(C.Structure):
@@ -60,6 +60,15 @@ class ResultC(C.Structure):
                 ("switch_iter", C.c_int * 3), ("seconds", C.c_double),
                 ("relres_hist", C.POINTER(C.c_double)), ("prec_hist", C.POINTER(C.c_uint8)),
                 ("kernel_launches", C.c_int64)]
+
+
+class TuningC(C.Structure):
+    _fields_ = [("fused", C.c_int * 6), ("us_plain", C.c_double * 6), ("us_fused", C.c_double * 6),
+                ("iters", C.c_int), ("cached", C.c_int), ("reserved", C.c_int), ("pad", C.c_int)]
+
+
+class BatchTuningC(C.Structure):
+    _fields_ = [("block", C.c_int * 2), ("ms", C.c_double * 2), ("chosen", C.c_int), ("iters", C.c_int)]
 
 
 class KernelTimesC(C.Structure):
@@ -127,6 +136,8 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_precond_apply.restype = C.c_int
     lib.ampcg_spmv_loop_step.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.POINTER(C.c_double)]
     lib.ampcg_spmv_loop_step.restype = C.c_int
+    lib.ampcg_spmv_block.argtypes = [vp, C.c_int, vp, vp]
+    lib.ampcg_spmv_block.restype = C.c_int
     lib.ampcg_residual.argtypes = [vp, vp, vp, vp]
     lib.ampcg_residual.restype = C.c_int
     lib.ampcg_selector_trace.argtypes = [C.POINTER(PolicyC), dp, C.c_int, C.c_double, C.c_double,
@@ -135,6 +146,15 @@ def load_library(path: str = LIB_PATH):
     lib.ampcg_selector_trace_noalloc.argtypes = [C.POINTER(PolicyC), dp, C.c_int, C.c_double,
                                                  C.c_double, C.POINTER(C.c_uint8)]
     lib.ampcg_selector_trace_noalloc.restype = C.c_int
+    lib.ampcg_tune.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(TuningC)]
+    lib.ampcg_tune.restype = C.c_int
+    lib.ampcg_set_tuning.argtypes = [vp, C.c_int, C.POINTER(TuningC)]
+    lib.ampcg_set_tuning.restype = C.c_int
+    lib.ampcg_tune_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(PolicyC), C.c_int,
+                                       C.POINTER(BatchTuningC)]
+    lib.ampcg_tune_batched.restype = C.c_int
+    lib.ampcg_set_batch_block.argtypes = [C.c_int, C.POINTER(vp), C.c_int]
+    lib.ampcg_set_batch_block.restype = C.c_int
     lib.ampcg_barrier_check.argtypes = [C.c_int, C.c_int, C.c_longlong]
     lib.ampcg_barrier_check.restype = C.c_int
     lib.ampcg_rows.argtypes = [vp]
@@ -337,11 +357,33 @@ class Solver:
             info.kernel_total_ms = kt.total_ms
         return x, info
 
+    def tune(self, scale: int = SCALE_LINF_POW2_LAG, iters: int = 20, pairs=None) -> dict:
+        """Autotune the persistent iteration kernel's form per precision pair
+        for solves under `scale` (SCALE_NONE or SCALE_LINF_POW2_LAG;
+        ampcg_tune): pairs is an iterable of phase indices 2*u_z + u_r, or
+        None for all six.  Returns the choices and the measured times."""
+        mask = 0 if pairs is None else sum(1 << p for p in pairs)
+        t = TuningC()
+        _check(load_library().ampcg_tune(self._h, scale, iters, mask, C.byref(t)))
+        return {"fused": {phase_name(p): t.fused[p] for p in range(6) if t.fused[p] >= 0},
+                "us_four_barrier": {phase_name(p): round(t.us_plain[p], 2) for p in range(6) if t.us_plain[p] > 0},
+                "us_three_barrier": {phase_name(p): round(t.us_fused[p], 2) for p in range(6) if t.us_fused[p] > 0},
+                "iters": t.iters, "cached": bool(t.cached)}
+
+    def set_tuning(self, fused, scale: int = SCALE_LINF_POW2_LAG):
+        """Set the kernel form per pair for solves under `scale`
+        (ampcg_set_tuning): fused is a sequence of six values -1 (automatic),
+        0 (four barriers) or 1 (three)."""
+        t = TuningC()
+        for p in range(6):
+            t.fused[p] = int(fused[p])
+        _check(load_library().ampcg_set_tuning(self._h, scale, C.byref(t)))
+
     def layout(self) -> dict:
         """Storage statistics of the sliced layout (ampcg_layout_stats)."""
         out = LayoutC()
         _check(load_library().ampcg_layout_stats(self._h, C.byref(out)))
-        return {k: getattr(out, k) for k, _ in LayoutC._fields_ if k != "reserved"}
+        return {k: getattr(out, k) for k, _ in LayoutC._fields_}
 
     def interval(self):
         """The Chebyshev interval (lmin, lmax) in use (ampcg_precond_interval)."""
@@ -392,6 +434,11 @@ class Solver:
     def spmv(self, p, q, prec: int = FP64):
         """q = A p in FP64 or FP32 (device arrays)."""
         _check(load_library().ampcg_spmv(self._h, prec, _ptr(p), _ptr(q)))
+        return q
+
+    def spmv_block(self, p, q, prec: int = FP64):
+        """q = A p with the 3 x 3 block-row layout (ampcg_spmv_block; device arrays)."""
+        _check(load_library().ampcg_spmv_block(self._h, prec, _ptr(p), _ptr(q)))
         return q
 
     def spmv_loop_step(self, p, q, uz: int, ur: int) -> float:
@@ -473,3 +520,20 @@ def barrier_check(nblocks: int = 2, absent_block: int = -1, spin_limit: int = 1 
     (absent_block in [0, nblocks) never arrives).  Other statuses raise."""
     return _check(load_library().ampcg_barrier_check(nblocks, absent_block, spin_limit),
                   ok=(OK, ERR_TIMEOUT))
+
+
+def tune_batched(solvers, iters: int = 20, policy: Policy | None = None) -> dict:
+    """Autotune ampcg_solve_batched's block size for this batch (ampcg_tune_batched)."""
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s._h.value for s in solvers])
+    pol = (policy or Policy()).to_c()
+    t = BatchTuningC()
+    _check(load_library().ampcg_tune_batched(n, hs, C.byref(pol), iters, C.byref(t)))
+    return {"ms": {t.block[j]: round(t.ms[j], 3) for j in range(2)}, "chosen": t.chosen, "iters": t.iters}
+
+
+def set_batch_block(solvers, block: int):
+    """Block size of the batched kernel for batches led by these solvers (0, 1024 or 512)."""
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s._h.value for s in solvers])
+    _check(load_library().ampcg_set_batch_block(n, hs, block))

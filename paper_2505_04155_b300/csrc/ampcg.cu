@@ -26,6 +26,7 @@
 
 #include "../../include/ampcg.h"
 #include "batched.cuh"
+#include "bsr.cuh"
 #include "kernel_table.h"
 
 using namespace ampcg;
@@ -35,7 +36,10 @@ const void* loop_kernel(int uz, int ur, int mt, int it, bool fused) {
   if (mt == M_JACOBI) return fused ? loop_kernel_jacobi_fused(uz, ur, it) : loop_kernel_jacobi_plain(uz, ur, it);
   return fused ? loop_kernel_none_fused(uz, ur, it) : loop_kernel_none_plain(uz, ur, it);
 }
-const void* batched_kernel(int it) { return it ? batched_kernel_idx16() : batched_kernel_idx32(); }
+const void* batched_kernel(int it, int bs) {
+  if (bs == kBatchBlockSmall) return it ? batched_kernel_idx16_b512() : batched_kernel_idx32_b512();
+  return it ? batched_kernel_idx16_b1024() : batched_kernel_idx32_b1024();
+}
 }  // namespace ampcg
 
 namespace {
@@ -87,7 +91,7 @@ ampcg_status dalloc(T** p, size_t count) {
 // One kernel launch of an iteration: function, launch shape, argument list
 // kind, timing slot (0 precondition, 1 search direction, 2 SpMV, 3 update)
 // and, for a Chebyshev step, its index and constants.
-enum { KA_ELEM = 0, KA_SPMV, KA_UPD, KA_CINIT, KA_CSTEP, KA_CFINAL, KA_LOOP };
+enum { KA_ELEM = 0, KA_SPMV, KA_UPD, KA_CINIT, KA_CSTEP, KA_CFINAL, KA_LOOP, KA_BSPMV, KA_BCSTEP };
 struct Launch {
   const void* fn;
   int grid, smem, kind, slot, j;
@@ -141,7 +145,12 @@ struct ampcg_ctx {
   Launch loop[2][6];      // [fused][pair]: four or three grid barriers per iteration
   bool loop_ok = true;    // every pair's k_loop configured (set while building)
   bool use_loop = false;
-  bool fused = false;     // the current solve's scale mode lets k_loop fuse (SCALE_NONE, LINF_POW2_LAG)
+  // k_loop form per pair for the scale modes that allow the three-barrier
+  // one ([0] SCALE_NONE, [1] LINF_POW2_LAG): -1 automatic (three barriers),
+  // 0 four, 1 three; set by ampcg_tune / ampcg_set_tuning
+  int loop_form[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
+  unsigned fused_mask = 0;   // the current solve's forms: bit ph set = three-barrier k_loop for pair ph
+  int batch_block = 0;       // block size of the batched kernel for batches led by this context (0: 1024)
   // Chebyshev preconditioner data (reading R8)
   int cheb_m = 0;
   int cheb_auto = 0;            // interval from the Gershgorin bound
@@ -163,11 +172,37 @@ struct ampcg_ctx {
     C.inv_theta = cheb_inv_theta;
     return C;
   }
+  // block-row layout of a 3 x 3 block matrix (bsr.cuh), when created from
+  // block CSR with bs = 3 and wide rows
+  bool bs3 = false;
+  int64_t nb3 = 0, nbs3 = 0, bstored = 0;
+  long long* boff = nullptr;
+  int* bw = nullptr;
+  int* bcol3 = nullptr;
+  double* bv64 = nullptr;
+  float* bv32 = nullptr;
+  double* bah64 = nullptr;
+  float* bah32 = nullptr;
+  __half* bah16 = nullptr;
+  BSell bsell() const {
+    BSell A;
+    A.nb = nb3;
+    A.nbs = nbs3;
+    A.boff = boff;
+    A.bw = bw;
+    A.bcol = bcol3;
+    A.v64 = bv64;
+    A.v32 = bv32;
+    A.ah64 = bah64;
+    A.ah32 = bah32;
+    A.ah16 = bah16;
+    return A;
+  }
   // device-side loop graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_chunk = 0;
-  bool graph_fused = false;
+  unsigned graph_fused = 0;
 
   Sell sell() const {
     Sell A;
@@ -213,7 +248,8 @@ static void release(ampcg_ctx* c) {
   void* ptrs[] = {c->ah64, c->ah32, c->ah16, c->ahp, c->ds64, c->ds32, c->ds16, c->cres, c->cd0, c->cd1, c->cu,
                   c->rowptr, c->off, c->width, c->cabs, c->coff, c->pat, c->rmask, c->v64, c->v32, c->dinv64, c->dinv32,
                   c->dinv16, c->x, c->b, c->r64, c->t, c->r32, c->z, c->p0, c->p1, c->q,
-                  c->part, c->pmax, c->bar, c->st, c->dhist, c->phist};
+                  c->part, c->pmax, c->bar, c->st, c->dhist, c->phist, c->boff, c->bw, c->bcol3, c->bv64,
+                  c->bv32, c->bah64, c->bah32, c->bah16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hst) cudaFreeHost(c->hst);
@@ -285,6 +321,7 @@ ampcg_status ampcg_layout_stats(ampcg_t c, ampcg_layout* out) {
   out->maxw = c->maxw;
   out->idx16 = c->idx16;
   out->stream_hint = c->stream_hint;
+  out->block3 = c->bs3 ? 1 : 0;
   if (c->pat) {
     std::vector<short> pat((size_t)c->nslices * kStageW);
     std::vector<int> w((size_t)c->nslices);
@@ -479,7 +516,7 @@ static ampcg_status create_impl(ampcg_ctx* c, int64_t n, int64_t nnz, const int3
   }
   int gi = occ_grid((const void*)k_init<0>, sms, rows_pad);
   if (gi > c->g_max) c->g_max = gi;
-  TRY(dalloc(&c->part, (size_t)c->g_max * 4));
+  TRY(dalloc(&c->part, (size_t)c->g_max * 6));   // the grid barriers' partials (device_util.cuh)
   TRY(dalloc(&c->pmax, (size_t)c->g_max * 2));   // two halves for the grid barriers
   TRY(dalloc(&c->bar, 12));
   TRY(dalloc(&c->st, 1));
@@ -585,9 +622,13 @@ static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
   v.clear();
   if constexpr (MT == M_CHEBYSHEV) {
     add((const void*)k_cheb_init<UZ, UR>, KA_CINIT, 0, n, 0);
-    for (int j = 1; j < c->cheb_m; ++j)
-      add((const void*)k_cheb_step<UZ, UR, IT>, KA_CSTEP, 0, c->nslices * 32, 0, j, c->cheb_c1[j - 1],
-          c->cheb_c2[j - 1]);
+    for (int j = 1; j < c->cheb_m; ++j) {
+      if (c->bs3)
+        add(bsr_cheb_kernel(UZ, UR), KA_BCSTEP, 0, c->nbs3 * 32, 0, j, c->cheb_c1[j - 1], c->cheb_c2[j - 1]);
+      else
+        add((const void*)k_cheb_step<UZ, UR, IT>, KA_CSTEP, 0, c->nslices * 32, 0, j, c->cheb_c1[j - 1],
+            c->cheb_c2[j - 1]);
+    }
     add((const void*)k_cheb_final<UZ, UR>, KA_CFINAL, 0, n, 0);
     add((const void*)k_axpy<UZ, UR>, KA_ELEM, 1, nvec, 0);
   } else {
@@ -598,8 +639,11 @@ static void phase_seq(ampcg_ctx* c, int sms, std::vector<Launch>& v) {
   }
   const bool wide = c->maxw > kStageW;
   const int sm = wide ? 0 : staged_smem_bytes<UR, IT>();
-  add(wide ? (const void*)k_spmv<UZ, UR, IT, true> : (const void*)k_spmv<UZ, UR, IT, false>, KA_SPMV, 2,
-      c->nslices * 32, sm);
+  if (c->bs3)
+    add(bsr_spmv_kernel(UZ, UR), KA_BSPMV, 2, c->nbs3 * 32, 0);
+  else
+    add(wide ? (const void*)k_spmv<UZ, UR, IT, true> : (const void*)k_spmv<UZ, UR, IT, false>, KA_SPMV, 2,
+        c->nslices * 32, sm);
   if (sm > 0) {
     // staged SpMV: a warp takes at most 32 slices, so at least nslices/32 warps
     int need = (int)((c->nslices + 32 * 8 - 1) / (32 * 8));
@@ -709,6 +753,7 @@ static ampcg_status cheb_prepare(ampcg_ctx* c) {
 struct ArgPack {
   Bufs B;
   Sell A;
+  BSell BA;
   Cheb C;
   int64_t n;
   DevState* st;
@@ -716,7 +761,8 @@ struct ArgPack {
   double c1, c2;
   void* a[8];
   explicit ArgPack(const ampcg_ctx* c, int it = 1)
-      : B(c->bufs()), A(c->sell()), C(c->cheb()), n(c->n), st(c->st), j(0), iters(it), c1(0), c2(0) {}
+      : B(c->bufs()), A(c->sell()), BA(c->bsell()), C(c->cheb()), n(c->n), st(c->st), j(0), iters(it), c1(0),
+        c2(0) {}
   void** args(const Launch& L) {
     switch (L.kind) {
       case KA_ELEM:
@@ -729,6 +775,11 @@ struct ArgPack {
         j = L.j; c1 = L.c1; c2 = L.c2;
         a[0] = &A; a[1] = &C; a[2] = &st; a[3] = &j; a[4] = &c1; a[5] = &c2;
         break;
+      case KA_BSPMV: a[0] = &BA; a[1] = &B; a[2] = &st; break;
+      case KA_BCSTEP:
+        j = L.j; c1 = L.c1; c2 = L.c2;
+        a[0] = &BA; a[1] = &C; a[2] = &st; a[3] = &j; a[4] = &c1; a[5] = &c2;
+        break;
     }
     return a;
   }
@@ -740,7 +791,7 @@ struct ArgPack {
 // The launches of one iteration of phase ph: k_loop (one iteration) where it
 // applies, else the phase's kernel sequence.
 static std::vector<Launch> iteration_launches(const ampcg_ctx* c, int ph) {
-  if (c->use_loop) return {c->loop[c->fused ? 1 : 0][ph]};
+  if (c->use_loop) return {c->loop[(c->fused_mask >> ph) & 1u][ph]};
   return c->seq[ph];
 }
 
@@ -788,7 +839,7 @@ static cudaError_t add_kernel_node(cudaGraphNode_t* node, cudaGraph_t g, const c
 // chunk, the chunk's remaining launches return at entry (phase_mismatch,
 // done).
 static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
-  if (c->gexec && c->graph_chunk == chunk && c->graph_fused == c->fused) return AMPCG_OK;
+  if (c->gexec && c->graph_chunk == chunk && c->graph_fused == c->fused_mask) return AMPCG_OK;
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
   CUDA_TRY(cudaGraphCreate(&c->graph, 0));
@@ -854,7 +905,7 @@ static ampcg_status ensure_graph(ampcg_ctx* c, int chunk) {
   CUDA_TRY(add_kernel_node(&cnode, body, &snode, (const void*)k_loop_ctl, 1, 1, actl));
   CUDA_TRY(cudaGraphInstantiate(&c->gexec, c->graph, 0));
   c->graph_chunk = chunk;
-  c->graph_fused = c->fused;
+  c->graph_fused = c->fused_mask;
   return AMPCG_OK;
 }
 
@@ -964,8 +1015,13 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   // return at entry but still cost a launch each)
   int chunk = pol.graph_chunk > 0 ? pol.graph_chunk : (c->use_loop ? kLoopChunk : kSeqChunk);
   // the persistent kernel's three-barrier form where omega_{k+1} is known
-  // before delta_{k+1} is reduced
-  c->fused = pol.scale == AMPCG_SCALE_NONE || pol.scale == AMPCG_SCALE_LINF_POW2_LAG;
+  // before delta_{k+1} is reduced, per pair as tuned (automatic: three)
+  c->fused_mask = 0;
+  if (pol.scale == AMPCG_SCALE_NONE || pol.scale == AMPCG_SCALE_LINF_POW2_LAG) {
+    const int* form = c->loop_form[pol.scale == AMPCG_SCALE_NONE ? 0 : 1];
+    for (int ph = 0; ph < 6; ++ph)
+      if (form[ph] != 0) c->fused_mask |= 1u << ph;
+  }
   cudaSetDevice(c->device);
   cudaStream_t s = s_override ? s_override : c->stream;
   ampcg_status hs = ensure_hist(c, maxit);
@@ -1160,6 +1216,20 @@ extern "C" ampcg_status ampcg_spmv_loop_step(ampcg_t c, int uz, int ur, const vo
     for (int i = 0; i < G; ++i) g += part[(size_t)i];
     *gamma = g;
   }
+  return AMPCG_OK;
+}
+
+extern "C" ampcg_status ampcg_spmv_block(ampcg_t c, int prec, const void* p, void* q) {
+  if (!c || !p || !q) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  if (prec != AMPCG_FP64 && prec != AMPCG_FP32) return fail(AMPCG_ERR_INVALID_ARG, "block spmv precision must be FP64 or FP32");
+  if (!c->bs3) return fail(AMPCG_ERR_UNSUPPORTED, "the context has no 3 x 3 block layout");
+  BSell A = c->bsell();
+  void* args[3] = {&A, const_cast<void**>(&p), &q};
+  const void* fn = bsr_spmv_step_kernel(prec);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int grid = occ_grid(fn, sms, c->nbs3 * 32);
+  CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, 0, c->stream));
   return AMPCG_OK;
 }
 
@@ -1465,6 +1535,74 @@ extern "C" ampcg_status ampcg_barrier_check(int nblocks, int absent_block, long 
 // ---------------------------------------------------------------------------
 // New values on the same pattern, and the adjoint solve.
 
+// Block-row layout of a 3 x 3 block matrix (bsr.cuh): values (and the
+// Chebyshev Ahat copies) from the scalar sliced layout, after creation and
+// after every value change.
+static ampcg_status fill_block_layout(ampcg_ctx* c) {
+  if (!c->bs3) return AMPCG_OK;
+  const int gb = (int)((c->nbs3 * 32 + kBlock - 1) / kBlock);
+  const bool ch = c->mtype == M_CHEBYSHEV;
+  if (c->idx16)
+    k_bfill<1><<<gb, kBlock, 0, c->stream>>>(c->sell(), c->rowptr, c->bsell(), c->bcol3, c->bv64, c->bv32,
+                                             ch ? c->ah64 : nullptr, ch ? c->bah64 : nullptr, c->bah32, c->bah16);
+  else
+    k_bfill<0><<<gb, kBlock, 0, c->stream>>>(c->sell(), c->rowptr, c->bsell(), c->bcol3, c->bv64, c->bv32,
+                                             ch ? c->ah64 : nullptr, ch ? c->bah64 : nullptr, c->bah32, c->bah16);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return AMPCG_OK;
+}
+
+static ampcg_status build_block_layout(ampcg_ctx* c) {
+  cudaStream_t s = c->stream;
+  c->nb3 = c->n / 3;
+  c->nbs3 = (c->nb3 + 31) / 32;
+  long long* total = nullptr;
+  ampcg_status st;
+  if ((st = dalloc(&c->bw, c->nbs3)) != AMPCG_OK) return st;
+  if ((st = dalloc(&c->boff, c->nbs3)) != AMPCG_OK) return st;
+  if ((st = dalloc(&total, 2)) != AMPCG_OK) return st;
+  const int gs = (int)((c->nbs3 + kBlock - 1) / kBlock);
+  k_bslice_width<<<gs, kBlock, 0, s>>>(c->nb3, c->nbs3, c->rowptr, c->bw);
+  k_slice_offsets<<<1, 1024, 0, s>>>(c->nbs3, c->bw, c->boff, total);
+  long long tot2[2] = {0, 0};
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tot2, total, sizeof(tot2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(total);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "block layout: %s", cudaGetErrorString(e));
+  c->bstored = tot2[0];
+  if ((st = dalloc(&c->bcol3, c->bstored)) != AMPCG_OK) return st;
+  if ((st = dalloc(&c->bv64, 9 * c->bstored)) != AMPCG_OK) return st;
+  if ((st = dalloc(&c->bv32, 9 * c->bstored)) != AMPCG_OK) return st;
+  if (c->mtype == M_CHEBYSHEV) {
+    if ((st = dalloc(&c->bah64, 9 * c->bstored)) != AMPCG_OK) return st;
+    if ((st = dalloc(&c->bah32, 9 * c->bstored)) != AMPCG_OK) return st;
+    if ((st = dalloc(&c->bah16, 9 * c->bstored)) != AMPCG_OK) return st;
+  }
+  c->bs3 = true;
+  if ((st = fill_block_layout(c)) != AMPCG_OK) return st;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  if ((st = build_sequences(c, sms)) != AMPCG_OK) return st;
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  // the block kernels' grids must fit the per-block partial arrays
+  int gmax = c->g_max;
+  for (int ph = 0; ph < 6; ++ph)
+    for (const Launch& L : c->seq[ph]) gmax = L.grid > gmax ? L.grid : gmax;
+  if (gmax > c->g_max) {
+    cudaFree(c->part);
+    cudaFree(c->pmax);
+    c->part = nullptr;
+    c->pmax = nullptr;
+    c->g_max = gmax;
+    if ((st = dalloc(&c->part, (size_t)c->g_max * 6)) != AMPCG_OK) return st;
+    if ((st = dalloc(&c->pmax, (size_t)c->g_max * 2)) != AMPCG_OK) return st;
+  }
+  return AMPCG_OK;
+}
+
 // After new matrix values: the Chebyshev data follow A; with an automatic
 // interval the constants change, so the launch sequences and the loop graph
 // are rebuilt.
@@ -1521,7 +1659,8 @@ extern "C" ampcg_status ampcg_update_values(ampcg_t c, const double* vals) {
   if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "update values: %s", cudaGetErrorString(e));
   if (hf & 8) return fail(AMPCG_ERR_NONFINITE, "matrix has non-finite values (context now holds them)");
   if (hf & 4) return fail(AMPCG_ERR_NOT_SPD, "a diagonal entry is not positive (context now holds it)");
-  return refresh_precond(c);
+  ampcg_status ps = refresh_precond(c);
+  return ps != AMPCG_OK ? ps : fill_block_layout(c);
 }
 
 extern "C" ampcg_status ampcg_adjoint(ampcg_t c, const double* x, const double* dLdx, double tol,
@@ -1593,7 +1732,8 @@ extern "C" ampcg_status ampcg_assemble_log_coeff(ampcg_t c, const double* theta,
   cudaFree(flags);
   if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "assemble: %s", cudaGetErrorString(e));
   if (hf & 4) return fail(AMPCG_ERR_INVALID_ARG, "a row has no stored diagonal entry");
-  return refresh_precond(c);
+  ampcg_status ps = refresh_precond(c);
+  return ps != AMPCG_OK ? ps : fill_block_layout(c);
 }
 
 extern "C" ampcg_status ampcg_grad_log_coeff(ampcg_t c, const double* x, const double* lambda,
@@ -1671,9 +1811,161 @@ extern "C" ampcg_status ampcg_create_bsr(ampcg_t* out, int64_t nb, int bs, int64
   }
   st = ampcg_create_csr(out, n, nnz, d_rp, d_c, d_v, M, cuda_stream);
   cleanup();
+  if (st != AMPCG_OK) return st;
+  // 3 x 3 blocks in rows wider than the staged path's slices (which would keep
+  // the scalar layout's uniform-offset slices): the block-row kernels
+  if (bs == 3 && (*out)->maxw > kStageW && !(*out)->use_loop) {
+    ampcg_layout lay;
+    st = ampcg_layout_stats(*out, &lay);
+    if (st == AMPCG_OK && lay.stored_uniform == 0) st = build_block_layout(*out);
+    if (st != AMPCG_OK) {
+      ampcg_destroy(*out);
+      *out = nullptr;
+    }
+  }
   return st;
 }
 
+
+// ---------------------------------------------------------------------------
+// Autotuning of the persistent iteration kernel's form.
+//
+// Per precision pair the kernel can run the four-barrier iteration (the
+// scaling and preconditioning in their own step) or, where the scale mode
+// allows, the three-barrier one (z_{k+1}, rho_{k+1} formed in the update step
+// and reduced with delta_{k+1}).  Which is faster depends on the pair and the
+// matrix: the three-barrier form saves a grid barrier but writes and re-reads
+// z in u_z (2 bytes a row in binary16, 8 in binary64).  ampcg_tune measures
+// both on the context's own matrix and keeps the faster; results are cached
+// per matrix shape within the process.
+
+namespace {
+struct TuneKey {
+  int device;
+  int64_t n, nnz, stored;
+  int maxw, idx16, mtype, scale;
+  bool operator==(const TuneKey& o) const {
+    return device == o.device && n == o.n && nnz == o.nnz && stored == o.stored && maxw == o.maxw &&
+           idx16 == o.idx16 && mtype == o.mtype && scale == o.scale;
+  }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, ampcg_tuning>> g_tune_cache;
+
+TuneKey tune_key(const ampcg_ctx* c, int scale) {
+  return TuneKey{c->device, c->n, c->nnz, c->stored, c->maxw, c->idx16, c->mtype, scale};
+}
+
+// Device time of `maxit` iterations of one fixed pair (plus the fixed costs
+// of a solve: copies, initial and true residual), CUDA events on the
+// context's stream.
+ampcg_status time_fixed_pair(ampcg_ctx* c, int ph, int scale, int maxit, const double* b, double* x,
+                             float* ms) {
+  ampcg_policy pol;
+  ampcg_policy_default(&pol);
+  pol.criterion = AMPCG_CRIT_FIXED;
+  pol.fixed_uz = ph / 2;
+  pol.fixed_ur = ph % 2;
+  pol.scale = scale;
+  pol.verify_refresh = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(AMPCG_ERR_CUDA, "event creation failed");
+  }
+  ampcg_result res;
+  memset(&res, 0, sizeof(res));
+  cudaEventRecord(e0, c->stream);
+  ampcg_status st = solve_impl(c, b, x, 1e-300, maxit, &pol, &res, nullptr);
+  cudaEventRecord(e1, c->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != AMPCG_OK && st != AMPCG_NOT_CONVERGED) return st;
+  if (res.iters != maxit) return fail(AMPCG_ERR_CUDA, "tuning solve stopped after %d of %d iterations", res.iters, maxit);
+  if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "tuning events: %s", cudaGetErrorString(e));
+  return AMPCG_OK;
+}
+}  // namespace
+
+static int scale_slot(int scale) {
+  return scale == AMPCG_SCALE_NONE ? 0 : (scale == AMPCG_SCALE_LINF_POW2_LAG ? 1 : -1);
+}
+
+extern "C" ampcg_status ampcg_set_tuning(ampcg_t c, int scale, const ampcg_tuning* t) {
+  if (!c || !t) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  const int sl = scale_slot(scale);
+  if (sl < 0) return fail(AMPCG_ERR_INVALID_ARG, "only AMPCG_SCALE_NONE and AMPCG_SCALE_LINF_POW2_LAG have two forms");
+  for (int ph = 0; ph < 6; ++ph)
+    if (t->fused[ph] < -1 || t->fused[ph] > 1) return fail(AMPCG_ERR_INVALID_ARG, "fused[%d] must be -1, 0 or 1", ph);
+  for (int ph = 0; ph < 6; ++ph) c->loop_form[sl][ph] = t->fused[ph];
+  return AMPCG_OK;
+}
+
+extern "C" ampcg_status ampcg_tune(ampcg_t c, int scale, int iters, int pairs, ampcg_tuning* out) {
+  if (!c || !out) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
+  const int sl = scale_slot(scale);
+  if (sl < 0) return fail(AMPCG_ERR_INVALID_ARG, "only AMPCG_SCALE_NONE and AMPCG_SCALE_LINF_POW2_LAG have two forms");
+  if (iters < 1 || iters > 10000) return fail(AMPCG_ERR_INVALID_ARG, "iters must be in [1, 10000]");
+  if (pairs < 0 || pairs > 63) return fail(AMPCG_ERR_INVALID_ARG, "pairs is a mask of 6 bits");
+  if (pairs == 0) pairs = 63;
+  memset(out, 0, sizeof(*out));
+  for (int ph = 0; ph < 6; ++ph) out->fused[ph] = -1;
+  out->iters = iters;
+  if (!c->use_loop) return AMPCG_OK;   // no persistent iteration kernel: nothing to choose
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const TuneKey key = tune_key(c, scale);
+    for (auto& kv : g_tune_cache) {
+      if (kv.first == key && kv.second.iters == iters && (kv.second.reserved & pairs) == pairs) {
+        *out = kv.second;
+        out->cached = 1;
+        for (int ph = 0; ph < 6; ++ph)
+          if ((pairs >> ph) & 1) c->loop_form[sl][ph] = out->fused[ph];
+        return AMPCG_OK;
+      }
+    }
+  }
+  cudaSetDevice(c->device);
+  double* b = nullptr;
+  double* x = nullptr;
+  const size_t vb = (size_t)c->n * sizeof(double);
+  ampcg_status st = dalloc(&b, c->n);
+  if (st == AMPCG_OK) st = dalloc(&x, c->n);
+  std::vector<double> ones((size_t)c->n, 1.0);
+  if (st == AMPCG_OK && cudaMemcpy(b, ones.data(), vb, cudaMemcpyHostToDevice) != cudaSuccess)
+    st = fail(AMPCG_ERR_CUDA, "tuning right-hand side copy failed");
+  int saved[6];
+  for (int ph = 0; ph < 6; ++ph) saved[ph] = c->loop_form[sl][ph];
+  for (int ph = 0; ph < 6 && st == AMPCG_OK; ++ph) {
+    if (!((pairs >> ph) & 1)) continue;
+    double us[2] = {0.0, 0.0};
+    for (int f = 0; f < 2 && st == AMPCG_OK; ++f) {
+      c->loop_form[sl][ph] = f;
+      float t1 = 0.f, t2 = 0.f, w = 0.f;
+      st = time_fixed_pair(c, ph, scale, iters, b, x, &w);   // warm-up (graph build)
+      if (st == AMPCG_OK) st = time_fixed_pair(c, ph, scale, iters, b, x, &t1);
+      if (st == AMPCG_OK) st = time_fixed_pair(c, ph, scale, 2 * iters, b, x, &t2);
+      us[f] = 1e3 * (double)(t2 - t1) / iters;
+    }
+    if (st != AMPCG_OK) break;
+    out->us_plain[ph] = us[0];
+    out->us_fused[ph] = us[1];
+    out->fused[ph] = us[1] < us[0] ? 1 : 0;
+  }
+  for (int ph = 0; ph < 6; ++ph) c->loop_form[sl][ph] = saved[ph];
+  cudaFree(b);
+  cudaFree(x);
+  if (st != AMPCG_OK) return st;
+  out->reserved = pairs;
+  for (int ph = 0; ph < 6; ++ph)
+    if ((pairs >> ph) & 1) c->loop_form[sl][ph] = out->fused[ph];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.emplace_back(tune_key(c, scale), *out);
+  return AMPCG_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Many independent systems in one call.
@@ -1766,18 +2058,21 @@ static ampcg_status batched_persistent(const std::vector<int>& idx, ampcg_t cons
       int* dcnt = (int*)(dev + off_cnt) + g;
       first += cnt;
       if (cnt == 0) continue;
-      const void* kern = batched_kernel(g);
-      const int smem = g ? batch_smem_bytes<1>() : batch_smem_bytes<0>();
+      const int bs = systems[idx[0]]->batch_block == kBatchBlockSmall ? kBatchBlockSmall : kBatchBlock;
+      const void* kern = batched_kernel(g, bs);
+      const int smem = bs == kBatchBlockSmall ? (g ? batch_smem_bytes<1, kBatchBlockSmall>()
+                                                    : batch_smem_bytes<0, kBatchBlockSmall>())
+                                              : (g ? batch_smem_bytes<1>() : batch_smem_bytes<0>());
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) break;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchBlock, smem) != cudaSuccess ||
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bs, smem) != cudaSuccess ||
           per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
       }
       const int grid = sms * per_sm < cnt ? sms * per_sm : cnt;
       void* kargs[7] = {&dsys, &dord, const_cast<int*>(&cnt), &dcnt, &dtmp, const_cast<int*>(&vr), &dout};
-      e = cudaLaunchKernel(kern, dim3(grid), dim3(kBatchBlock), kargs, (size_t)smem, s);
+      e = cudaLaunchKernel(kern, dim3(grid), dim3(bs), kargs, (size_t)smem, s);
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out.data(), dev + off_out, sizeof(BatchOut) * m, cudaMemcpyDeviceToHost, s);
@@ -1913,4 +2208,80 @@ extern "C" ampcg_status ampcg_solve_batched(int nsys, ampcg_t const* systems, co
     }
   }
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the batched kernel's block size: 1024 threads (one system
+// per SM) or 512 (two per SM).  Large systems favour the wide block, many
+// small ones the narrow blocks; the batch's own mix decides, by measurement.
+
+extern "C" ampcg_status ampcg_tune_batched(int nsys, ampcg_t const* systems, const ampcg_policy* policy,
+                                           int iters, ampcg_batch_tuning* out) {
+  if (nsys < 1 || !systems || !out) return fail(AMPCG_ERR_INVALID_ARG, "bad batched tuning arguments");
+  if (iters < 1 || iters > 10000) return fail(AMPCG_ERR_INVALID_ARG, "iters must be in [1, 10000]");
+  memset(out, 0, sizeof(*out));
+  int64_t total = 0;
+  for (int i = 0; i < nsys; ++i) {
+    if (!systems[i]) return fail(AMPCG_ERR_INVALID_ARG, "NULL system %d", i);
+    total += systems[i]->n;
+  }
+  ampcg_policy pol;
+  if (policy) pol = *policy;
+  else ampcg_policy_default(&pol);
+  ampcg_status st = check_policy(&pol);
+  if (st != AMPCG_OK) return st;
+  pol.verify_refresh = 0;
+  double* b = nullptr;
+  double* x = nullptr;
+  if ((st = dalloc(&b, total)) != AMPCG_OK) return st;
+  if ((st = dalloc(&x, total)) != AMPCG_OK) { cudaFree(b); return st; }
+  std::vector<double> ones((size_t)total, 1.0);
+  std::vector<const double*> bp((size_t)nsys);
+  std::vector<double*> xp((size_t)nsys);
+  int64_t off = 0;
+  for (int i = 0; i < nsys; ++i) {
+    bp[(size_t)i] = b + off;
+    xp[(size_t)i] = x + off;
+    off += systems[i]->n;
+  }
+  std::vector<int> saved((size_t)nsys);
+  for (int i = 0; i < nsys; ++i) saved[(size_t)i] = systems[i]->batch_block;
+  if (cudaMemcpy(b, ones.data(), (size_t)total * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    st = fail(AMPCG_ERR_CUDA, "tuning right-hand sides copy failed");
+  const int cand[2] = {kBatchBlock, kBatchBlockSmall};
+  for (int j = 0; j < 2 && st == AMPCG_OK; ++j) {
+    for (int i = 0; i < nsys; ++i) systems[i]->batch_block = cand[j];
+    double best = 0.0;
+    for (int rep = 0; rep < 3 && st == AMPCG_OK; ++rep) {   // the first run is a warm-up
+      if (cudaMemset(x, 0, (size_t)total * sizeof(double)) != cudaSuccess) {
+        st = fail(AMPCG_ERR_CUDA, "tuning memset failed");
+        break;
+      }
+      auto t0 = std::chrono::steady_clock::now();
+      st = ampcg_solve_batched(nsys, systems, bp.data(), xp.data(), 1e-300, iters, &pol, nullptr);
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (st == AMPCG_NOT_CONVERGED) st = AMPCG_OK;
+      if (rep == 1 || (rep > 1 && ms < best)) best = ms;
+    }
+    out->block[j] = cand[j];
+    out->ms[j] = best;
+  }
+  cudaFree(b);
+  cudaFree(x);
+  const int choice = (st == AMPCG_OK && out->ms[1] < out->ms[0]) ? kBatchBlockSmall : kBatchBlock;
+  for (int i = 0; i < nsys; ++i) systems[i]->batch_block = st == AMPCG_OK ? choice : saved[(size_t)i];
+  out->chosen = choice;
+  out->iters = iters;
+  return st;
+}
+
+extern "C" ampcg_status ampcg_set_batch_block(int nsys, ampcg_t const* systems, int block) {
+  if (nsys < 0 || (nsys > 0 && !systems)) return fail(AMPCG_ERR_INVALID_ARG, "bad arguments");
+  if (block != 0 && block != kBatchBlock && block != kBatchBlockSmall)
+    return fail(AMPCG_ERR_INVALID_ARG, "block must be 0, %d or %d", kBatchBlock, kBatchBlockSmall);
+  for (int i = 0; i < nsys; ++i) {
+    if (!systems[i]) return fail(AMPCG_ERR_INVALID_ARG, "NULL system %d", i);
+    systems[i]->batch_block = block;
+  }
+  return AMPCG_OK;
 }

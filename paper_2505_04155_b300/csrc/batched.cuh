@@ -39,16 +39,20 @@ struct BatchOut {
   double true_relres, updated_relres, nb;
 };
 
+// Block sizes of the batched kernel: 1024 threads (one system per SM) or 512
+// (two per SM, each with half the threads); ampcg_tune_batched picks one.
 constexpr int kBatchBlock = 1024;
+constexpr int kBatchBlockSmall = 512;
 
-// The staged SpMV in a 32-warp block: 3 stages per warp for binary32 values,
-// 2 for binary64, so the stages of every variant fit in shared memory.
+// The staged SpMV in a block of BS / 32 warps: 3 stages per warp for
+// binary32 values, 2 for binary64, so the stages of every variant fit in
+// shared memory (two 512-thread blocks per SM fit as one 1024-thread block).
 template <int UR> struct BatchStages { static constexpr int K = UR == P64 ? 2 : 3; };
-template <int IT>
+template <int IT, int BS = kBatchBlock>
 constexpr int batch_smem_bytes() {
-  return staged_smem_bytes<P32, IT, 3>(kBatchBlock / 32) > staged_smem_bytes<P64, IT, 2>(kBatchBlock / 32)
-             ? staged_smem_bytes<P32, IT, 3>(kBatchBlock / 32)
-             : staged_smem_bytes<P64, IT, 2>(kBatchBlock / 32);
+  return staged_smem_bytes<P32, IT, 3>(BS / 32) > staged_smem_bytes<P64, IT, 2>(BS / 32)
+             ? staged_smem_bytes<P32, IT, 3>(BS / 32)
+             : staged_smem_bytes<P64, IT, 2>(BS / 32);
 }
 // Work partition over the block's threads.  Vectors that other threads of
 // the block write during the launch are read with coherent loads
@@ -67,11 +71,14 @@ struct TeamPart {
 
 template <int UZ, int UR, int MT, int IT>
 __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int64_t n, DevState* S,
-                                              unsigned char* dsm) {
+                                              unsigned char* dsm, bool fused) {
   using Part = TeamPart;
+  constexpr bool kSmall = (UR != P64) && (UZ != P64);
   // Alg. 3: scale, precondition, rho_k and beta (a second pass only when the
-  // lagged scale made rho_k non-finite, reading R20)
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  // lagged scale made rho_k non-finite, reading R20); skipped when the
+  // previous update step formed z_k and rho_k (fused: no scaling or the lagged
+  // power of two, the same pair)
+  for (int attempt = 0; attempt < 2 && !S->z_ready; ++attempt) {
     double rho = 0.0;
     Dot2 d2;
     precond_and_cast<UZ, UR, MT, 8, Part>(B, n, S, rho, d2);
@@ -109,23 +116,41 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
     __syncthreads();
     if (S->done) return;
   }
-  // Alg. 3: x and r updates, delta_{k+1}, stopping test, next precisions
+  // Alg. 3: x and r updates, delta_{k+1}, stopping test, next precisions;
+  // fused: also z_{k+1} and rho_{k+1} in the same pass
   {
-    double rr = 0.0;
-    Dot2 d2;
+    double rr = 0.0, rho = 0.0;
+    Dot2 d2, d2z;
     unsigned long long mx = 0ull;
-    update_rows<UZ, UR, 8, Part>(B, n, S, rr, d2, mx);
-    double v[1];
+    if (fused) {
+      const PrecondScalars cn = PrecondScalars::next(S);
+      update_precond_rows<UZ, UR, MT, 8, Part>(B, n, S, cn, rr, d2, mx, rho, d2z);
+    } else {
+      update_rows<UZ, UR, 8, Part>(B, n, S, rr, d2, mx);
+    }
+    double v[1], w[1] = {0.0};
     if constexpr (UR != P64) {
       v[0] = block_sum_dot2(d2, S->inv_sig2);
     } else {
       v[0] = rr;
       block_sum_wide<1>(v);
     }
+    if (fused) {
+      if constexpr (kSmall) {
+        w[0] = block_sum_dot2(d2z, S->inv_sig);
+      } else {
+        w[0] = rho;
+        block_sum_wide<1>(w);
+      }
+    }
     mx = block_max(mx);
     if (threadIdx.x == 0) {
       double d = update_step(S, v[0], mx);
       S->delta_hist[S->k] = d;
+      if (fused && !S->done && S->uz == UZ && S->ur == UR) {
+        rho_step(S, w[0]);
+        S->z_ready = S->redo ? 0 : 1;
+      }
     }
     __syncthreads();
   }
@@ -133,22 +158,22 @@ __device__ __forceinline__ void cta_iteration(const Sell& A, const Bufs& B, int6
 
 template <int MT, int IT>
 __device__ __forceinline__ void cta_dispatch(int ph, const Sell& A, const Bufs& B, int64_t n, DevState* S,
-                                             unsigned char* dsm) {
+                                             unsigned char* dsm, bool fused) {
   switch (ph) {
-    case 0: cta_iteration<P64, P64, MT, IT>(A, B, n, S, dsm); break;
-    case 1: cta_iteration<P64, P32, MT, IT>(A, B, n, S, dsm); break;
-    case 2: cta_iteration<P32, P64, MT, IT>(A, B, n, S, dsm); break;
-    case 3: cta_iteration<P32, P32, MT, IT>(A, B, n, S, dsm); break;
-    case 4: cta_iteration<P16, P64, MT, IT>(A, B, n, S, dsm); break;
-    default: cta_iteration<P16, P32, MT, IT>(A, B, n, S, dsm); break;
+    case 0: cta_iteration<P64, P64, MT, IT>(A, B, n, S, dsm, fused); break;
+    case 1: cta_iteration<P64, P32, MT, IT>(A, B, n, S, dsm, fused); break;
+    case 2: cta_iteration<P32, P64, MT, IT>(A, B, n, S, dsm, fused); break;
+    case 3: cta_iteration<P32, P32, MT, IT>(A, B, n, S, dsm, fused); break;
+    case 4: cta_iteration<P16, P64, MT, IT>(A, B, n, S, dsm, fused); break;
+    default: cta_iteration<P16, P32, MT, IT>(A, B, n, S, dsm, fused); break;
   }
 }
 
 template <int IT>
 __device__ __forceinline__ void cta_dispatch_mt(int mt, int ph, const Sell& A, const Bufs& B, int64_t n,
-                                                DevState* S, unsigned char* dsm) {
-  if (mt == M_JACOBI) cta_dispatch<M_JACOBI, IT>(ph, A, B, n, S, dsm);
-  else cta_dispatch<M_NONE, IT>(ph, A, B, n, S, dsm);
+                                                DevState* S, unsigned char* dsm, bool fused) {
+  if (mt == M_JACOBI) cta_dispatch<M_JACOBI, IT>(ph, A, B, n, S, dsm, fused);
+  else cta_dispatch<M_NONE, IT>(ph, A, B, n, S, dsm, fused);
 }
 
 // The whole solve of one system by one block (every thread calls it).
@@ -176,9 +201,12 @@ __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh, un
   }
   int bodies = 0;
   const int limit = S->maxit + 1;
+  // the update step forms z_{k+1}, rho_{k+1} where omega_{k+1} is known
+  // before delta_{k+1} is reduced
+  const bool fused = S->scale == SCALE_NONE || S->scale == SCALE_LINF_POW2_LAG;
   for (;;) {
     while (!S->done) {
-      cta_dispatch_mt<IT>(D.mt, 2 * S->uz + S->ur, A, B, n, S, dsm);
+      cta_dispatch_mt<IT>(D.mt, 2 * S->uz + S->ur, A, B, n, S, dsm, fused);
       if (++bodies > limit) {      // every iteration advances k or stops: cannot happen
         if (threadIdx.x == 0) {
           S->status = ST_INTERNAL;
@@ -219,10 +247,10 @@ __device__ void cta_solve(const BatchSys& D, DevState* S, int verify_refresh, un
 // queue is empty.  tmpl: the initial state (policy, tol, maxit) shared by all
 // systems.  Per system: x updated in place, the outcome in out[], histories
 // in the system's arrays.
-template <int IT>
-__global__ void __launch_bounds__(kBatchBlock) k_batched(const BatchSys* sys, const int* order, int nsys,
-                                                         int* next, const DevState* tmpl,
-                                                         int verify_refresh, BatchOut* out) {
+template <int IT, int BS>
+__global__ void __launch_bounds__(BS, kBatchBlock / BS) k_batched(const BatchSys* sys, const int* order, int nsys,
+                                                                  int* next, const DevState* tmpl,
+                                                                  int verify_refresh, BatchOut* out) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ DevState S;
   __shared__ BatchSys D;   // the system's descriptor, shared by the block (not per-thread local memory)

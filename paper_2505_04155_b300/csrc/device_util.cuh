@@ -433,10 +433,11 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
 // it before each solve.  A wait that runs out after kBarrierSpin polls (about
 // a second; it cannot happen with every block resident) returns false in
 // every thread of the block instead of hanging.  The partials alternate
-// between two halves of part (2 * gridDim.x doubles each) and of pmax
-// (gridDim.x each), selected by the launch's barrier count `nb`: a block that
-// has passed barrier j may publish for barrier j + 1 while another still
-// reads barrier j's partials.
+// between two halves of part and of pmax (gridDim.x entries each for the
+// single-sum forms; the two-sum form has its own halves after them),
+// selected by the launch's barrier count `nb`: a block that has passed
+// barrier j may publish for barrier j + 1 while another still reads barrier
+// j's partials.
 struct GridSumBarrier {
   unsigned long long arrive;   // tickets taken
   unsigned long long pad[3];
@@ -448,6 +449,10 @@ template <int NSUM, bool MAX>
 __device__ __forceinline__ bool grid_barrier_sums(GridSumBarrier* g, double* part, unsigned long long* pmax,
                                                   int& nb, const double* v, unsigned long long mx, double* tot,
                                                   unsigned long long& mtot, long long spin);
+template <int MODE>
+__device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* part, unsigned long long* pmax,
+                                                    int& nb, double v, unsigned long long mx, double& tot,
+                                                    unsigned long long& mtot, long long spin = kBarrierSpin);
 
 // Fixed-order sum of G partials (block g's value j at part[g*stride + j]) in
 // the last block; thread 0 gets the totals.  Thread t adds partials t, t + B,
@@ -523,8 +528,9 @@ __device__ __forceinline__ unsigned long long final_sum_max(const double* part, 
 }
 
 // Grid barrier with NSUM grid-wide sums (0, 1 or 2 per block, v[j] valid in
-// thread 0; block g's partial j at part[parity * 2G + g * NSUM + j], parity =
-// the barrier's count in the launch mod 2; part holds 4G doubles) and, with
+// thread 0; block g's partial j at part[2G + parity * 2G + g * NSUM + j],
+// parity = the barrier's count in the launch mod 2; part holds 6G doubles)
+// and, with
 // MAX, the grid-wide maximum of the blocks' mx; tot[j] and mtot end up in
 // every thread.  spin: polls per polling warp before the wait gives up.  The
 // block passes the barrier when any of its pollers saw it complete; it fails
@@ -536,10 +542,11 @@ __device__ __forceinline__ bool grid_barrier_sums(GridSumBarrier* g, double* par
   static_assert(NSUM >= 0 && NSUM <= 2, "0, 1 or 2 sums");
   __shared__ double s_tot[2];
   __shared__ unsigned long long s_max;
-  // consecutive barriers use disjoint halves of 2G entries each (2 G doubles
-  // for up to two sums per block), whatever their number of sums
+  // its partials live after the single-sum forms' two halves (2G doubles):
+  // halves of 2G doubles at 2G and 4G, so consecutive barriers of either kind
+  // never share entries
   const int parity = nb++ & 1;
-  if constexpr (NSUM >= 1) part += parity * 2 * (int)gridDim.x;
+  if constexpr (NSUM >= 1) part += 2 * (int)gridDim.x + parity * 2 * (int)gridDim.x;
   if constexpr (MAX) pmax += parity * (int)gridDim.x;
   __shared__ unsigned long long s_target;
   __shared__ volatile int s_seen;
@@ -620,15 +627,82 @@ __device__ __forceinline__ bool grid_barrier_sums(GridSumBarrier* g, double* par
   return true;
 }
 
-// The single-sum forms: MODE 0 plain barrier, 1 one sum, 2 one sum and the max.
+// The single-sum forms: MODE 0 plain barrier, 1 one sum, 2 one sum and the
+// max; block g's partial at part[parity * G + g] (halves G apart).  Kept
+// apart from grid_barrier_sums (measured on B300: the shared two-sum code
+// cost 0.6-2.5 us per iteration of the persistent kernel in these forms).
 template <int MODE>
 __device__ __forceinline__ bool grid_reduce_barrier(GridSumBarrier* g, double* part, unsigned long long* pmax,
                                                     int& nb, double v, unsigned long long mx, double& tot,
-                                                    unsigned long long& mtot, long long spin = kBarrierSpin) {
-  double vv[1] = {v}, tt[1] = {0.0};
-  const bool ok = grid_barrier_sums<MODE == 0 ? 0 : 1, MODE == 2>(g, part, pmax, nb, vv, mx, tt, mtot, spin);
-  if constexpr (MODE >= 1) tot = tt[0];
-  return ok;
+                                                    unsigned long long& mtot, long long spin) {
+  __shared__ double s_tot;
+  __shared__ unsigned long long s_max;
+  const int half = (nb++ & 1) * (int)gridDim.x;
+  if constexpr (MODE >= 1) part += half;
+  if constexpr (MODE == 2) pmax += half;
+  __shared__ unsigned long long s_target;
+  __shared__ volatile int s_seen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if constexpr (MODE >= 1) part[blockIdx.x] = v;
+    if constexpr (MODE == 2) pmax[blockIdx.x] = mx;
+    __threadfence();
+    const unsigned long long G = gridDim.x;
+    const unsigned long long a = atomicAdd(&g->arrive, 1ull);
+    s_target = (a / G + 1) * G;
+    s_seen = 0;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0 && (threadIdx.x >> 5) < kPollers) {
+    const int w = threadIdx.x >> 5;
+    if (w) __nanosleep(150u * (unsigned)w);
+    const unsigned long long target = s_target;
+    for (long long it = 0;; ++it) {
+      if (s_seen) break;
+      unsigned long long r;
+      asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(r) : "l"(&g->arrive) : "memory");
+      if (r >= target) {
+        s_seen = 1;
+        break;
+      }
+      if (it >= spin) break;
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if constexpr (MODE >= 1) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int G = gridDim.x;
+      double t = 0.0;
+      unsigned long long m = 0ull;
+      for (int i0 = lane; i0 < G; i0 += 32 * 8) {
+        double pv[8];
+        unsigned long long pw[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + 32 * u;
+          pv[u] = i < G ? __ldcg(part + i) : 0.0;
+          if constexpr (MODE == 2) pw[u] = i < G ? __ldcg(pmax + i) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (i0 + 32 * u < G) t += pv[u];
+          if constexpr (MODE == 2) m = pw[u] > m ? pw[u] : m;
+        }
+      }
+      t = warp_sum(t);
+      if constexpr (MODE == 2) m = warp_max(m);
+      if (lane == 0) {
+        s_tot = t;
+        s_max = m;
+      }
+    }
+    __syncthreads();
+    tot = s_tot;
+    if constexpr (MODE == 2) mtot = s_max;
+  }
+  return s_seen != 0;   // passed when any poller saw the barrier complete
 }
 
 }  // namespace ampcg

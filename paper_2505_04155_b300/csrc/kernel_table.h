@@ -20,9 +20,17 @@ const void* loop_kernel_jacobi_fused(int uz, int ur, int it);
 // k_spmv_loop_step<u_z, u_r, it>
 const void* loop_spmv_kernel(int uz, int ur, int it);
 
-// k_batched<it>
-const void* batched_kernel(int it);
-const void* batched_kernel_idx32();
-const void* batched_kernel_idx16();
+// k_batched<it, bs>, bs = 1024 or 512 threads
+const void* batched_kernel(int it, int bs);
+const void* batched_kernel_idx32_b1024();
+const void* batched_kernel_idx32_b512();
+const void* batched_kernel_idx16_b1024();
+const void* batched_kernel_idx16_b512();
+
+// block-row kernels for 3 x 3 block matrices (bsr.cuh): k_bspmv<u_z, u_r>,
+// k_bcheb_step<u_z, u_r>, k_bspmv_step<u_r>
+const void* bsr_spmv_kernel(int uz, int ur);
+const void* bsr_cheb_kernel(int uz, int ur);
+const void* bsr_spmv_step_kernel(int ur);
 
 }  // namespace ampcg

@@ -1568,7 +1568,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
       // Alg. 3: scaling, preconditioning, rho_k and beta_{k-1}; with binary16
       // storage p_{k-1} of the register-held vectors is loaded before the
       // barrier (it does not depend on beta_{k-1}; not when it is converted)
-      for (;;) {
+      {
         pre = (UZ == P16) && !S.p_cast && !S.first;
         const PrecondScalars c(&S);
         double rho = 0.0;
@@ -1610,9 +1610,12 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
         if (!ok) break;
         if (threadIdx.x == 0) rho_step(&S, tot[0]);
         __syncthreads();
-        if (!S.redo) break;   // else: omega_k is now the exact power of two (reading R20)
       }
       if (!ok || S.done) break;
+      if (S.redo) {   // omega_k is now the exact power of two (reading R20): the head again
+        --it;
+        continue;
+      }
       have = true;
     }
     if (threadIdx.x == 0) S.phase_runs[2 * UZ + UR] += 1;

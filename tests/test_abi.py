@@ -38,15 +38,16 @@ def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "ampcg.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(ampcg_policy), sizeof(ampcg_result),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(ampcg_policy), sizeof(ampcg_result),"
         " sizeof(ampcg_precond_spec), offsetof(ampcg_result, relres_hist), offsetof(ampcg_policy, graph_chunk),"
-        " offsetof(ampcg_result, seconds), sizeof(ampcg_layout)); return 0;}\n")
+        " offsetof(ampcg_result, seconds), sizeof(ampcg_layout), sizeof(ampcg_tuning),"
+        " offsetof(ampcg_tuning, iters)); return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(P.PolicyC), C.sizeof(P.ResultC), C.sizeof(P.PrecondSpec),
             P.ResultC.relres_hist.offset, P.PolicyC.graph_chunk.offset, P.ResultC.seconds.offset,
-            C.sizeof(P.LayoutC)]
+            C.sizeof(P.LayoutC), C.sizeof(P.TuningC), P.TuningC.iters.offset]
     assert got == want
 
 

@@ -167,3 +167,45 @@ def test_batched_statuses():
     assert infos[0].status == P.ERR_NONFINITE and infos[1].status == P.OK
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("block", [1024, 512])
+@pytest.mark.parametrize("kind", ["amp16_lag", "fp64"])
+def test_each_block_size_matches_oracle(block, kind):
+    # the batched kernel's block sizes the tuner chooses between: both run
+    # Alg. 3 per system (reductions over other thread counts), each system
+    # meets the parity bars against the oracle
+    mats, rhs = W.batch_2d(12, seed=7, smin=16, smax=100)
+    gp, op = {
+        "amp16_lag": (P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3, scale=P.SCALE_LINF_POW2_LAG),
+                      oracle.Policy(u0=oracle.FP16, criterion=oracle.LINEAR, verify_refresh=3,
+                                    scale=oracle.SCALE_LINF_POW2_LAG)),
+        "fp64": (P.Policy.pcg64(), oracle.Policy(criterion=oracle.FIXED, fixed_uz=oracle.FP64,
+                                                 fixed_ur=oracle.FP64, scale=oracle.SCALE_NONE)),
+    }[kind]
+    solvers = [P.Solver(m.rowptr, m.col, m.val) for m in mats]
+    P.set_batch_block(solvers, block)
+    xs, infos = _solve_batched(solvers, rhs, gp)
+    for m, b, x, info in zip(mats, rhs, xs, infos):
+        ref = oracle.ampcg(m.rowptr, m.col, m.val, b, tol=1e-10, maxit=5000, policy=op)
+        assert info.converged and ref.converged
+        if kind == "fp64":
+            assert abs(info.iters - ref.iters) <= 1
+        else:
+            assert abs(info.iters - ref.iters) <= max(3, 0.05 * ref.iters)
+        t = oracle.residual64(m.rowptr, m.col, m.val, b, x.cpu().numpy())
+        assert np.linalg.norm(t) / np.linalg.norm(b) <= (1.01e-10 if kind == "fp64" else 1e-10)
+    for s in solvers:
+        s.close()
+
+
+def test_tune_batched_stores_the_faster_block():
+    mats, rhs = W.batch_2d(40, seed=9, smin=16, smax=128)
+    solvers = [P.Solver(m.rowptr, m.col, m.val) for m in mats]
+    t = P.tune_batched(solvers, iters=10, policy=P.Policy(scale=P.SCALE_LINF_POW2_LAG))
+    assert set(t["ms"]) == {1024, 512} and all(v > 0 for v in t["ms"].values())
+    assert t["chosen"] == min(t["ms"], key=t["ms"].get)
+    xs, infos = _solve_batched(solvers, rhs, P.Policy(verify_refresh=3, scale=P.SCALE_LINF_POW2_LAG))
+    assert all(i.converged and i.true_relres <= 1e-10 for i in infos)
+    for s in solvers:
+        s.close()

@@ -210,7 +210,7 @@ def test_repeated_solves_are_deterministic():
 
 
 @pytest.mark.parametrize("kind", ["amp16", "amp16_lag", "amp64_window", "amp64_window_lag", "cheb",
-                                  "wide_jacobi", "wide_jacobi_lag", "pcg64"])
+                                  "wide_jacobi", "wide_jacobi_lag", "pcg64", "bsr_cheb", "bsr_jacobi"])
 def test_loop_graph_equals_kernel_by_kernel(kind):
     # the loop graph (SWITCH per precision change, inner loop of chunks) runs
     # the same kernels in the same order as the host-driven launches, for any
@@ -222,9 +222,15 @@ def test_loop_graph_equals_kernel_by_kernel(kind):
         a = W.elasticity_q1(7, seed=2).to_csr()
     else:
         a = W.diffusion3d(20, 2.0, 6)
-    b = torch.as_tensor(W.rhs_uniform(a.n, 8), device="cuda")
-    kw = dict(precond=P.M_CHEBYSHEV, degree=4) if kind == "cheb" else {}
-    s = P.Solver(a.rowptr, a.col, a.val, **kw)
+    if kind.startswith("bsr"):
+        a = W.elasticity_q1(7, seed=2)   # 3 x 3 blocks: the block-row kernels
+    b = torch.as_tensor(W.rhs_uniform(a.n if not kind.startswith("bsr") else a.nb * 3, 8), device="cuda")
+    kw = dict(precond=P.M_CHEBYSHEV, degree=4) if kind in ("cheb", "bsr_cheb") else {}
+    if kind.startswith("bsr"):
+        s = P.Solver.from_bsr(a.browptr, a.bcol, a.bval.reshape(-1), 3, **kw)
+        assert s.layout()["block3"] == 1
+    else:
+        s = P.Solver(a.rowptr, a.col, a.val, **kw)
     lag = P.SCALE_LINF_POW2_LAG
     pol = {"amp64_window": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3),
            "amp64_window_lag": P.Policy(u0=P.FP64, criterion=P.CRIT_WINDOW, verify_refresh=3, scale=lag),
@@ -233,7 +239,8 @@ def test_loop_graph_equals_kernel_by_kernel(kind):
            "pcg64": P.Policy.pcg64(verify_refresh=3)}.get(kind, P.Policy(verify_refresh=3))
     x0, i0 = s.solve(b, tol=TOL, maxit=5000, policy=pol, timed=True)
     assert i0.converged
-    assert kind in ("cheb", "wide_jacobi", "wide_jacobi_lag", "pcg64") or any(k >= 0 for k in i0.switch_iter)
+    assert kind in ("cheb", "wide_jacobi", "wide_jacobi_lag", "pcg64", "bsr_cheb", "bsr_jacobi") or \
+        any(k >= 0 for k in i0.switch_iter)
     for chunk in (1, 3, 16, 64):
         pol.graph_chunk = chunk
         x1, i1 = s.solve(b, tol=TOL, maxit=5000, policy=pol)

@@ -1,0 +1,83 @@
+"""Autotuning of the persistent iteration kernel (ampcg_tune, ampcg_set_tuning).
+
+The tuner picks, per precision pair, the four- or three-barrier form of the
+iteration kernel by timing both on the context's matrix.  Both forms compute
+Alg. 3 (their inner products differ only in summation order), so a tuned
+solve must meet the same parity bars against the oracle as the default one,
+and each forced form must too."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2505_04155_b300")
+
+LAG = P.SCALE_LINF_POW2_LAG
+
+
+def _opol(gp):
+    return oracle.Policy(u0=gp.u0, criterion=gp.criterion, d=gp.d, ell=gp.ell, C=gp.C, tau_zs=gp.tau_zs,
+                         tau_zh=gp.tau_zh, scale=gp.scale, latch=gp.latch, verify_refresh=gp.verify_refresh,
+                         fixed_uz=gp.fixed_uz, fixed_ur=gp.fixed_ur)
+
+
+def test_tune_measures_both_forms_and_caches_per_shape():
+    a = W.diffusion3d(40, 2.0, 0)
+    s1 = P.Solver(a.rowptr, a.col, a.val)
+    t1 = s1.tune(scale=LAG, iters=10)
+    assert set(t1["fused"]) == {P.phase_name(p) for p in range(6)}
+    assert all(v in (0, 1) for v in t1["fused"].values())
+    assert all(v > 0 for v in t1["us_four_barrier"].values()) and len(t1["us_three_barrier"]) == 6
+    for ph, f in t1["fused"].items():
+        assert f == (1 if t1["us_three_barrier"][ph] < t1["us_four_barrier"][ph] else 0)
+    assert not t1["cached"]
+    s2 = P.Solver(a.rowptr, a.col, a.val)          # same shape: the cached result
+    t2 = s2.tune(scale=LAG, iters=10)
+    assert t2["cached"] and t2["fused"] == t1["fused"]
+    t3 = s2.tune(scale=P.SCALE_NONE, iters=10)     # another scale mode: measured on its own
+    assert not t3["cached"]
+    with pytest.raises(P.AmpcgError):
+        s2.tune(scale=P.SCALE_LINF_POW2, iters=10)
+    s1.close()
+    s2.close()
+
+
+def test_tune_without_the_persistent_kernel():
+    a = W.diffusion3d(8, 1.0, 0)
+    s = P.Solver(a.rowptr, a.col, a.val, precond=P.M_CHEBYSHEV, degree=4)
+    t = s.tune(scale=LAG, iters=5)
+    assert t["fused"] == {} and not t["us_four_barrier"]
+    s.close()
+
+
+@pytest.mark.parametrize("form", ["tuned", "four", "three"])
+@pytest.mark.parametrize("variant", ["amp16_lag", "pcg64"])
+def test_each_form_matches_oracle(form, variant):
+    a = W.diffusion3d(24, 2.0, 0)
+    b = W.rhs_uniform(a.n, 1)
+    s = P.Solver(a.rowptr, a.col, a.val)
+    gp = P.Policy(scale=LAG, verify_refresh=3) if variant == "amp16_lag" else P.Policy.pcg64()
+    if form == "tuned":
+        s.tune(scale=gp.scale, iters=10)
+    else:
+        s.set_tuning([0 if form == "four" else 1] * 6, scale=gp.scale)
+    bd = torch.as_tensor(b, device="cuda")
+    x, info = s.solve(bd, tol=1e-10, maxit=5000, policy=gp)
+    x2, info2 = s.solve(bd, tol=1e-10, maxit=5000, policy=gp, timed=True)   # launch by launch: same form
+    s.close()
+    ref = oracle.ampcg(a.rowptr, a.col, a.val, b, tol=1e-10, maxit=5000, policy=_opol(gp))
+    assert info.converged and ref.converged
+    assert info2.iters == info.iters and torch.equal(x, x2)
+    if variant == "pcg64":
+        assert abs(info.iters - ref.iters) <= 1
+    else:
+        assert abs(info.iters - ref.iters) <= max(2, 0.05 * ref.iters)
+    m = min(20, info.iters)
+    np.testing.assert_allclose(info.relres_hist[:m], ref.relres_hist[:m], rtol=1e-6)
+    xr = x.cpu().numpy()
+    assert np.linalg.norm(xr - ref.x) / np.linalg.norm(ref.x) <= 1e-6   # kappa(A) ~ 7.5e5, relres 1e-10
+    assert info.true_relres <= 1e-10 or variant == "pcg64" and info.true_relres <= 1.01e-10
