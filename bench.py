@@ -64,11 +64,12 @@ def config_dict(a, extra=None):
     return d
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture (--metrics dram__bytes_read.sum,dram__bytes_write.sum on the same
-# launch), keyed by kernel and by the source revision of the kernel it was
-# taken on; a kernel without a capture of its current form reports null.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel in
+# its current form (dram__bytes_read.sum + dram__bytes_write.sum of a
+# single-iteration launch on the benchmark system); a stored figure, to be
+# recaptured whenever the kernel changes.  Kernels without one report null.
+NCU_TRAFFIC = {"amp:iteration:uz16_ur64": 170.31e6, "amp:iteration:uz16_ur32": 102.45e6,
+               "fp64:iteration:uz64_ur64": 213.48e6}
 
 
 def peaks():
@@ -322,7 +323,8 @@ def run_ours(args, rank, world):
     dk, dv = dom
     achieved = dv["gbs"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 3), "traffic": NCU_TRAFFIC.get(dk), "kernel": dk,
+                "frac": round(achieved / peak, 3), "traffic": NCU_TRAFFIC.get(dk),
+                "traffic_source": "stored ncu dram bytes (read + write) of one launch of this kernel", "kernel": dk,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
     # per-iteration device time inside the loop graph, per precision pair:
@@ -532,7 +534,9 @@ def run_profile(args):
     iterates as the graph path; profilers cannot see kernel nodes of graphs
     with conditional nodes).  `amp` is the benchmarked AMP-PCG policy;
     `p1`/`p2`/`fp64` pin the precision pair of Phase 1 (u_z=FP16, u_r=FP64),
-    Phase 2 (FP16, FP32) or PCG(FP64)."""
+    Phase 2 (FP16, FP32) or PCG(FP64) (four-barrier iteration kernel);
+    `p1_lag`/`p2_lag` the same pairs under the lagged scale (three-barrier
+    iteration kernel)."""
     import torch
     import paper_2505_04155_b300 as P
     torch.cuda.set_device(0)
@@ -572,10 +576,15 @@ def run_profile(args):
         return
     a, b = workload()
     s = P.Solver(a.rowptr, a.col, a.val)
+    lag = P.SCALE_LINF_POW2_LAG
     pol = {"amp": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3),
            "p1": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64),
            "p2": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32),
+           "p1_lag": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64, scale=lag),
+           "p2_lag": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32, scale=lag),
            "fp64": P.Policy.pcg64()}[args.profile]
+    if args.profile == "fp64":
+        s.set_tuning([0] * 6, scale=P.SCALE_NONE)   # the form the autotuner keeps for FP64 PCG
     maxit = args.profile_iters if args.profile_iters > 0 else MAXIT
     bd = torch.as_tensor(b, device="cuda")
     _, info = s.solve(bd, tol=TOL, maxit=maxit, policy=pol, history=False, timed=True)
@@ -594,7 +603,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--profile", choices=["amp", "p1", "p2", "fp64", "batch_p1", "batch_p2", "cheb_p2", "cheb_fp64"],
+    ap.add_argument("--profile", choices=["amp", "p1", "p2", "p1_lag", "p2_lag", "fp64", "batch_p1", "batch_p2",
+                                          "cheb_p2", "cheb_fp64"],
                     default=None,
                     help="run one solve for a profiler and exit")
     ap.add_argument("--profile-iters", type=int, default=0, help="maxit of the profiled solve (0: converge)")
