@@ -353,6 +353,27 @@ def run_ours(args, rank, world):
         graph_iter[ph] = {"us": round(best, 2), "alg_bytes": int(by), "gbs": round(by / (best * 1e-6) / 1e9, 1),
                           "frac": round(by / (best * 1e-6) / 1e9 / peak, 3)}
 
+    # the choice of omega_k (Sec. 3.3; reading R5): the same AMP-PCG(FP16)
+    # solve under omega = 1/||r_k|| (Alg. 3 as printed), the exact power of two
+    # 2^-ceil(log2 max|r_k|) (the default) and the lagged one (reading R20),
+    # GPU time and iterations beside the oracle's iterations and binary16
+    # underflow fractions (an oracle-written file)
+    study = {}
+    oracle_study = {}
+    sp = os.path.join(ROOT, "tests", "golden", "c2_scale_study.json")
+    if os.path.exists(sp):
+        with open(sp) as f:
+            oracle_study = json.load(f)
+    for name, sc in (("L2", P.SCALE_L2), ("LINF_POW2", P.SCALE_LINF_POW2), ("LINF_POW2_LAG", P.SCALE_LINF_POW2_LAG)):
+        pol = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3, scale=sc)
+        timed(pol, 1)
+        ms_, inf_, _ = timed(pol, 3)
+        o = oracle_study.get(name, {})
+        study[name] = {"ms": round(statistics.mean(ms_), 3), "iters": inf_[-1].iters,
+                       "switch_iter": list(inf_[-1].switch_iter), "true_relres": inf_[-1].true_relres,
+                       "oracle_iters": o.get("iters"),
+                       "oracle_y16_below_normal_frac": o.get("y16_below_normal_frac")}
+
     # end to end through the C ABI with pinned host buffers
     bh = torch.as_tensor(b).pin_memory()
     xh = torch.zeros(a.n, dtype=torch.float64).pin_memory()
@@ -392,7 +413,7 @@ def run_ours(args, rank, world):
                "true_relres_amp64_window": w_info[-1].true_relres,
                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": clocks, "gpu_launches": launches,
-               "iteration_in_graph": graph_iter, "layout": lay, "autotune": tuning,
+               "iteration_in_graph": graph_iter, "layout": lay, "autotune": tuning, "scale_study": study,
                "gpu_launches_note": "library kernels in the timed region (all timed solves), counted by the library"}
         print(json.dumps(out), flush=True)
     s.close()
