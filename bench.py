@@ -496,6 +496,9 @@ def run_workload(args):
         tb, ib = _event_ms(lambda: batched(amp), args.steps, flush)
         tl, il = _event_ms(lambda: loop(amp), args.steps, flush)
         tb6, ib6 = _event_ms(lambda: batched(f64), args.steps, flush)
+        amp_lag = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3, scale=P.SCALE_LINF_POW2_LAG)
+        batched(amp_lag)
+        tbl, ibl = _event_ms(lambda: batched(amp_lag), args.steps, flush)
         same = all(i.iters == j.iters for i, j in zip(ib, il))
         for s in ss:
             s.close()
@@ -509,6 +512,8 @@ def run_workload(args):
                           "solver": "AMP-PCG(FP16) linear criterion, Jacobi", "l2_flush": True},
                "host_loop_ms": round(tl, 3), "speedup_vs_host_loop": round(tl / tb, 3),
                "fp64_batched_ms": round(tb6, 3), "speedup_vs_fp64_batched": round(tb6 / tb, 3),
+               "amp_lag_batched_ms": round(tbl, 3), "iters_max_amp_lag": max(i.iters for i in ibl),
+               "all_converged_amp_lag": all(i.converged for i in ibl),
                "iters_max": max(i.iters for i in ib), "iters_mean": round(statistics.mean(i.iters for i in ib), 1),
                "all_converged": all(i.converged for i in ib), "batched_iters_equal_single": same,
                "unknowns_per_s": round(n_tot / (tb * 1e-3), 1), "autotune": btune}
@@ -533,6 +538,11 @@ def run_workload(args):
         for _ in range(args.warmup):
             grad(amp), grad(f64)
         ta, ga = _event_ms(lambda: grad(amp), args.steps, flush)
+        amp_lag = P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3, scale=P.SCALE_LINF_POW2_LAG)
+        s.tune(scale=P.SCALE_LINF_POW2_LAG, iters=20, pairs=[4, 5])
+        s.tune(scale=P.SCALE_NONE, iters=20, pairs=[0])
+        grad(amp_lag)
+        tl, gl = _event_ms(lambda: grad(amp_lag), args.steps, flush)
         t6, g6 = _event_ms(lambda: grad(f64), args.steps, flush)
         rel = float(torch.linalg.norm(ga - g6) / torch.linalg.norm(g6))
         s.close()
@@ -544,7 +554,8 @@ def run_workload(args):
                                       "b~U[-1,1] seed 1; L = 0.5||x(theta) - x_t||^2",
                           "n": int(a.n), "nnz": int(a.nnz), "l2_flush": True},
                "fp64_ms": round(t6, 3), "speedup_vs_fp64": round(t6 / ta, 3),
-               "grad_rel_diff_amp_vs_fp64": rel}
+               "grad_rel_diff_amp_vs_fp64": rel, "amp_lag_ms": round(tl, 3),
+               "grad_rel_diff_amp_lag_vs_fp64": float(torch.linalg.norm(gl - g6) / torch.linalg.norm(g6))}
     out.update(base)
     print(json.dumps(out), flush=True)
 

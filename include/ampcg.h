@@ -391,7 +391,9 @@ typedef struct {
  * per matrix shape (rows, entries, layout, preconditioner, device) and scale
  * mode within the process: a later call for an equal shape reuses them
  * (out->cached = 1).  Contexts without the persistent kernel get fused[] = -1
- * and AMPCG_OK.  Allocates two vectors of n doubles; synchronous. */
+ * and AMPCG_OK; so does a pair whose timing solve (right-hand side of ones,
+ * x_0 = 0) breaks down or stops early on this system (for example binary16
+ * z without scaling).  Allocates two vectors of n doubles; synchronous. */
 ampcg_status ampcg_tune(ampcg_t ctx, int scale, int iters, int pairs, ampcg_tuning* out);
 
 /* Applies the forms of t->fused[] (-1, 0 or 1 per pair) for solves under the

@@ -1883,9 +1883,13 @@ ampcg_status time_fixed_pair(ampcg_ctx* c, int ph, int scale, int maxit, const d
   if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (st != AMPCG_OK && st != AMPCG_NOT_CONVERGED) return st;
-  if (res.iters != maxit) return fail(AMPCG_ERR_CUDA, "tuning solve stopped after %d of %d iterations", res.iters, maxit);
   if (e != cudaSuccess) return fail(AMPCG_ERR_CUDA, "tuning events: %s", cudaGetErrorString(e));
+  // a pair that breaks down on this system (e.g. binary16 z without scaling)
+  // or stops early cannot be timed: AMPCG_NOT_CONVERGED tells the caller
+  if (st == AMPCG_ERR_BREAKDOWN || st == AMPCG_ERR_NONFINITE || (st == AMPCG_OK && res.iters != maxit) ||
+      (st == AMPCG_NOT_CONVERGED && res.iters != maxit))
+    return AMPCG_NOT_CONVERGED;
+  if (st != AMPCG_NOT_CONVERGED && st != AMPCG_OK) return st;
   return AMPCG_OK;
 }
 }  // namespace
@@ -1942,15 +1946,21 @@ extern "C" ampcg_status ampcg_tune(ampcg_t c, int scale, int iters, int pairs, a
   for (int ph = 0; ph < 6 && st == AMPCG_OK; ++ph) {
     if (!((pairs >> ph) & 1)) continue;
     double us[2] = {0.0, 0.0};
-    for (int f = 0; f < 2 && st == AMPCG_OK; ++f) {
+    bool timed = true;
+    for (int f = 0; f < 2 && st == AMPCG_OK && timed; ++f) {
       c->loop_form[sl][ph] = f;
       float t1 = 0.f, t2 = 0.f, w = 0.f;
       st = time_fixed_pair(c, ph, scale, iters, b, x, &w);   // warm-up (graph build)
       if (st == AMPCG_OK) st = time_fixed_pair(c, ph, scale, iters, b, x, &t1);
       if (st == AMPCG_OK) st = time_fixed_pair(c, ph, scale, 2 * iters, b, x, &t2);
+      if (st == AMPCG_NOT_CONVERGED) {   // the pair does not run on this system: not timed
+        timed = false;
+        st = AMPCG_OK;
+      }
       us[f] = 1e3 * (double)(t2 - t1) / iters;
     }
     if (st != AMPCG_OK) break;
+    if (!timed) continue;                // fused[ph] stays -1 (automatic)
     out->us_plain[ph] = us[0];
     out->us_fused[ph] = us[1];
     out->fused[ph] = us[1] < us[0] ? 1 : 0;

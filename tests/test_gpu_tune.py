@@ -81,3 +81,14 @@ def test_each_form_matches_oracle(form, variant):
     xr = x.cpu().numpy()
     assert np.linalg.norm(xr - ref.x) / np.linalg.norm(ref.x) <= 1e-6   # kappa(A) ~ 7.5e5, relres 1e-10
     assert info.true_relres <= 1e-10 or variant == "pcg64" and info.true_relres <= 1.01e-10
+
+
+def test_tune_skips_a_pair_that_breaks_down():
+    # binary16 z without scaling breaks down on this system (the paper's
+    # motivating failure of plain FP16 PCG); the tuner leaves such pairs on the
+    # automatic form instead of failing
+    theta, theta_t, a, a_t, b = W.log_coeff_problem(16, sigma=1.0, seed=0)
+    s = P.Solver(a.rowptr, a.col, a.val)
+    t = s.tune(scale=P.SCALE_NONE, iters=10)
+    assert t["fused"].get("uz64_ur64") in (0, 1)
+    s.close()
