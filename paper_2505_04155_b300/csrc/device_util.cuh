@@ -400,6 +400,68 @@ __device__ __forceinline__ unsigned long long block_max(unsigned long long v) {
   return v;
 }
 
+// block_sum_dot2 of NS pairs (scaled by scale[k]) and block_max in one pass:
+// the same per-warp reductions and the same fixed-order totals as the
+// separate calls, hence the same bits, with two block barriers instead of
+// 2 (NS + 1).  Totals valid in warp 0 (thread 0 uses them).
+template <int NS>
+__device__ __forceinline__ void block_sums_dot2_max(Dot2 (&d)[NS], const double (&scale)[NS], double (&out)[NS],
+                                                    unsigned long long& mx) {
+  __shared__ double shd[NS][32];
+  __shared__ unsigned long long shm[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) d[k].warp_reduce();
+  mx = warp_max(mx);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) shd[k][wid] = __dmul_rn(d[k].to_f64(), scale[k]);
+    shm[wid] = mx;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) out[k] = warp_sum(lane < nw ? shd[k][lane] : 0.0);
+    mx = warp_max(lane < nw ? shm[lane] : 0ull);
+  }
+}
+
+// block_sum_wide of NV values and block_max in one pass (the same sums and
+// bits as the separate calls; two block barriers instead of four).
+template <int NV>
+__device__ __forceinline__ void block_sum_wide_max(double (&v)[NV], unsigned long long& mx) {
+  __shared__ double sh[NV][1024];
+  __shared__ double sw[NV][8];
+  __shared__ unsigned long long shm[32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) sh[j][t] = v[j];
+  mx = warp_max(mx);
+  if (lane == 0) shm[wid] = mx;
+  __syncthreads();
+  if (t < 256) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double a = sh[j][t];
+      for (int u = t + 256; u < (int)blockDim.x; u += 256) a += sh[j][u];
+      a = warp_sum(a);
+      if (lane == 0) sw[j][wid] = a;
+    }
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double a = lane < 8 ? sw[j][lane] : 0.0;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+      v[j] = a;
+    }
+    mx = warp_max(lane < nw ? shm[lane] : 0ull);
+  }
+}
+
 // Single-pass grid reduction: every block publishes its partials, then takes
 // a ticket; the block that draws the last ticket sees all partials.  Returns
 // true in every thread of that block.  The last block must reset *ticket.
@@ -585,39 +647,43 @@ __device__ __forceinline__ bool grid_barrier_sums(GridSumBarrier* g, double* par
   const bool ok = s_seen != 0;
   if (!ok) return false;   // uniform across the block: s_seen is read after the barrier
   if constexpr (NSUM >= 1 || MAX) {
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      const int G = gridDim.x;
-      double t[2] = {0.0, 0.0};
-      unsigned long long m = 0ull;
-      constexpr int U = NSUM == 2 ? 4 : 8;   // loads in flight per lane
+    // warp q < NSUM sums partial q, warp NSUM takes the max: each lane adds
+    // partials lane, lane + 32, ... in that order (loads of five issued
+    // before the first add: one memory round trip up to 160 blocks), then a
+    // fixed tree
+    constexpr int U = 5;
+    const int wq = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int G = gridDim.x;
+    if (wq < NSUM) {
+      double t = 0.0;
       for (int i0 = lane; i0 < G; i0 += 32 * U) {
-        double pv[U][2];
+        double pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = i0 + 32 * u;
+          pv[u] = i < G ? __ldcg(part + (size_t)i * NSUM + wq) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (i0 + 32 * u < G) t += pv[u];
+      }
+      t = warp_sum(t);
+      if (lane == 0) s_tot[wq] = t;
+    } else if (MAX && wq == NSUM) {
+      unsigned long long m = 0ull;
+      for (int i0 = lane; i0 < G; i0 += 32 * U) {
         unsigned long long pw[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int i = i0 + 32 * u;
-#pragma unroll
-          for (int j = 0; j < NSUM; ++j) pv[u][j] = i < G ? __ldcg(part + (size_t)i * NSUM + j) : 0.0;
-          if constexpr (MAX) pw[u] = i < G ? __ldcg(pmax + i) : 0ull;
+          pw[u] = i < G ? __ldcg(pmax + i) : 0ull;
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (i0 + 32 * u < G) {
-#pragma unroll
-            for (int j = 0; j < NSUM; ++j) t[j] += pv[u][j];
-          }
-          if constexpr (MAX) m = pw[u] > m ? pw[u] : m;
-        }
+        for (int u = 0; u < U; ++u) m = pw[u] > m ? pw[u] : m;
       }
-#pragma unroll
-      for (int j = 0; j < NSUM; ++j) t[j] = warp_sum(t[j]);
-      if constexpr (MAX) m = warp_max(m);
-      if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < NSUM; ++j) s_tot[j] = t[j];
-        s_max = m;
-      }
+      m = warp_max(m);
+      if (lane == 0) s_max = m;
     }
     __syncthreads();
 #pragma unroll

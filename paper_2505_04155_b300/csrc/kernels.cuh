@@ -1697,33 +1697,41 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
       } else {
         update_rows<UZ, UR, V, Part>(B, n, &S, rr, d2, mx);
       }
-      double v[2];
-      if constexpr (UR != P64) {
-        v[0] = block_sum_dot2(d2, S.inv_sig2);
-      } else {
-        v[0] = rr;
-      }
+      // block totals of ||r||^2 (and rho_{k+1}) with max|r|, one pass where
+      // the operand types allow
+      double v[2] = {0.0, 0.0};
       if constexpr (kSmall) {
-        if constexpr (fused) v[1] = block_sum_dot2(d2z, S.inv_sig);
-      } else {
-        v[1] = rho;
-      }
-      if constexpr (UR == P64 && !kSmall) {
         if constexpr (fused) {
-          block_sum_wide<2>(v);
+          Dot2 dd[2] = {d2, d2z};
+          const double sc[2] = {S.inv_sig2, S.inv_sig};
+          block_sums_dot2_max<2>(dd, sc, v, mx);
         } else {
-          double w[1] = {v[0]};
-          block_sum_wide<1>(w);
+          Dot2 dd[1] = {d2};
+          const double sc[1] = {S.inv_sig2};
+          double w[1];
+          block_sums_dot2_max<1>(dd, sc, w, mx);
           v[0] = w[0];
         }
-      } else if constexpr (!kSmall) {
+      } else if constexpr (UR == P64) {
+        v[0] = rr;
+        v[1] = rho;
         if constexpr (fused) {
-          double w[1] = {v[1]};
+          block_sum_wide_max<2>(v, mx);
+        } else {
+          double w[1] = {v[0]};
+          block_sum_wide_max<1>(w, mx);
+          v[0] = w[0];
+        }
+      } else {
+        // u_z = FP64, u_r = FP32: ||r||^2 by Dot2, rho_{k+1} in binary64
+        v[0] = block_sum_dot2(d2, S.inv_sig2);
+        if constexpr (fused) {
+          double w[1] = {rho};
           block_sum_wide<1>(w);
           v[1] = w[0];
         }
+        mx = block_max(mx);
       }
-      mx = block_max(mx);
       if constexpr (fused) ok = grid_barrier_sums<2, true>(bar, B.part, B.pmax, nb, v, mx, tot, mtot, kBarrierSpin);
       else ok = grid_barrier_sums<1, true>(bar, B.part, B.pmax, nb, v, mx, tot, mtot, kBarrierSpin);
       if (!ok) break;
