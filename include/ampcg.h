@@ -366,11 +366,17 @@ ampcg_status ampcg_barrier_check(int nblocks, int absent_block, long long spin_l
 /* Autotuning of the persistent iteration kernel (Jacobi or no
  * preconditioner, slices at most 8 wide; not from the paper).  For each
  * precision pair ph = 2 u_z + u_r the kernel runs either the four-barrier
- * iteration (scaling and preconditioning in their own step) or, where the
- * scale mode allows it (AMPCG_SCALE_NONE, AMPCG_SCALE_LINF_POW2_LAG), the
+ * iteration (scaling and preconditioning in their own step) or the
  * three-barrier one (z_{k+1}, rho_{k+1} formed in the update step and reduced
- * with delta_{k+1}); both compute Alg. 3, their inner products differ only in
- * summation order.  Without tuning the three-barrier form is used. */
+ * with delta_{k+1}).  The three-barrier form needs omega_{k+1} before
+ * delta_{k+1} is reduced: AMPCG_SCALE_NONE and AMPCG_SCALE_LINF_POW2_LAG know
+ * it; under AMPCG_SCALE_LINF_POW2 the update step forms z_{k+1} with the
+ * exponent of max|r_k| and keeps it when max|r_{k+1}| has the same exponent
+ * (then omega_{k+1} is that power of two and z_{k+1} is bit for bit the one
+ * the four-barrier form computes), else the iteration forms it again in its
+ * own step.  AMPCG_SCALE_L2 has the four-barrier form only.  Both forms
+ * compute Alg. 3; their inner products differ only in summation order.
+ * Without tuning the three-barrier form is used. */
 typedef struct {
   int fused[6];        /* per pair: 1 three-barrier form, 0 four-barrier, -1 automatic */
   double us_plain[6];  /* measured device time per iteration, four-barrier form (0: not timed) */
@@ -382,8 +388,9 @@ typedef struct {
 } ampcg_tuning;
 
 /* Measures, on the context's own matrix and under the scale mode `scale`
- * (AMPCG_SCALE_NONE or AMPCG_SCALE_LINF_POW2_LAG, the modes with two forms;
- * AMPCG_ERR_INVALID_ARG otherwise), `iters` (1..10000) iterations of both
+ * (AMPCG_SCALE_NONE, AMPCG_SCALE_LINF_POW2_LAG or AMPCG_SCALE_LINF_POW2, the
+ * modes with two forms, tuned separately; AMPCG_ERR_INVALID_ARG for
+ * AMPCG_SCALE_L2), `iters` (1..10000) iterations of both
  * forms for every pair in the bit mask `pairs` (bit ph; 0 = all six), as the
  * difference of two fixed-pair solves of iters and 2 iters iterations (CUDA
  * events; fixed costs cancel), keeps the faster form per pair in the context

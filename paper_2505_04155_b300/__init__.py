@@ -359,8 +359,8 @@ class Solver:
 
     def tune(self, scale: int = SCALE_LINF_POW2_LAG, iters: int = 20, pairs=None) -> dict:
         """Autotune the persistent iteration kernel's form per precision pair
-        for solves under `scale` (SCALE_NONE or SCALE_LINF_POW2_LAG;
-        ampcg_tune): pairs is an iterable of phase indices 2*u_z + u_r, or
+        for solves under `scale` (SCALE_NONE, SCALE_LINF_POW2_LAG or
+        SCALE_LINF_POW2, each tuned on its own; ampcg_tune): pairs is an iterable of phase indices 2*u_z + u_r, or
         None for all six.  Returns the choices and the measured times."""
         mask = 0 if pairs is None else sum(1 << p for p in pairs)
         t = TuningC()

@@ -148,7 +148,8 @@ struct ampcg_ctx {
   // k_loop form per pair for the scale modes that allow the three-barrier
   // one ([0] SCALE_NONE, [1] LINF_POW2_LAG): -1 automatic (three barriers),
   // 0 four, 1 three; set by ampcg_tune / ampcg_set_tuning
-  int loop_form[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
+  // per scale slot (NONE, lagged power of two, exact power of two; see scale_slot)
+  int loop_form[3][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
   unsigned fused_mask = 0;   // the current solve's forms: bit ph set = three-barrier k_loop for pair ph
   int batch_block = 0;       // block size of the batched kernel for batches led by this context (0: 1024)
   // Chebyshev preconditioner data (reading R8)
@@ -977,6 +978,16 @@ static ampcg_status timed_loop(ampcg_ctx* c, ampcg_kernel_times* kt, cudaEvent_t
   return AMPCG_OK;
 }
 
+// Tuning slot of a scale mode: the iteration kernel's form is chosen
+// separately for NONE, the lagged and the exact power of two (-1: L2, which
+// has the four-barrier form only).
+static int scale_slot(int scale) {
+  if (scale == AMPCG_SCALE_NONE) return 0;
+  if (scale == AMPCG_SCALE_LINF_POW2_LAG) return 1;
+  if (scale == AMPCG_SCALE_LINF_POW2) return 2;
+  return -1;
+}
+
 static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double tol, int maxit,
                                const ampcg_policy* policy, ampcg_result* res,
                                ampcg_kernel_times* kt, cudaStream_t s_override = nullptr);
@@ -1014,11 +1025,14 @@ static ampcg_status solve_impl(ampcg_ctx* c, const double* b, double* x, double 
   // 128^3 solves), short for the kernel sequence (its launches after the stop
   // return at entry but still cost a launch each)
   int chunk = pol.graph_chunk > 0 ? pol.graph_chunk : (c->use_loop ? kLoopChunk : kSeqChunk);
-  // the persistent kernel's three-barrier form where omega_{k+1} is known
-  // before delta_{k+1} is reduced, per pair as tuned (automatic: three)
+  // the persistent kernel's three-barrier form, per pair as tuned
+  // (automatic: three): for the scale modes whose omega_{k+1} is known before
+  // delta_{k+1} is reduced, and for the exact power of two, whose z_{k+1} is
+  // formed with the exponent of max|r_k| and kept when max|r_{k+1}| has it
   c->fused_mask = 0;
-  if (pol.scale == AMPCG_SCALE_NONE || pol.scale == AMPCG_SCALE_LINF_POW2_LAG) {
-    const int* form = c->loop_form[pol.scale == AMPCG_SCALE_NONE ? 0 : 1];
+  const int fslot = scale_slot(pol.scale);
+  if (fslot >= 0) {
+    const int* form = c->loop_form[fslot];
     for (int ph = 0; ph < 6; ++ph)
       if (form[ph] != 0) c->fused_mask |= 1u << ph;
   }
@@ -1894,14 +1908,11 @@ ampcg_status time_fixed_pair(ampcg_ctx* c, int ph, int scale, int maxit, const d
 }
 }  // namespace
 
-static int scale_slot(int scale) {
-  return scale == AMPCG_SCALE_NONE ? 0 : (scale == AMPCG_SCALE_LINF_POW2_LAG ? 1 : -1);
-}
 
 extern "C" ampcg_status ampcg_set_tuning(ampcg_t c, int scale, const ampcg_tuning* t) {
   if (!c || !t) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
   const int sl = scale_slot(scale);
-  if (sl < 0) return fail(AMPCG_ERR_INVALID_ARG, "only AMPCG_SCALE_NONE and AMPCG_SCALE_LINF_POW2_LAG have two forms");
+  if (sl < 0) return fail(AMPCG_ERR_INVALID_ARG, "AMPCG_SCALE_L2 has one form of the iteration kernel");
   for (int ph = 0; ph < 6; ++ph)
     if (t->fused[ph] < -1 || t->fused[ph] > 1) return fail(AMPCG_ERR_INVALID_ARG, "fused[%d] must be -1, 0 or 1", ph);
   for (int ph = 0; ph < 6; ++ph) c->loop_form[sl][ph] = t->fused[ph];
@@ -1911,7 +1922,7 @@ extern "C" ampcg_status ampcg_set_tuning(ampcg_t c, int scale, const ampcg_tunin
 extern "C" ampcg_status ampcg_tune(ampcg_t c, int scale, int iters, int pairs, ampcg_tuning* out) {
   if (!c || !out) return fail(AMPCG_ERR_INVALID_ARG, "NULL argument");
   const int sl = scale_slot(scale);
-  if (sl < 0) return fail(AMPCG_ERR_INVALID_ARG, "only AMPCG_SCALE_NONE and AMPCG_SCALE_LINF_POW2_LAG have two forms");
+  if (sl < 0) return fail(AMPCG_ERR_INVALID_ARG, "AMPCG_SCALE_L2 has one form of the iteration kernel");
   if (iters < 1 || iters > 10000) return fail(AMPCG_ERR_INVALID_ARG, "iters must be in [1, 10000]");
   if (pairs < 0 || pairs > 63) return fail(AMPCG_ERR_INVALID_ARG, "pairs is a mask of 6 bits");
   if (pairs == 0) pairs = 63;

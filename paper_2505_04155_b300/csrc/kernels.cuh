@@ -694,13 +694,15 @@ struct PrecondScalars {
       : r_cast(st->r_cast), pow2(st->omega_pow2), oe(st->omega_e),
         om_one(st->omega_pow2 && st->omega_e == 0), om(st->omega), omf(st->omega_f), sigf(st->sig_f) {}
   // The scalars of iteration k + 1 as the update step of iteration k knows
-  // them, for scale modes whose omega_{k+1} does not depend on r_{k+1}: NONE
-  // (1) and the lagged power of two 2^-ceil(log2 max|r_k|) (reading R20).
-  // The binary32 dot-product scale stays sigma_k (a power of two that only
-  // keeps the terms in range; the block totals are unscaled by it).
+  // them: NONE (omega = 1); the lagged power of two 2^-ceil(log2 max|r_k|)
+  // (reading R20); and for the exact power of two the same exponent as a
+  // guess, kept only when max|r_{k+1}| turns out to have it (the caller
+  // checks).  The binary32 dot-product scale stays sigma_k (a power of two
+  // that only keeps the terms in range; the block totals are unscaled by it).
   __device__ __forceinline__ static PrecondScalars next(const DevState* st) {
     PrecondScalars c(st);
-    const int e = st->scale == SCALE_LINF_POW2_LAG ? omega_exponent(st->maxr) : 0;
+    const bool p2 = st->scale == SCALE_LINF_POW2_LAG || st->scale == SCALE_LINF_POW2;
+    const int e = p2 ? omega_exponent(st->maxr) : 0;
     c.r_cast = 0;
     c.pow2 = 1;
     c.oe = e;
@@ -1738,9 +1740,14 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
       if (threadIdx.x == 0) {
         const double d = update_step(&S, tot[0], mtot);
         if (blockIdx.x == 0) S.delta_hist[S.k] = d;
-        if (FUSED && !S.done && S.uz == UZ && S.ur == UR) {
-          // the pair is kept: z_{k+1} and rho_{k+1} stand (or are retried by
-          // the head step with the exact power of two)
+        // the pair is kept: z_{k+1} and rho_{k+1} stand (or are retried by
+        // the head step with the exact power of two).  Under the exact power
+        // of two they were formed with the exponent of max|r_k|: they are the
+        // exact scale's own (the same omega and sigma, so the same bits of
+        // z) when max|r_{k+1}| has that exponent, else the head step forms
+        // them again
+        if (FUSED && !S.done && S.uz == UZ && S.ur == UR &&
+            (S.scale != SCALE_LINF_POW2 || S.omega_e == omega_exponent(S.maxr_prev))) {
           rho_step(&S, tot[1]);
           S.z_ready = S.redo ? 0 : 1;
         }

@@ -40,8 +40,10 @@ def test_tune_measures_both_forms_and_caches_per_shape():
     assert t2["cached"] and t2["fused"] == t1["fused"]
     t3 = s2.tune(scale=P.SCALE_NONE, iters=10)     # another scale mode: measured on its own
     assert not t3["cached"]
+    t4 = s2.tune(scale=P.SCALE_LINF_POW2, iters=10)   # the exact power of two: a slot of its own
+    assert not t4["cached"]
     with pytest.raises(P.AmpcgError):
-        s2.tune(scale=P.SCALE_LINF_POW2, iters=10)
+        s2.tune(scale=P.SCALE_L2, iters=10)       # omega = 1/||r||: the four-barrier form only
     s1.close()
     s2.close()
 
@@ -55,12 +57,14 @@ def test_tune_without_the_persistent_kernel():
 
 
 @pytest.mark.parametrize("form", ["tuned", "four", "three"])
-@pytest.mark.parametrize("variant", ["amp16_lag", "pcg64"])
+@pytest.mark.parametrize("variant", ["amp16_lag", "amp16_exact", "pcg64"])
 def test_each_form_matches_oracle(form, variant):
     a = W.diffusion3d(24, 2.0, 0)
     b = W.rhs_uniform(a.n, 1)
     s = P.Solver(a.rowptr, a.col, a.val)
-    gp = P.Policy(scale=LAG, verify_refresh=3) if variant == "amp16_lag" else P.Policy.pcg64()
+    gp = {"amp16_lag": P.Policy(scale=LAG, verify_refresh=3),
+          "amp16_exact": P.Policy(scale=P.SCALE_LINF_POW2, verify_refresh=3),
+          "pcg64": P.Policy.pcg64()}[variant]
     if form == "tuned":
         s.tune(scale=gp.scale, iters=10)
     else:
