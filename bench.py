@@ -609,9 +609,11 @@ def run_profile(args):
     iterates as the graph path; profilers cannot see kernel nodes of graphs
     with conditional nodes).  `amp` is the benchmarked AMP-PCG policy;
     `p1`/`p2`/`fp64` pin the precision pair of Phase 1 (u_z=FP16, u_r=FP64),
-    Phase 2 (FP16, FP32) or PCG(FP64) (four-barrier iteration kernel);
-    `p1_lag`/`p2_lag` the same pairs under the lagged scale (three-barrier
-    iteration kernel)."""
+    Phase 2 (FP16, FP32) or PCG(FP64): the AMP pairs under the benchmark's
+    exact power-of-two scale in the three-barrier iteration kernel the
+    benchmark runs, PCG(FP64) in the four-barrier one its tuner keeps;
+    `p1_four`/`p2_four` the AMP pairs in the four-barrier kernel;
+    `p1_lag`/`p2_lag` the same pairs under the lagged scale."""
     import torch
     import paper_2505_04155_b300 as P
     torch.cuda.set_device(0)
@@ -655,11 +657,15 @@ def run_profile(args):
     pol = {"amp": P.Policy(u0=P.FP16, criterion=P.CRIT_LINEAR, verify_refresh=3),
            "p1": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64),
            "p2": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32),
+           "p1_four": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64),
+           "p2_four": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32),
            "p1_lag": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP64, scale=lag),
            "p2_lag": P.Policy(criterion=P.CRIT_FIXED, fixed_uz=P.FP16, fixed_ur=P.FP32, scale=lag),
            "fp64": P.Policy.pcg64()}[args.profile]
     if args.profile == "fp64":
         s.set_tuning([0] * 6, scale=P.SCALE_NONE)   # the form the autotuner keeps for FP64 PCG
+    if args.profile.endswith("_four"):
+        s.set_tuning([0] * 6, scale=P.SCALE_LINF_POW2)
     maxit = args.profile_iters if args.profile_iters > 0 else MAXIT
     bd = torch.as_tensor(b, device="cuda")
     _, info = s.solve(bd, tol=TOL, maxit=maxit, policy=pol, history=False, timed=True)
@@ -678,8 +684,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--profile", choices=["amp", "p1", "p2", "p1_lag", "p2_lag", "fp64", "batch_p1", "batch_p2",
-                                          "cheb_p2", "cheb_fp64"],
+    ap.add_argument("--profile", choices=["amp", "p1", "p2", "p1_four", "p2_four", "p1_lag", "p2_lag", "fp64",
+                                          "batch_p1", "batch_p2", "cheb_p2", "cheb_fp64"],
                     default=None,
                     help="run one solve for a profiler and exit")
     ap.add_argument("--profile-iters", type=int, default=0, help="maxit of the profiled solve (0: converge)")
