@@ -48,7 +48,7 @@ typedef enum {
   AMPCG_ERR_OOM = -6,          /* device allocation failed */
   AMPCG_ERR_TIMEOUT = -7,      /* a bounded device wait ran out */
   AMPCG_ERR_NO_DEVICE = -8,    /* no CUDA device is visible */
-  AMPCG_ERR_UNSUPPORTED = -9   /* valid request this build does not support */
+  AMPCG_ERR_UNSUPPORTED = -9   /* valid request the library does not support */
 } ampcg_status;
 
 /* Preconditioner M (Alg. 3 applies M^-1 to the scaled residual). */

@@ -1,8 +1,8 @@
 """The benchmark solve itself (128^3 high-contrast diffusion, 2,097,152
 unknowns) against the oracle's own solves of the same system, stored in
 tests/golden/c2_diffusion128.json by tests/golden/make_c2_golden.py (which
-calls only the oracle).  The bars are the ones the method's parity is judged
-by: iterations within 5% of the oracle's (the reductions run in another order,
+calls only the oracle).  The bars the method's parity is held to:
+iterations within 5% of the oracle's (the reductions run in another order,
 so the trajectories part after hundreds of iterations), the u_r switch within
 the same 5% (10% for the lagged scale, see BAND), an FP64-verified relative
 residual of 1e-10, and the solution
@@ -43,8 +43,8 @@ def _rel(u, v):
     return float(np.linalg.norm(u - v) / np.linalg.norm(v))
 
 
-# iteration band against the oracle's count: the benchmark spec's 5% for the
-# default (exact power-of-two) scale; the lagged scale (reading R20) is held
+# iteration band against the oracle's count: 5% for the default (exact
+# power-of-two) scale; the lagged scale (reading R20) is held
 # to 10%: its binary16 trajectory on this system parts more from the oracle's
 # under the other summation order (measured: 1475 against 1569, 6%)
 BAND = {"amp16_linear": 0.05, "amp16_linear_lag": 0.10}
