@@ -1,15 +1,16 @@
 // kernels.cuh -- AMP-PCG (Algorithm 3 of Guo, de Sturler, Warburton) on one
 // B300.  The row loops of each step of Alg. 3 are device functions shared by
-// three drivers:
+// three kernel families:
 //   k_loop (Jacobi or no preconditioner, slices at most kStageW wide): the
 //     iteration loop of one precision pair in one cooperative launch; grid
 //     barriers (with the grid sums) separate the steps.
-//   the kernel sequence (Chebyshev preconditioner, wide slices, and the
-//     launch-by-launch mode): the precondition step (k_precond_dir, or the
-//     Chebyshev kernels then k_axpy), k_spmv and k_update; each grid reduction
-//     is single-pass (last-block ticket) and its last block runs the scalar
-//     step of the algorithm.
+//   the kernel sequence (Chebyshev preconditioner, wide slices): the
+//     precondition step (k_precond_dir, or the Chebyshev kernels then k_axpy),
+//     k_spmv and k_update; each grid reduction is single-pass (last-block
+//     ticket) and its last block runs the scalar step of the algorithm.
 //   k_batched (batched.cuh): one block per system.
+// The launch-by-launch mode (per-kernel timing) runs the same kernels, k_loop
+// one iteration per launch.
 // The steps: scaling and preconditioning y = omega r (u_r), z = M^-1 y (u_z),
 // rho and beta; search direction p = z + beta p (u_z); q = A p (u_r), gamma
 // and alpha; x += alpha p (FP64), r -= alpha q (u_r), ||r||, max|r|, the
