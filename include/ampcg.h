@@ -78,7 +78,12 @@ typedef enum {
 typedef enum {
   AMPCG_SCALE_NONE = 0,      /* omega = 1 (plain PCG) */
   AMPCG_SCALE_L2 = 1,        /* omega = 1/||r_k||, as printed in Alg. 3 */
-  AMPCG_SCALE_LINF_POW2 = 2, /* omega = 2^-ceil(log2 max|r_k|): exact, max|y| in (0.5, 1] */
+  AMPCG_SCALE_LINF_POW2 = 2, /* omega = 2^-ceil(log2 max|r_k|): exact, max|y| in (0.5, 1].
+                                The persistent iteration kernel forms z_{k+1} and rho_{k+1} in
+                                its update step with the exponent of max|r_k| and keeps them
+                                when max|r_{k+1}| has that exponent (then they are the ones
+                                this omega gives, bit for bit); otherwise the iteration forms
+                                them again (see ampcg_tune). */
   AMPCG_SCALE_LINF_POW2_LAG = 3 /* omega_k = 2^-ceil(log2 max|r_{k-1}|) (k >= 1; omega_0 from r_0):
                                  the previous iteration's power of two, a lagged factor as
                                  Sec. 3.3 allows; if rho_k comes out non-finite (y_k overflowed
