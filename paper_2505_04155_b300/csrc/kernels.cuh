@@ -1558,26 +1558,32 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
   // parameter rather than a run-time branch: one kernel holding both update
   // steps spilled 112-172 bytes of registers against 32-100.
   constexpr bool fused = FUSED;
+  // z_k of the first kZr vectors of a thread kept in registers from the head
+  // step to the direction step (the four-barrier form, whose every iteration
+  // runs the head step); the three-barrier form runs it only now and then and
+  // passes z_k through its buffer, which leaves the registers to the rest
+  constexpr int kZr = FUSED ? 0 : kZreg;
+  constexpr int kZa = kZr > 0 ? kZr : 1;
   double tot[2] = {0.0, 0.0};
   unsigned long long mtot = 0ull;
   bool ok = true;
   int nb = 0;   // barriers passed in this launch
   for (int it = 0; it < iters; ++it) {
-    alignas(16) TZ zr[kZreg][VZ];
-    alignas(16) TZ pr[kZreg][VZ];
-    bool have = false;   // z_k of the first kZreg vectors of the thread in registers
+    alignas(16) TZ zr[kZa][VZ];
+    alignas(16) TZ pr[kZa][VZ];
+    bool have = false;   // z_k of the first kZr vectors of the thread in registers
     bool pre = false;    // and p_{k-1} of those vectors
     if (!S.z_ready) {
       // Alg. 3: scaling, preconditioning, rho_k and beta_{k-1}; with binary16
       // storage p_{k-1} of the register-held vectors is loaded before the
       // barrier (it does not depend on beta_{k-1}; not when it is converted)
       {
-        pre = (UZ == P16) && !S.p_cast && !S.first;
+        pre = kZr > 0 && (UZ == P16) && !S.p_cast && !S.first;
         const PrecondScalars c(&S);
         double rho = 0.0;
         Dot2 d2;
 #pragma unroll
-        for (int t = 0; t < kZreg; ++t) {
+        for (int t = 0; t < kZr; ++t) {
           const int64_t v = v0 + t * stride;
           if (v < nvz) {
             const int64_t i0 = v * VZ;
@@ -1588,13 +1594,13 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
           if (pre) {
             const TZ* po = (const TZ*)(S.pcur ? B.p[1] : B.p[0]);
 #pragma unroll
-            for (int t = 0; t < kZreg; ++t) {
+            for (int t = 0; t < kZr; ++t) {
               const int64_t v = v0 + t * stride;
               if (v < nvz) vldcg<VZ>(po + v * VZ, pr[t]);
             }
           }
         }
-        for (int64_t v = v0 + kZreg * stride; v < nvz; v += stride) {
+        for (int64_t v = v0 + kZr * stride; v < nvz; v += stride) {
           const int64_t i0 = v * VZ;
           const int m = (n - i0 < VZ) ? (int)(n - i0) : VZ;
           alignas(16) TZ zz[VZ];
@@ -1619,7 +1625,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
         --it;
         continue;
       }
-      have = true;
+      have = kZr > 0;
     }
     if (threadIdx.x == 0) S.phase_runs[2 * UZ + UR] += 1;
     // Alg. 3: search direction p_k = z_k + beta_{k-1} p_{k-1}
@@ -1651,7 +1657,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
       };
       if (have) {
 #pragma unroll
-        for (int t = 0; t < kZreg; ++t) {
+        for (int t = 0; t < kZr; ++t) {
           const int64_t v = v0 + t * stride;
           if (v < nvz) {
             const int64_t i0 = v * VZ;
@@ -1661,7 +1667,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
       }
       // z_k of the other vectors (all of them when the previous update step
       // formed z_k) is in its buffer, written by other threads before a barrier
-      for (int64_t v = v0 + (have ? kZreg * stride : 0); v < nvz; v += stride) {
+      for (int64_t v = v0 + (have ? kZr * stride : 0); v < nvz; v += stride) {
         const int64_t i0 = v * VZ;
         alignas(16) TZ zz[VZ];
         vldcg<VZ>(z + i0, zz);
