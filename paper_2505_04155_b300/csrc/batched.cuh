@@ -61,6 +61,8 @@ constexpr int batch_smem_bytes() {
 struct TeamPart {
   __device__ static __forceinline__ int64_t first() { return threadIdx.x; }
   __device__ static __forceinline__ int64_t count() { return blockDim.x; }
+  __device__ static __forceinline__ int64_t warp() { return threadIdx.x >> 5; }
+  __device__ static __forceinline__ int64_t warps() { return blockDim.x >> 5; }
   template <class T>
   __device__ static __forceinline__ T ldm(const T* p) { return __ldca(p); }
   template <int V, class T>

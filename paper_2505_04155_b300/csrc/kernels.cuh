@@ -407,6 +407,9 @@ __device__ void decide(DevState* st, H hist) {
 struct GridPart {
   __device__ static __forceinline__ int64_t first() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
   __device__ static __forceinline__ int64_t count() { return (int64_t)gridDim.x * blockDim.x; }
+  // warps in block order (the slice loops: a warp per slice or per run of slices)
+  __device__ static __forceinline__ int64_t warp() { return first() >> 5; }
+  __device__ static __forceinline__ int64_t warps() { return count() >> 5; }
   template <class T>
   __device__ static __forceinline__ T ldm(const T* p) { return *p; }
   template <int V, class T>
@@ -594,8 +597,8 @@ template <int IT, class Part = GridPart>
 __device__ __forceinline__ void init_rows(const Sell& A, const Bufs& B, double (&v)[2],
                                           unsigned long long& mx) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = Part::first() >> 5;
-  const int64_t nwarps = Part::count() >> 5;
+  const int64_t warp = Part::warp();
+  const int64_t nwarps = Part::warps();
   for (int64_t s = warp; s < A.nslices; s += nwarps) {
     int row = (int)s * 32 + lane;
     if (row < A.n) {
@@ -1055,8 +1058,8 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   TR* sv = (TR*)(smem + (size_t)wib * K * SE * (sizeof(TR) + sizeof(TI)));
   TI* si = (TI*)(sv + K * SE);
-  const int64_t gw = Part::first() >> 5;
-  const int64_t nw = Part::count() >> 5;
+  const int64_t gw = Part::warp();
+  const int64_t nw = Part::warps();
   const int64_t spw = (A.nslices + nw - 1) / nw;
   const int64_t s1 = gw * spw + spw < A.nslices ? gw * spw + spw : A.nslices;
   const bool hint = A.stream_hint != 0;
@@ -1216,8 +1219,8 @@ __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const De
   constexpr bool kSmall = (UR != P64) && (UZ != P64);
   const TR* __restrict__ va = mat_vals<UR>(A);
   const int lane = threadIdx.x & 31;
-  const int64_t gw = (Part::first()) >> 5;
-  const int64_t nw = (Part::count()) >> 5;
+  const int64_t gw = Part::warp();
+  const int64_t nw = Part::warps();
   const int64_t spw = (A.nslices + nw - 1) / nw;
   const int64_t s0 = gw * spw;
   const int64_t s1 = s0 + spw < A.nslices ? s0 + spw : A.nslices;
@@ -1508,8 +1511,19 @@ __global__ void __launch_bounds__(256) k_update(Bufs B, int64_t n, DevState* st)
 // writes the histories).  Data that other blocks write during the launch is
 // read through L2 (LoopPart), never through the read-only path.
 struct LoopPart {
-  __device__ static __forceinline__ int64_t first() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+  // Rank of the thread in the grid-stride loops over rows or vectors, warps
+  // interleaved across the blocks (warp w of block b is warp w G + b, G
+  // blocks): a loop whose trip count is not the same for every thread gives
+  // its extra trips to the first warps of every block rather than to whole
+  // blocks, so the work per SM (the FP64 pipe is an SM's own) differs by at
+  // most a warp's.  Each warp still covers 32 consecutive indices.
+  __device__ static __forceinline__ int64_t first() {
+    return ((int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+  }
   __device__ static __forceinline__ int64_t count() { return (int64_t)gridDim.x * blockDim.x; }
+  // warps in block order (the staged SpMV: each warp a contiguous run of slices)
+  __device__ static __forceinline__ int64_t warp() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+  __device__ static __forceinline__ int64_t warps() { return count() >> 5; }
   // the loads carry an L2 evict-last hint: the vectors stay in L2 across
   // iterations while the matrix streams through (evict-first)
   template <class T>
@@ -1840,8 +1854,8 @@ __global__ void k_loop_ctl(DevState* st, cudaGraphConditionalHandle h) {
 template <int IT, class Part = GridPart>
 __device__ __forceinline__ void true_res_rows(const Sell& A, const Bufs& B, double (&v)[1]) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = Part::first() >> 5;
-  const int64_t nwarps = Part::count() >> 5;
+  const int64_t warp = Part::warp();
+  const int64_t nwarps = Part::warps();
   for (int64_t s = warp; s < A.nslices; s += nwarps) {
     int row = (int)s * 32 + lane;
     if (row < A.n) {
