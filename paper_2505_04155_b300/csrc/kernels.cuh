@@ -761,7 +761,6 @@ __device__ __forceinline__ void precond_vec(const Bufs& B, const PrecondScalars&
                                             typename Store<UZ>::T (&zz)[V], double& rho, Dot2& d2) {
   using TZ = typename Store<UZ>::T;
   using TR = typename Store<UR>::T;
-  constexpr bool kSmall = (UR != P64) && (UZ != P64);
   alignas(16) TR r[V];
   if constexpr (UR == P64) {
     if (c.r_cast) {
