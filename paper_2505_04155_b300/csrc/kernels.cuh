@@ -1059,15 +1059,16 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
   TI* si = (TI*)(sv + K * SE);
   const int64_t gw = Part::warp();
   const int64_t nw = Part::warps();
-  const int64_t spw = (A.nslices + nw - 1) / nw;
-  const int64_t s1 = gw * spw + spw < A.nslices ? gw * spw + spw : A.nslices;
+  // warp gw owns slices [gw S / W, (gw + 1) S / W): runs differ by at most
+  // one slice, the longer ones spread evenly over the blocks (SMs)
+  const int64_t s1 = (gw + 1) * A.nslices / nw;
   const bool hint = A.stream_hint != 0;
   const unsigned long long pol = hint ? l2_policy_evict_first() : 0ull;
   // slice-uniform offsets (int16 layout): such a slice stages its values only
   const bool upat = IT == 1 && A.pat != nullptr;
   // chunks of at most 32 slices (one header per lane); one chunk in the
   // single-system launch, whose grid gives every warp at most 32 slices
-  for (int64_t s0 = gw * spw; s0 < s1; s0 += 32) {
+  for (int64_t s0 = gw * A.nslices / nw; s0 < s1; s0 += 32) {
     const int cnt = (int)(s1 - s0 < 32 ? s1 - s0 : 32);
     long long hoff = 0;
     int hw = 0;
@@ -1220,9 +1221,8 @@ __device__ __forceinline__ void spmv_rows(const Sell& A, const Bufs& B, const De
   const int lane = threadIdx.x & 31;
   const int64_t gw = Part::warp();
   const int64_t nw = Part::warps();
-  const int64_t spw = (A.nslices + nw - 1) / nw;
-  const int64_t s0 = gw * spw;
-  const int64_t s1 = s0 + spw < A.nslices ? s0 + spw : A.nslices;
+  const int64_t s0 = gw * A.nslices / nw;        // runs as in spmv_rows_staged
+  const int64_t s1 = (gw + 1) * A.nslices / nw;
   for (int64_t sb = s0; sb < s1; sb += 32) {
     const int64_t sh = sb + lane;
     long long hoff = 0;
@@ -1785,7 +1785,7 @@ __global__ void __launch_bounds__(kLoopBlock, 1) k_loop(Sell A, Bufs B, int64_t 
 
 // The staged SpMV of k_loop on its own, launched with k_loop's grid and
 // shared memory, so its work split (each warp a contiguous run of
-// ceil(nslices / warps) slices, LoopStageCfg stages per warp, the two-slice
+// floor or ceil(nslices / warps) slices, LoopStageCfg stages per warp, the two-slice
 // overlapped trip, the L2 hint of the matrix stream) is the one the solve
 // runs: q = A p in u_r; part[b] = block b's partial of gamma = q^T p.  B.p[0]
 // and B.p[1] both hold p.  For parity tests of that code path.
