@@ -68,8 +68,8 @@ def config_dict(a, extra=None):
 # its current form (dram__bytes_read.sum + dram__bytes_write.sum of a
 # single-iteration launch on the benchmark system); a stored figure, to be
 # recaptured whenever the kernel changes.  Kernels without one report null.
-NCU_TRAFFIC = {"amp:iteration:uz16_ur64": 165.80e6, "amp:iteration:uz16_ur32": 98.30e6,
-               "fp64:iteration:uz64_ur64": 212.70e6}
+NCU_TRAFFIC = {"amp:iteration:uz16_ur64": 165.90e6, "amp:iteration:uz16_ur32": 97.90e6,
+               "fp64:iteration:uz64_ur64": 212.40e6}
 
 
 def peaks():

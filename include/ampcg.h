@@ -398,7 +398,10 @@ typedef struct {
  * AMPCG_SCALE_L2), `iters` (1..10000) iterations of both
  * forms for every pair in the bit mask `pairs` (bit ph; 0 = all six), as the
  * difference of two fixed-pair solves of iters and 2 iters iterations (CUDA
- * events; fixed costs cancel), keeps the faster form per pair in the context
+ * events, the best of three timings of each; fixed costs cancel; where the
+ * difference is not positive, as on a small system whose fixed costs swamp
+ * it, both forms are compared on their 2 iters solves, per iteration), keeps
+ * the faster form per pair in the context
  * for later solves under that scale mode, and fills *out.  Results are cached
  * per matrix shape (rows, entries, layout, preconditioner, device) and scale
  * mode within the process: a later call for an equal shape reuses them
