@@ -33,7 +33,9 @@ def test_tune_measures_both_forms_and_caches_per_shape():
     assert all(v in (0, 1) for v in t1["fused"].values())
     assert all(v > 0 for v in t1["us_four_barrier"].values()) and len(t1["us_three_barrier"]) == 6
     for ph, f in t1["fused"].items():
-        assert f == (1 if t1["us_three_barrier"][ph] < t1["us_four_barrier"][ph] else 0)
+        u3, u4 = t1["us_three_barrier"][ph], t1["us_four_barrier"][ph]
+        if abs(u3 - u4) > 0.011:   # the times are reported to 0.01 us: a tie may go either way
+            assert f == (1 if u3 < u4 else 0)
     assert not t1["cached"]
     s2 = P.Solver(a.rowptr, a.col, a.val)          # same shape: the cached result
     t2 = s2.tune(scale=LAG, iters=10)
