@@ -998,8 +998,9 @@ __global__ void __launch_bounds__(256) k_precond_dir(Bufs B, int64_t n, DevState
 // alpha_k = rho_k / gamma_k.  One thread per row of a warp's slice.
 // ---------------------------------------------------------------------------
 // Staged SpMV.  The matrix stream (values and column indices) is the bulk of
-// the bytes; a warp owns a contiguous run of at most 32 slices (the launch
-// guarantees it) whose data is one contiguous region, and copies it into
+// the bytes; a warp owns a contiguous run of slices (floor or ceil of slices
+// per warp), taken in chunks of at most 32 (one header per lane), whose data
+// is one contiguous region, and copies it into
 // shared memory with a K-stage cp.async pipeline (16-byte copies through L2
 // only), so K-1 slices are in flight while the current slice's gathers and
 // fmas run.  cp.async.wait_group is a hardware wait, not a spin loop.  Every
@@ -1066,8 +1067,9 @@ __device__ __forceinline__ void spmv_rows_staged(const Sell& A, const Bufs& B, c
   const unsigned long long pol = hint ? l2_policy_evict_first() : 0ull;
   // slice-uniform offsets (int16 layout): such a slice stages its values only
   const bool upat = IT == 1 && A.pat != nullptr;
-  // chunks of at most 32 slices (one header per lane); one chunk in the
-  // single-system launch, whose grid gives every warp at most 32 slices
+  // chunks of at most 32 slices (one header per lane); one chunk per warp
+  // while the runs hold at most 32 slices (the persistent kernel on 148 SMs:
+  // up to 4.8 M rows)
   for (int64_t s0 = gw * A.nslices / nw; s0 < s1; s0 += 32) {
     const int cnt = (int)(s1 - s0 < 32 ? s1 - s0 : 32);
     long long hoff = 0;
