@@ -50,6 +50,22 @@ def test_tune_measures_both_forms_and_caches_per_shape():
     s2.close()
 
 
+def test_tune_small_system_times_every_pair():
+    # 12^3 rows: the fixed costs of a solve (copies, initial and true
+    # residual) are comparable to the timed iterations, so the difference of
+    # the iters and 2 iters solves can vanish; every pair still gets a positive
+    # time per form and a choice that follows the times
+    a = W.diffusion3d(12, 1.0, 0)
+    s = P.Solver(a.rowptr, a.col, a.val)
+    t = s.tune(scale=P.SCALE_LINF_POW2, iters=4)
+    assert len(t["us_four_barrier"]) == 6 and len(t["us_three_barrier"]) == 6
+    for ph, f in t["fused"].items():
+        u3, u4 = t["us_three_barrier"][ph], t["us_four_barrier"][ph]
+        if abs(u3 - u4) > 0.011:
+            assert f == (1 if u3 < u4 else 0)
+    s.close()
+
+
 def test_tune_without_the_persistent_kernel():
     a = W.diffusion3d(8, 1.0, 0)
     s = P.Solver(a.rowptr, a.col, a.val, precond=P.M_CHEBYSHEV, degree=4)
