@@ -6,7 +6,8 @@ warps (from 151,553 rows up on a 148-SM B300): the runs hold floor or
 ceil(slices / warps) slices, so runs of two or more occur (from 22% of the
 warps at 57^3 to every warp at 128^3, 13-14 slices), the two-slice overlapped
 trip and the stage refills run, and at 128^3 the matrix stream carries the L2
-evict-first hint.  q is compared bit for bit (one fma per stored entry in
+evict-first hint; a 20^3 system (250 slices) has warps with one slice and
+warps with none.  q is compared bit for bit (one fma per stored entry in
 ascending column order in both); gamma is a reduction in another order and
 must agree to 1e-12 relative."""
 import numpy as np
@@ -55,6 +56,7 @@ def _long_range(n):
 
 CASES = {
     "diffusion_64cubed": lambda: W.diffusion3d(64, 2.0, 3),
+    "diffusion_20cubed_few_slices": lambda: W.diffusion3d(20, 2.0, 6),
     "diffusion_57cubed_ragged": lambda: W.diffusion3d(57, 2.0, 4),
     "diffusion_128cubed": lambda: W.diffusion3d(128, 2.0, 0),
     "random_narrow_200003": lambda: _random_narrow(200003, 5),
@@ -77,7 +79,10 @@ def test_layout_takes_the_paths_under_test(case):
     name, a, s = case
     lay = s.layout()
     warps = 148 * 32
-    assert lay["nslices"] > warps, "runs of two or more slices need more slices than warps"
+    if name.endswith("few_slices"):
+        assert lay["nslices"] < warps      # runs of zero or one slice
+    else:
+        assert lay["nslices"] > warps, "runs of two or more slices need more slices than warps"
     assert lay["maxw"] <= 8
     assert lay["idx16"] == (0 if name.startswith("long_range") else 1)
     if name == "diffusion_128cubed":
